@@ -1,0 +1,359 @@
+"""Pins of the oracle's scheme: the paper's printed convergence table, the exact
+Sod solution, closed-form averaged divergences, conservation, positivity,
+symmetry, and hand-built detection cases with known outcomes."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import exact_riemann as ER
+import oracle as O
+from paper_2110_08683_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def euler_flux(U, gamma=1.4):
+    # eq. euler_eqn, x direction
+    r, mx, my, E = U
+    u, v = mx / r, my / r
+    p = (gamma - 1.0) * (E - 0.5 * r * (u * u + v * v))
+    return np.array([mx, mx * u + p, mx * v, u * (E + p)])
+
+
+def cons(r, u, v, p, gamma=1.4):
+    return np.array([r, r * u, r * v, p / (gamma - 1) + 0.5 * r * (u * u + v * v)])
+
+
+# --------------------------------------------------------------------------
+# Riemann solver
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("state", [(1.0, 0.3, -0.2, 1.0), (0.125, -2.0, 0.5, 0.1), (8.0, 7.1, -4.1, 116.5)])
+def test_hllc_consistency(state):
+    U = cons(*state)
+    np.testing.assert_allclose(O.hllc(U, U), euler_flux(U), rtol=1e-14, atol=1e-14)
+    Uy = np.array([U[0], U[2], U[1], U[3]])
+    Gy = O.hllc(U, U, direction=1)
+    Fx = euler_flux(Uy)
+    np.testing.assert_allclose(Gy, [Fx[0], Fx[2], Fx[1], Fx[3]], rtol=1e-14, atol=1e-14)
+
+
+def test_hllc_resolves_stationary_contact_exactly():
+    # a contact with u = 0 and equal pressure: the exact flux is (0, p, 0, 0)
+    UL, UR = cons(1.0, 0.0, 0.3, 0.7), cons(0.2, 0.0, -0.5, 0.7)
+    np.testing.assert_allclose(O.hllc(UL, UR), [0.0, 0.7, 0.0, 0.0], atol=1e-15)
+
+
+def test_hllc_supersonic_is_upwind():
+    UL, UR = cons(1.0, 3.0, 0.1, 0.4), cons(0.5, 2.5, 0.0, 0.3)
+    np.testing.assert_allclose(O.hllc(UL, UR), euler_flux(UL), rtol=1e-15)
+    UL, UR = cons(1.0, -3.0, 0.1, 0.4), cons(0.5, -3.5, 0.0, 0.3)
+    np.testing.assert_allclose(O.hllc(UL, UR), euler_flux(UR), rtol=1e-15)
+
+
+def test_sod_against_exact_riemann_solution():
+    # Sod tube (1D, GP-R2 cascade 5->3->1, ell = 12 dx, CFL 0.8, t = 0.2):
+    # L1 density error against the exact solution decreases under refinement
+    errs = []
+    for n in (64, 128, 256):
+        p = I.sod_1d(n=n)
+        o = O.Oracle(p)
+        U, _, t = o.run(p["U0"], 0.2)
+        assert abs(t - 0.2) < 1e-14
+        xc = (np.arange(n) + 0.5) / n
+        errs.append(np.abs(U[0, 0] - ER.sod_density(xc, 0.2)).sum() / n)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 7e-3
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 0.8  # first order at discontinuities
+
+
+def test_fog_is_first_order_godunov_and_more_diffusive():
+    # radius 0 (FOG, Sec. 2.6): converges to the exact solution, slower than GP
+    e = {}
+    for cas in ([0], [2, 1, 0]):
+        errs = []
+        for n in (128, 256):
+            p = I.sod_1d(n=n, cascade=cas)
+            o = O.Oracle(p)
+            U, _, _ = o.run(p["U0"], 0.2)
+            xc = (np.arange(n) + 0.5) / n
+            errs.append(np.abs(U[0, 0] - ER.sod_density(xc, 0.2)).sum() / n)
+        e[len(cas)] = errs
+    assert e[1][1] < e[1][0]
+    assert e[1][0] > 2.0 * e[3][0]
+
+
+# --------------------------------------------------------------------------
+# spatial operator
+# --------------------------------------------------------------------------
+def _exact_averaged_divergence(n, amp):
+    # rho = 1 + amp sin(2 pi (x + y)), u = v = p = 1: every component of
+    # dF/dx + dG/dy is d(rho)/dx + d(rho)/dy; its exact cell average is the
+    # boundary integral of rho divided by the cell area
+    d = 1.0 / n
+    c = (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(c, c, indexing="xy")
+
+    def face(xf, lo, hi):  # int_lo^hi sin(2 pi (xf + s)) ds
+        return (np.cos(2 * np.pi * (xf + lo)) - np.cos(2 * np.pi * (xf + hi))) / (2 * np.pi)
+
+    ex = face(X + d / 2, Y - d / 2, Y + d / 2) - face(X - d / 2, Y - d / 2, Y + d / 2)
+    ey = face(Y + d / 2, X - d / 2, X + d / 2) - face(Y - d / 2, X - d / 2, X + d / 2)
+    return amp * (ex + ey) / (d * d)
+
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_spatial_order_is_2R_plus_1(R):
+    amp = 0.2
+    ns = (32, 64) if R < 3 else (24, 48)
+    errs = []
+    for n in ns:
+        p = I.density_wave(n=n, amp=amp, R=R, ell=0.1)
+        o = O.Oracle(p)
+        Fn = o.residual(p["U0"], np.full((n, n), R, np.uint8))
+        ex = _exact_averaged_divergence(n, amp)
+        for v in range(4):
+            errs_v = np.abs(Fn[v] - ex).mean()
+            if v == 0:
+                errs.append(errs_v)
+    eoc = math.log2(errs[0] / errs[1])
+    assert eoc > 2 * R + 1 - 0.5, (R, errs, eoc)
+
+
+@pytest.mark.parametrize("R", [0, 1, 2, 3])
+@pytest.mark.parametrize("bc", ["periodic", "outflow", "reflect"])
+def test_uniform_state_is_preserved(R, bc):
+    st = (1.0, 0.0, 0.0, 1.0) if bc == "reflect" else (1.3, 0.4, -0.25, 0.9)
+    p = I.uniform(12, 10, R=max(R, 1), state=st, bc=bc)
+    p["cascade"] = list(range(R, -1, -1))
+    o = O.Oracle(p)
+    U = p["U0"]
+    for _ in range(3):
+        U, stats, ordm, _ = o.step(U, 0.0)
+        assert stats["iters"] == [0, 0, 0]
+    np.testing.assert_allclose(U, p["U0"], rtol=2e-14, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# full scheme
+# --------------------------------------------------------------------------
+@pytest.mark.slow
+def test_table1_gpmood3_errors_reproduced():
+    # Table 1: GP-MOOD3 (R1 -> FOG), SSP-RK3, CFL 0.8, ell = 1, vortex on
+    # [0,20]^2 to t = 20; L1 = sum |rho - rho_exact| dx dy (the table's norm)
+    gold = json.load(open(os.path.join(GOLD, "table1_gpmood3_diamond.json")))
+    errs = []
+    for n, ref in zip(gold["N"][:2], gold["L1"][:2]):
+        p = I.vortex(n=n, lo=0.0, hi=20.0, R=1, ell=1.0)
+        o = O.Oracle(p)
+        U, _, _ = o.run(p["U0"], 20.0)
+        ex = I.vortex(n=n, lo=0.0, hi=20.0, R=1, ell=1.0, t=20.0)["U0"]
+        L1 = np.abs(U[0] - ex[0]).sum() * (20.0 / n) ** 2
+        errs.append(L1)
+        assert abs(L1 - ref) < 2e-3 * ref, (n, L1, ref)
+    eoc = math.log2(errs[0] / errs[1])
+    assert abs(eoc - gold["EOC"][1]) < 0.02
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_full_scheme_convergence_on_density_wave(R):
+    # SSP-RK3 with dt ~ dx^((2R+1)/3) so that time error does not dominate
+    amp = 0.1
+    errs = []
+    for n in (16, 32):
+        p = I.density_wave(n=n, amp=amp, R=R, ell=0.1)
+        o = O.Oracle(p)
+        dx = 1.0 / n
+        dt = 0.3 * dx ** ((2 * R + 1) / 3.0) if R > 1 else 0.3 * dx
+        t_end = 0.1
+        nst = int(math.ceil(t_end / dt))
+        dt = t_end / nst
+        U = p["U0"]
+        for k in range(nst):
+            U, st, _, _ = o.step(U, k * dt, dt_fixed=dt)
+        ex = I.density_wave(n=n, amp=amp, R=R, ell=0.1, t=t_end)["U0"]
+        errs.append(np.abs(U[0] - ex[0]).mean())
+    eoc = math.log2(errs[0] / errs[1])
+    assert eoc > 2 * R + 1 - 0.6, (errs, eoc)
+
+
+def test_smooth_vortex_keeps_top_order():
+    # Sec. 5.1: on smooth flow no cell is reduced below the top order
+    p = I.vortex(n=32, R=3)
+    o = O.Oracle(p)
+    U = p["U0"]
+    t = 0.0
+    for _ in range(4):
+        U, st, ordm, bad = o.step(U, t)
+        t += st["dt"]
+        assert st["nbad_first"] == [0, 0, 0]
+        assert (ordm == 3).all()
+
+
+def test_periodic_conservation_to_round_off():
+    p = I.quadrants(n=24, R=3, seed=3)
+    p["bc"] = ["periodic"] * 4
+    o = O.Oracle(p)
+    U0 = p["U0"]
+    U = U0
+    t = 0.0
+    total_iters = 0
+    for _ in range(5):
+        U, st, _, _ = o.step(U, t)
+        t += st["dt"]
+        total_iters += sum(st["iters"])
+    assert total_iters > 0  # the MOOD loop ran
+    for v in range(4):
+        s0, s1 = U0[v].sum(), U[v].sum()
+        assert abs(s1 - s0) <= 1e-13 * np.abs(U0[v]).sum()
+
+
+def test_positivity_on_double_mach_reflection():
+    p = I.dmr(nx=64, ny=16, R=3)
+    o = O.Oracle(p)
+    U = p["U0"]
+    t = 0.0
+    flagged = 0
+    for _ in range(6):
+        U, st, _, _ = o.step(U, t)
+        t += st["dt"]
+        flagged += st["nbad_first"][0]
+        gam = 1.4
+        pr = (gam - 1) * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+        assert U[0].min() > 0 and pr.min() > 0
+    assert flagged > 0
+
+
+def test_transpose_symmetry():
+    # x <-> y with u <-> v gives the transposed solution (Sec. 5.2.4 symmetry)
+    st = I.quadrant_states(seed=5)[0]
+    p = I.quadrants(n=16, R=2, states=st)
+    # quadrant order (x>,y>), (x<,y>), (x<,y<), (x>,y<): transposing swaps 1 and 3
+    stT = st[[0, 3, 2, 1]][:, [0, 2, 1, 3]]
+    pT = I.quadrants(n=16, R=2, states=stT)
+    o, oT = O.Oracle(p), O.Oracle(pT)
+    U, UT = p["U0"], pT["U0"]
+    np.testing.assert_allclose(UT[[0, 2, 1, 3]].transpose(0, 2, 1), U, rtol=1e-14, atol=1e-15)
+    for k in range(3):
+        U, s, om, _ = o.step(U, 0.0)
+        UT, sT, omT, _ = oT.step(UT, 0.0)
+        np.testing.assert_allclose(UT[[0, 2, 1, 3]].transpose(0, 2, 1), U, rtol=1e-12, atol=1e-13)
+
+
+def test_mood_iteration_cap_reports_error():
+    p = I.quadrants(n=16, R=3, seed=1)
+    p["max_iters"] = 0
+    o = O.Oracle(p)
+    with pytest.raises(RuntimeError):
+        o.step(p["U0"], 0.0)
+
+
+def test_nan_cell_cascades_to_fog():
+    p = I.vortex(n=16, R=3)
+    o = O.Oracle(p)
+    U = p["U0"].copy()
+    U[:, 8, 8] = np.nan
+    Y, ordm, bad, iters, tot = o.stage(U, 0.0, 1e-3)
+    # the NaN cell and every cell whose stencil reaches it end at FOG
+    assert ordm[8, 8] == 0 and ordm[8, 7] == 0 and ordm[7, 8] == 0
+    assert iters >= 3
+    assert bad.sum() > 0
+
+
+# --------------------------------------------------------------------------
+# detection branches on hand-built states (Steps 4-9)
+# --------------------------------------------------------------------------
+def _detector(csd_on=1, state=(1.0, 0.0, 0.0, 1.0), n=8):
+    p = I.uniform(n, n, R=1, state=state, bc="periodic")
+    p["csd_on"] = csd_on
+    return O.Oracle(p), p
+
+
+def _ghost(o, U):
+    return o.fill_ghosts(U, 0.0)
+
+
+def test_detect_cad_and_pad():
+    o, p = _detector()
+    Xg = _ghost(o, p["U0"])
+    Y = p["U0"][:, 3, 3].copy()
+    assert o.detect_cell(Xg, 3, 3, Y) == O.ACCEPT_CSD
+    for bad in (np.nan, np.inf):
+        Z = Y.copy()
+        Z[0] = bad
+        assert o.detect_cell(Xg, 3, 3, Z) == O.FAIL_CAD
+    Z = Y.copy()
+    Z[3] = np.nan  # NaN energy -> NaN pressure
+    assert o.detect_cell(Xg, 3, 3, Z) == O.FAIL_CAD
+    Z = Y.copy()
+    Z[0] = -0.5
+    assert o.detect_cell(Xg, 3, 3, Z) == O.FAIL_PAD
+    Z = Y.copy()
+    Z[3] = 0.1 * Z[3] - 1.0  # negative pressure
+    assert o.detect_cell(Xg, 3, 3, Z) == O.FAIL_PAD
+
+
+def test_detect_plateau_dmp_u2():
+    o, p = _detector(csd_on=0)
+    U = p["U0"].copy()
+    # plateau: tiny variation in rho below min(dx^3, dy^3) = 1/512
+    U[0, 3, 4] += 1e-4
+    Xg = _ghost(o, U)
+    Y = U[:, 3, 3].copy()
+    Y[0] += 0.01  # outside the range but on a plateau
+    assert o.detect_cell(Xg, 3, 3, Y) == O.ACCEPT_PLATEAU
+    # DMP: a jump in the neighbourhood, candidate within [min, max]
+    U = p["U0"].copy()
+    U[0, 3, 4] = 2.0
+    Xg = _ghost(o, U)
+    Y = U[:, 3, 3].copy()
+    Y[0] = 1.5
+    assert o.detect_cell(Xg, 3, 3, Y) == O.ACCEPT_DMP
+    # DMP fails at a sharp jump with same-sign-free curvatures -> u2 fails
+    Y[0] = 2.5
+    assert o.detect_cell(Xg, 3, 3, Y) == O.FAIL_U2
+    # smooth extremum: rho = 1 + 0.05 (x^2 + y^2)-like bump with a new maximum
+    n = 8
+    dx = 1.0 / n
+    xc = (np.arange(n) + 0.5) * dx
+    X, Yy = np.meshgrid(xc, xc, indexing="xy")
+    U = p["U0"].copy()
+    U[0] = 1.0 + 0.01 * np.cos(2 * np.pi * (X - xc[3])) * np.cos(2 * np.pi * (Yy - xc[3]))
+    Xg = _ghost(o, U)
+    Y = U[:, 3, 3].copy()
+    Y[0] = U[0, 3, 3] + 1e-4  # a new maximum at a smooth extremum
+    assert o.detect_cell(Xg, 3, 3, Y) == O.ACCEPT_U2
+
+
+def test_detect_csd_rejects_strong_compression():
+    o, p = _detector(csd_on=1)
+    gam = 1.4
+
+    def state(compress):
+        U = p["U0"].copy()
+        U[0, 3, 4] = 1.2  # a density jump: no plateau
+        if compress:  # converging flow: divV = (u_E - u_W)/(2 dx) < -sigma_v
+            U[1, 3, 2] = 1.0 * U[0, 3, 2]
+            U[1, 3, 4] = -1.0 * U[0, 3, 4]
+        U[3] = 1.0 / (gam - 1.0) + 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0]  # p = 1
+        return U
+
+    U = state(False)
+    Y = U[:, 3, 3].copy()
+    Y[0] = 1.1
+    assert o.detect_cell(_ghost(o, U), 3, 3, Y) == O.ACCEPT_CSD
+    U = state(True)
+    Y = U[:, 3, 3].copy()
+    Y[0] = 1.1
+    assert o.detect_cell(_ghost(o, U), 3, 3, Y) == O.ACCEPT_DMP
+    Y[0] = 1.3
+    assert o.detect_cell(_ghost(o, U), 3, 3, Y) == O.FAIL_U2
+    # a strong pressure gradient alone also sends the cell on to the DMP
+    U = state(False)
+    U[3, 3, 4] = 20.0 / (gam - 1.0)
+    Y = U[:, 3, 3].copy()
+    Y[0] = 1.1
+    assert o.detect_cell(_ghost(o, U), 3, 3, Y) == O.ACCEPT_DMP
