@@ -1,0 +1,370 @@
+"""Benchmark of the GB300 GP-MOOD hot path.
+
+Workload: the 2D isentropic vortex on the periodic square [-5,5]^2 at 512^2
+cells, GP-R3 with the 7->5->3->1 cascade (ell = 0.5), SSP-RK3 at CFL 0.8 --
+one step is one full SSP-RK3 step (three stages, each with its MOOD loop,
+ghost fill and the time-step reduction).  Metric: cell-updates per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py --impl reference ...    (the FP64 CPU oracle on the host)
+
+Under torchrun (N > 1) every rank runs its own replica of the workload on its
+own GPU (the method has no data exchange between independent problems);
+value = all ranks' cell-updates / the slowest rank's time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D Euler GP-MOOD cell-updates/s"
+UNIT = "cell-updates/s"
+N_DEFAULT = 512
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 128 FFMA/clk/SM
+HLLC_FLOPS = 78  # per pointwise HLLC flux, divisions and square roots counted once
+
+
+def workload(n):
+    from paper_2110_08683_gb300 import inputs as I
+
+    return I.vortex(n=n, R=3)
+
+
+def faces_flops_per_face(R=3):
+    """Arithmetic of one first-pass face launch per face: the parity sums of
+    the cell (4 variables), the q/2 parity dot products of length N and the
+    butterflies, then q HLLC fluxes and the Gauss sum."""
+    N = 2 * R * R + 2 * R + 1
+    q = R + 1
+    sums = 2 * R * 2 + (R * (R - 1) // 2) * 8
+    pairs, middle = q // 2, q % 2
+    recon = 4 * (sums + 2 * N * (pairs + middle) + 8 * pairs + 2 * middle)
+    return recon + q * (HLLC_FLOPS + 8)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2110_08683_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision):
+    """DRAM bytes per launch of the x-face kernel from the committed ncu
+    summary, or None when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "faces_x_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(precision)
+    if not ent or ent.get("kernel_sha") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = str(index)
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.index],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        # one GPU per process, selected before any CUDA call
+        os.environ["CUDA_VISIBLE_DEVICES"] = str(local)
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(n, steps=2):
+    """The FP64 CPU oracle as it stands, single thread, on a bounded sample:
+    `steps` full SSP-RK3 steps of the same workload."""
+    import oracle as O
+
+    p = workload(n)
+    o = O.Oracle(p)
+    U = p["U0"]
+    t0 = time.perf_counter()
+    t = 0.0
+    for _ in range(steps):
+        U, st, _, _ = o.step(U, t)
+        t += st["dt"]
+    el = time.perf_counter() - t0
+    return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full SSP-RK3 steps of the {n}^2 vortex, 1 thread, {el:.1f} s"}
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2110_08683_gb300 as gp
+
+    torch.cuda.set_device(0 if world > 1 else local)
+    dev_index = local
+    n = args.n
+    p = workload(n)
+    g = gp.GPMood(p, args.precision)
+    stream = torch.cuda.Stream()
+    g.set_stream(stream.cuda_stream)
+    # L2 (129 MB) is flushed between timed steps by writing 256 MB
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    g.set_state(p["U0"])
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.step()
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(dev_index)
+    g.profile(True)
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            e0[k].record(stream)
+            g.step()
+            e1[k].record(stream)
+            launches += g.last_launches()
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    kt = g.kernel_times()
+    g.profile(False)
+    ms_max = allreduce_max(ms, world)
+    cells = float(n * n * args.steps) * world
+    value = cells / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: every step copies
+    # the state in from pinned host memory and reads the result back
+    Uh = torch.empty((4, n, n), dtype=torch.float64, pin_memory=True).numpy()
+    Uh[...] = p["U0"]
+    Uo = torch.empty((4, n, n), dtype=torch.float64, pin_memory=True).numpy()
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            f0[k].record(stream)
+            g.set_state(Uh)
+            g.step()
+            g.get_state(Uo)
+            f1[k].record(stream)
+            Uh[...] = Uo
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = allreduce_max(sum(a.elapsed_time(b) for a, b in zip(f0, f1)), world)
+    e2e = {"value": cells / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(Uh.nbytes), "d2h_bytes_per_step": int(Uo.nbytes)}
+
+    # roofline of the dominant kernel: the first-pass x-face kernel
+    fx_ms, fx_n = kt["faces_x"]
+    per_launch_s = fx_ms / 1e3 / max(fx_n, 1)
+    faces = (n + 1) * n
+    flops = faces * faces_flops_per_face(3)
+    real64 = args.precision == "fp64"
+    peak = FP64_PEAK_TFLOPS if real64 else FP32_PEAK_TFLOPS
+    achieved = flops / per_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(args.precision),
+                "kernel": "k_faces<R=3,%s,x>" % ("double" if real64 else "float"),
+                "flops_per_launch": flops, "launch_ms": round(per_launch_s * 1e3, 4),
+                "peak_source": "derived: 152 SMs x %s/clk x 2.07 GHz (of nominal; measured DFMA "
+                               "1.19 TFLOP/s, FFMA 69.9 TFLOP/s)" % ("4 FP64 flop" if real64
+                                                                     else "256 FP32 flop")}
+    total_kernel_ms = sum(v[0] for v in kt.values())
+    shares = {k: round(v[0] / total_kernel_ms, 4) if total_kernel_ms else None
+              for k, v in kt.items()}
+
+    g.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if real64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"isentropic vortex {n}^2 periodic [-5,5]^2, GP-R3 cascade "
+                               f"7->5->3->1, ell=0.5, SSP-RK3, CFL 0.8, HLLC",
+                   "cells": n * n, "precision": args.precision,
+                   "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
+        "roofline": roofline,
+        "kernel_shares": shares,
+        "gpu_launches": int(allreduce_sum(launches, world)),
+        "e2e": e2e,
+    }
+    return line, sampler.summary()
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle (the reference arm of this tier) on the host cores."""
+    import oracle as O
+
+    n = args.n
+    p = workload(n)
+    o = O.Oracle(p)
+    U = p["U0"]
+    t = 0.0
+    # each step is one full SSP-RK3 step of the same workload; the count is
+    # capped so that the run stays within a few minutes
+    t0 = time.perf_counter()
+    U, st, _, _ = o.step(U, t)
+    t += st["dt"]
+    one = time.perf_counter() - t0
+    budget = 150.0
+    w = min(args.warmup, max(0, int(budget / 4 / max(one, 1e-3))))
+    k = max(1, min(args.steps, int(budget / max(one, 1e-3))))
+    for _ in range(max(0, w - 1)):
+        U, st, _, _ = o.step(U, t)
+        t += st["dt"]
+    t0 = time.perf_counter()
+    for _ in range(k):
+        U, st, _, _ = o.step(U, t)
+        t += st["dt"]
+    el = time.perf_counter() - t0
+    value = n * n * k / el
+    sample = f"{k} full SSP-RK3 steps of the {n}^2 vortex (of {args.steps} requested), 1 thread"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": k, "warmup": w, "ms_per_step": el * 1e3 / k, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"isentropic vortex {n}^2 periodic [-5,5]^2, GP-R3 cascade "
+                               f"7->5->3->1, ell=0.5, SSP-RK3, CFL 0.8, HLLC",
+                   "cells": n * n, "precision": "fp64", "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    line, clocks = run_ours(args, world, rank, local)
+    line["clocks"] = clocks
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.n)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

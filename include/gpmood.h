@@ -1,0 +1,183 @@
+/*
+ * gpmood.h -- C ABI of the GB300 GP-MOOD hot path.
+ *
+ * The method is GP-MOOD (Bourgeois & Lee, arXiv:2110.08683): finite-volume
+ * updates of the 2D Euler equations (Sec. 2.1, eqs. gov, euler_eqn,
+ * fvm_discrete, fvm_F) with Gaussian-process face reconstruction of radius R
+ * and order 2R+1 (Sec. 2.2-2.5, eqs. SE-pred, SE-cov, gp_reconstructor,
+ * normalized_z), HLLC fluxes at Gauss points (Table QR), SSP-RK3 (Sec. 3.8,
+ * eq. rk3) and the a-posteriori MOOD loop (Sec. 3, Sec. 4 Steps 1-10: CAD,
+ * PAD, CSD, plateau, DMP, u2, EDP1 face orders, cascade to first-order
+ * Godunov).
+ *
+ * Conventions for every call:
+ *  - Return 0 (GPMOOD_OK) on success or a negative GPMOOD_E_* code.  No
+ *    exception or signal crosses the ABI.  After a numerical error
+ *    (GPMOOD_E_MOOD_CAP, GPMOOD_E_DT) the handle stays valid so that the state
+ *    can be read back.
+ *  - A handle owns all of its device memory (cudaMalloc at create, freed at
+ *    destroy).  Pointers passed in are borrowed for the duration of the call.
+ *  - Work is ordered on the handle's CUDA stream (the legacy default stream
+ *    unless gpmood_set_stream gave another).  Calls that return host data
+ *    synchronise that stream.
+ *  - State arrays are conservative cell averages U = (rho, rho u, rho v, rho E)
+ *    in double precision, structure-of-arrays: U[v*ny*nx + j*nx + i] for
+ *    variable v < 4, row j < ny, column i < nx (no ghost cells).
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef GPMOOD_H
+#define GPMOOD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpmood_s* gpmood_t;
+
+/* boundary kinds per side, sides ordered W, E, S, N */
+enum {
+  GPMOOD_BC_PERIODIC = 0,   /* both sides of an axis must be periodic */
+  GPMOOD_BC_OUTFLOW = 1,    /* zero gradient: ghosts copy the nearest interior cell */
+  GPMOOD_BC_REFLECT = 2,    /* mirror, normal momentum negated */
+  GPMOOD_BC_DIRICHLET = 3,  /* fixed primitive state bc_prim[side] */
+  GPMOOD_BC_DMR_BOTTOM = 4, /* S only: x < dmr_wall_x0 -> dmr_post, else reflect */
+  GPMOOD_BC_DMR_TOP = 5     /* N only: x < dmr_xs0 + dmr_xs_speed t -> dmr_post, else dmr_pre */
+};
+
+enum { GPMOOD_FP64 = 0, GPMOOD_FP32 = 1 };
+
+enum {
+  GPMOOD_OK = 0,
+  GPMOOD_E_INVAL = -1,     /* bad argument */
+  GPMOOD_E_CUDA = -2,      /* a CUDA call failed */
+  GPMOOD_E_OOM = -3,       /* device allocation failed */
+  GPMOOD_E_WEIGHTS = -4,   /* covariance matrix not positive definite in the weight solve */
+  GPMOOD_E_MOOD_CAP = -5,  /* the MOOD loop reached max_mood_iters with cells still flagged */
+  GPMOOD_E_DT = -6,        /* the time step came out non-positive or not finite */
+  GPMOOD_E_NOSTATE = -7    /* step/run/get before set_state */
+};
+
+/* grid and boundary description (Sec. 2.1); caller-owned, copied at create */
+typedef struct {
+  int nx, ny;                 /* interior cells, each >= R_max + 1 (and >= 2) */
+  double x0, x1, y0, y1;      /* domain; dx = (x1-x0)/nx, dy = (y1-y0)/ny */
+  int bc[4];                  /* GPMOOD_BC_* for W, E, S, N */
+  double bc_prim[4][4];       /* (rho, u, v, p) for DIRICHLET sides */
+  double dmr_post[4], dmr_pre[4];            /* primitive states for the DMR kinds */
+  double dmr_wall_x0, dmr_xs0, dmr_xs_speed; /* DMR wall start and shock line x_s(t) */
+} gpmood_grid;
+
+/* options; a zero-initialised struct (or NULL) gives the paper's defaults */
+typedef struct {
+  int ncascade;         /* 0: the full cascade R_max, R_max-1, ..., 1, 0 */
+  int cascade[4];       /* GP radii, strictly decreasing, ending with 0 (FOG), e.g. {3,1,0} */
+  int precision;        /* GPMOOD_FP64 (default) or GPMOOD_FP32 (reconstruction, Riemann
+                           solver and detection in FP32; state and stage sums in FP64) */
+  double sigma_v;       /* CSD threshold on -div V (0 -> 5, Sec. 3.4) */
+  double sigma_p;       /* CSD threshold on the normalised |grad p| (0 -> 5) */
+  int csd_off;          /* 1 disables CSD (Step 6) */
+  int max_mood_iters;   /* cap on MOOD iterations per RK stage (0 -> 64) */
+} gpmood_options;
+
+/* per-step diagnostics of the most recent step */
+typedef struct {
+  double t;             /* simulation time after the step */
+  double dt;            /* the step's Delta t */
+  long long nsteps;     /* steps taken since set_state */
+  int iters[3];         /* MOOD iterations per RK stage */
+  int nbad_first[3];    /* troubled cells after the first pass, per stage */
+  int nbad_total[3];    /* troubled cells summed over all iterations, per stage */
+  int nfog_pad[3];      /* FOG candidates failing PAD (accepted per Step 10, reported) */
+  int status;           /* GPMOOD_OK or the error code of the last step */
+} gpmood_stats;
+
+/*
+ * Create a handle for one grid.  gamma: ratio of specific heats; R_max in
+ * 0..3 is the top GP radius (0 = FOG only); ell the SE length scale in
+ * physical units (ell = 12 dx in most of the paper's runs).  Solves the GP
+ * prediction vectors for every radius of the cascade in binary128 (Sec. 2.5),
+ * stores them in double and float, and allocates the device buffers.
+ * Returns GPMOOD_E_INVAL for bad sizes/kinds, GPMOOD_E_WEIGHTS if a
+ * covariance matrix is not positive definite, GPMOOD_E_OOM / _CUDA on
+ * allocation failures.  *out is NULL on failure.
+ */
+int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
+                  const gpmood_options* opts, gpmood_t* out);
+
+/* Use this CUDA stream (a cudaStream_t, may be NULL for the legacy stream). */
+int gpmood_set_stream(gpmood_t h, void* stream);
+
+/* Copy the cell averages U (layout above) in; on_device != 0 means U is a
+   device pointer.  Resets t and the step count to 0. */
+int gpmood_set_state(gpmood_t h, const double* U, int on_device);
+
+/* Set the simulation time of the current state (time-dependent boundaries
+   read it); set_state resets it to 0.  Use it to resume from a checkpoint. */
+int gpmood_set_time(gpmood_t h, double t);
+
+/* Copy the current cell averages out (device pointer if on_device != 0). */
+int gpmood_get_state(gpmood_t h, double* U, int on_device);
+
+/*
+ * One SSP-RK3 step with the MOOD loop in every stage.  Delta t is
+ * cfl * min over cells of min(dx/(|u|+c), dy/(|v|+c)), computed on the device
+ * (cfl > 0).  If dt_out is non-NULL the call waits and returns Delta t there.
+ * Returns GPMOOD_E_MOOD_CAP / GPMOOD_E_DT on numerical failure.
+ */
+int gpmood_step(gpmood_t h, double cfl, double* dt_out);
+
+/* The same with a given Delta t (> 0) instead of the CFL rule. */
+int gpmood_step_dt(gpmood_t h, double dt);
+
+/* Step until t_end, clipping the last step; the step count goes to nsteps_out. */
+int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out);
+
+/*
+ * Diagnostics of the last step (waits).  order_out (nullable, host) receives
+ * the final GP radius of every cell in each of the three stages,
+ * [3][ny][nx] uint8 (0 = FOG).  first_out (nullable, host) the first-pass
+ * troubled-cell map [3][ny][nx] (1 = flagged).  stats_out (nullable).
+ */
+int gpmood_flags(gpmood_t h, uint8_t* order_out, uint8_t* first_out, gpmood_stats* stats_out);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+int gpmood_destroy(gpmood_t h);
+
+/* Static string for a GPMOOD_E_* code. */
+const char* gpmood_strerror(int code);
+
+/*
+ * Kernel launch count of the last step (device kernels this library
+ * launched), for accounting.
+ */
+int gpmood_last_launches(gpmood_t h);
+
+/* kernel classes for gpmood_kernel_times */
+enum {
+  GPMOOD_K_DT = 0,      /* time-step reduction */
+  GPMOOD_K_GHOST = 1,   /* ghost-cell fill */
+  GPMOOD_K_FACES_X = 2, /* first-pass x faces: reconstruction, face CAD, HLLC */
+  GPMOOD_K_FACES_Y = 3, /* first-pass y faces */
+  GPMOOD_K_UPDATE = 4,  /* first-pass candidate, detection, RK sum, compaction */
+  GPMOOD_K_MOOD = 5,    /* MOOD iterations (lower, faces, update) */
+  GPMOOD_NKCLASS = 6
+};
+
+/*
+ * Device-time accounting per kernel class with CUDA events recorded on the
+ * handle's stream around every launch.  enable != 0 starts (and zeroes) the
+ * accounting, 0 stops it.  Off by default; it adds event records between
+ * launches but no synchronisation.
+ */
+int gpmood_profile(gpmood_t h, int enable);
+
+/* Accumulated milliseconds and launch counts per class (arrays of
+   GPMOOD_NKCLASS entries, either may be NULL); waits for the stream. */
+int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -846,6 +846,7 @@ double orc_dt(orc_ctx* c, const double* U, double cfl) {
       double cs = sqrt(gam * pressure(S, gam) / S[0]);
       double a = c->dx / (fabs(u) + cs);
       if (c->cfg.dim == 2) a = dmin2(a, c->dy / (fabs(v) + cs));
+      if (!(a > 0.0) || !isfinite(a)) return NAN; /* no admissible step */
       best = dmin2(best, a);
     }
   return cfl * best;

@@ -1,0 +1,285 @@
+"""GB300-native GP-MOOD hot path: Python binding of the C ABI in include/gpmood.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libgpmood.so (built in-tree by ``build.build()``).  There is no CPU fallback:
+loading fails loudly if the library is missing or no CUDA device is present.
+
+Function names follow the C ABI (gpmood_create, gpmood_set_state,
+gpmood_get_state, gpmood_step, gpmood_step_dt, gpmood_run, gpmood_flags,
+gpmood_destroy, gpmood_strerror); ``GPMood`` wraps a handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5}
+FP64, FP32 = 0, 1
+
+E_CODES = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "device allocation failed",
+           -4: "GP covariance matrix not positive definite", -5: "MOOD iteration cap reached",
+           -6: "time step not positive or not finite", -7: "no state set"}
+
+
+class GpmoodError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {gpmood_strerror(code)} ({code})")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+        ("bc", C.c_int * 4), ("bc_prim", (C.c_double * 4) * 4),
+        ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4),
+        ("dmr_wall_x0", C.c_double), ("dmr_xs0", C.c_double), ("dmr_xs_speed", C.c_double),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("ncascade", C.c_int), ("cascade", C.c_int * 4), ("precision", C.c_int),
+        ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
+        ("max_mood_iters", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("t", C.c_double), ("dt", C.c_double), ("nsteps", C.c_longlong),
+        ("iters", C.c_int * 3), ("nbad_first", C.c_int * 3), ("nbad_total", C.c_int * 3),
+        ("nfog_pad", C.c_int * 3), ("status", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libgpmood.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgpmood.so not found at {path}; run build()")
+    L = C.CDLL(path)
+    p, i, d = C.c_void_p, C.c_int, C.c_double
+    L.gpmood_create.argtypes = [C.POINTER(Grid), d, i, d, C.POINTER(Options), C.POINTER(p)]
+    L.gpmood_set_stream.argtypes = [p, p]
+    L.gpmood_set_state.argtypes = [p, p, i]
+    L.gpmood_get_state.argtypes = [p, p, i]
+    L.gpmood_set_time.argtypes = [p, d]
+    L.gpmood_step.argtypes = [p, d, C.POINTER(d)]
+    L.gpmood_step_dt.argtypes = [p, d]
+    L.gpmood_run.argtypes = [p, d, d, C.POINTER(C.c_longlong)]
+    L.gpmood_flags.argtypes = [p, p, p, C.POINTER(Stats)]
+    L.gpmood_destroy.argtypes = [p]
+    L.gpmood_strerror.argtypes = [i]
+    L.gpmood_strerror.restype = C.c_char_p
+    L.gpmood_last_launches.argtypes = [p]
+    L.gpmood_profile.argtypes = [p, i]
+    L.gpmood_kernel_times.argtypes = [p, p, p]
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise GpmoodError(rc, what)
+
+
+def gpmood_strerror(code):
+    return E_CODES.get(code, "unknown error")
+
+
+def make_grid(prob):
+    g = Grid()
+    g.nx, g.ny = int(prob["nx"]), int(prob["ny"])
+    g.x0, g.x1, g.y0, g.y1 = prob["x0"], prob["x1"], prob["y0"], prob["y1"]
+    for s in range(4):
+        g.bc[s] = BC[prob["bc"][s]]
+        for k in range(4):
+            g.bc_prim[s][k] = prob["bc_prim"][s][k]
+    for k in range(4):
+        g.dmr_post[k] = prob["dmr_post"][k]
+        g.dmr_pre[k] = prob["dmr_pre"][k]
+    g.dmr_wall_x0 = prob["dmr_wall_x0"]
+    g.dmr_xs0 = prob["dmr_xs0"]
+    g.dmr_xs_speed = prob["dmr_xs_speed"]
+    return g
+
+
+def make_options(prob, precision=FP64):
+    o = Options()
+    cas = list(prob["cascade"])
+    o.ncascade = len(cas)
+    for k, r in enumerate(cas):
+        o.cascade[k] = r
+    o.precision = precision
+    o.sigma_v, o.sigma_p = prob["sigma_v"], prob["sigma_p"]
+    o.csd_off = 0 if prob["csd_on"] else 1
+    o.max_mood_iters = int(prob.get("max_iters", 64))
+    return o
+
+
+def gpmood_create(grid, gamma, R_max, ell, opts):
+    h = C.c_void_p()
+    _check(load().gpmood_create(C.byref(grid), gamma, R_max, ell, C.byref(opts), C.byref(h)),
+           "gpmood_create")
+    return h
+
+
+def _ptr_of(U):
+    """(pointer, on_device) of a contiguous float64 numpy array or CUDA tensor."""
+    if hasattr(U, "data_ptr") and getattr(U, "is_cuda", False):
+        return C.c_void_p(U.data_ptr()), 1
+    return U.ctypes.data_as(C.c_void_p), 0
+
+
+def gpmood_set_state(h, U):
+    p, dev = _ptr_of(U)
+    _check(load().gpmood_set_state(h, p, dev), "gpmood_set_state")
+
+
+def gpmood_set_time(h, t):
+    _check(load().gpmood_set_time(h, t), "gpmood_set_time")
+
+
+def gpmood_get_state(h, out):
+    p, dev = _ptr_of(out)
+    _check(load().gpmood_get_state(h, p, dev), "gpmood_get_state")
+    return out
+
+
+def gpmood_step(h, cfl, want_dt=False):
+    if want_dt:
+        dt = C.c_double(0.0)
+        _check(load().gpmood_step(h, cfl, C.byref(dt)), "gpmood_step")
+        return dt.value
+    _check(load().gpmood_step(h, cfl, None), "gpmood_step")
+    return None
+
+
+def gpmood_step_dt(h, dt):
+    _check(load().gpmood_step_dt(h, dt), "gpmood_step_dt")
+
+
+def gpmood_run(h, t_end, cfl):
+    n = C.c_longlong(0)
+    _check(load().gpmood_run(h, t_end, cfl, C.byref(n)), "gpmood_run")
+    return n.value
+
+
+def gpmood_flags(h, nx, ny, maps=True):
+    st = Stats()
+    if maps:
+        order = np.zeros((3, ny, nx), dtype=np.uint8)
+        first = np.zeros((3, ny, nx), dtype=np.uint8)
+        _check(load().gpmood_flags(h, order.ctypes.data_as(C.c_void_p),
+                                   first.ctypes.data_as(C.c_void_p), C.byref(st)), "gpmood_flags")
+    else:
+        order = first = None
+        _check(load().gpmood_flags(h, None, None, C.byref(st)), "gpmood_flags")
+    stats = dict(t=st.t, dt=st.dt, nsteps=st.nsteps, iters=list(st.iters),
+                 nbad_first=list(st.nbad_first), nbad_total=list(st.nbad_total),
+                 nfog_pad=list(st.nfog_pad), status=st.status)
+    return order, first, stats
+
+
+def gpmood_destroy(h):
+    if h:
+        load().gpmood_destroy(h)
+
+
+def gpmood_set_stream(h, stream_ptr):
+    _check(load().gpmood_set_stream(h, C.c_void_p(stream_ptr)), "gpmood_set_stream")
+
+
+def gpmood_last_launches(h):
+    return load().gpmood_last_launches(h)
+
+
+KERNEL_CLASSES = ("dt", "ghost", "faces_x", "faces_y", "update", "mood")
+
+
+def gpmood_profile(h, enable):
+    _check(load().gpmood_profile(h, 1 if enable else 0), "gpmood_profile")
+
+
+def gpmood_kernel_times(h):
+    ms = np.zeros(len(KERNEL_CLASSES))
+    n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+    _check(load().gpmood_kernel_times(h, ms.ctypes.data_as(C.c_void_p),
+                                      n.ctypes.data_as(C.c_void_p)), "gpmood_kernel_times")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+class GPMood:
+    """One GP-MOOD problem on the GPU: a handle of the C ABI."""
+
+    def __init__(self, prob, precision="fp64"):
+        self.prob = prob
+        self.nx, self.ny = int(prob["nx"]), int(prob["ny"])
+        self.precision = FP32 if precision in ("fp32", FP32) else FP64
+        cas = list(prob["cascade"])
+        self.h = gpmood_create(make_grid(prob), prob["gamma"], cas[0], prob["ell"],
+                               make_options(prob, self.precision))
+
+    def close(self):
+        if getattr(self, "h", None):
+            gpmood_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        gpmood_set_stream(self.h, stream_ptr)
+
+    def set_state(self, U):
+        if not (hasattr(U, "data_ptr") and getattr(U, "is_cuda", False)):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            assert U.shape == (4, self.ny, self.nx), U.shape
+        gpmood_set_state(self.h, U)
+
+    def set_time(self, t):
+        gpmood_set_time(self.h, t)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((4, self.ny, self.nx))
+        return gpmood_get_state(self.h, out)
+
+    def step(self, cfl=None, want_dt=False):
+        return gpmood_step(self.h, self.prob["cfl"] if cfl is None else cfl, want_dt)
+
+    def step_dt(self, dt):
+        gpmood_step_dt(self.h, dt)
+
+    def run(self, t_end, cfl=None):
+        return gpmood_run(self.h, t_end, self.prob["cfl"] if cfl is None else cfl)
+
+    def flags(self, maps=True):
+        return gpmood_flags(self.h, self.nx, self.ny, maps)
+
+    def last_launches(self):
+        return gpmood_last_launches(self.h)
+
+    def profile(self, enable=True):
+        gpmood_profile(self.h, enable)
+
+    def kernel_times(self):
+        return gpmood_kernel_times(self.h)

@@ -1,0 +1,30 @@
+/* gp_weights.h -- host-side binary128 GP weight solve (see gp_weights.c). */
+#ifndef GPMOOD_GP_WEIGHTS_H
+#define GPMOOD_GP_WEIGHTS_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* prediction vectors of one radius: z[face][k][m], face 0 = east, 1 = north,
+   k over the q Gauss points g[k] (ordered +1/2 .. -1/2), m over the stencil
+   (da[m], db[m]) */
+typedef struct {
+  int n, q;
+  int da[25], db[25];
+  double g[4], w[4];
+  double z[2][4][25];
+} gpw_radius;
+
+int gpw_stencil(int R, int* da, int* db);
+void gpw_gauss(int q, double* g, double* w);
+/* returns 0, -1 for a bad radius, -2 if C is not positive definite */
+int gpw_solve(int R, double dx, double dy, double ell, gpw_radius* out);
+/* App. B second-derivative weights on the R = 1 stencil, physical units;
+   returns the stencil size (5) or -2 */
+int gpw_second_derivative(double dx, double dy, double ell, int* da, int* db, double* wxx,
+                          double* wyy);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

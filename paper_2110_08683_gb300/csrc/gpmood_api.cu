@@ -1,0 +1,635 @@
+// gpmood_api.cu -- the C ABI (include/gpmood.h): handle, buffers, weights,
+// and the host driver of one SSP-RK3 step with the MOOD loop per stage.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/gpmood.h"
+#include "common_kernels.cuh"
+#include "gp_weights.h"
+#include "gpmood_launch.h"
+
+using namespace gpm;
+
+struct gpmood_s {
+  Grid g;
+  Cascade cas;
+  Detect det;
+  int precision;
+  int max_iters;
+  cudaStream_t stream;
+  double* U[3];
+  void* Fx;
+  void* Fy;
+  uint8_t* cad;
+  uint8_t* ord;    // [3][nc]
+  uint8_t* first;  // [3][nc]
+  uint32_t* stamp;
+  int* queue[2];
+  Scalars* sc;     // device
+  Scalars* hsc;    // pinned host mirror
+  ParityW<double> pw64;
+  ParityW<float> pw32;
+  DirectW<double> dw64;
+  DirectW<float> dw32;
+  int cur;         // buffer holding U^n
+  int has_state;
+  uint32_t stamp_ctr;
+  int launches;
+  int last_status;
+  // optional per-class event timing
+  int prof_on;
+  int npend;
+  int pend_cls[64];
+  cudaEvent_t ev[128];
+  double prof_ms[GPMOOD_NKCLASS];
+  long long prof_n[GPMOOD_NKCLASS];
+};
+
+namespace {
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+void prim_to_cons(const double* P, double gam, double* U) {
+  U[0] = P[0];
+  U[1] = P[0] * P[1];
+  U[2] = P[0] * P[2];
+  U[3] = P[3] / (gam - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2]);
+}
+
+// index of offset (a,b) in the stencil order of gp_weights.c
+int sidx(const gpw_radius& w, int a, int b) {
+  for (int m = 0; m < w.n; ++m)
+    if (w.da[m] == a && w.db[m] == b) return m;
+  return -1;
+}
+
+template <class Real>
+void fill_weights(const gpw_radius* wr, int top, const double* d2x, const double* d2y,
+                  ParityW<Real>& P, DirectW<Real>& D) {
+  memset(&P, 0, sizeof(P));
+  memset(&D, 0, sizeof(D));
+  D.top = top;
+  D.w[0][0] = Real(1);
+  for (int m = 0; m < 5; ++m) {
+    D.d2x[m] = (Real)d2x[m];
+    D.d2y[m] = (Real)d2y[m];
+  }
+  for (int R = 1; R <= 3; ++R) {
+    const gpw_radius& w = wr[R];
+    if (w.n == 0) continue;
+    const int q = w.q;
+    for (int k = 0; k < q; ++k) D.w[R][k] = (Real)w.w[k];
+    // direct weights from the east / north solves at g >= 0 by the mirrors
+    for (int k = 0; k < q; ++k) {
+      const int kp = k < (q + 1) / 2 ? k : q - 1 - k;  // the +g point of the pair
+      const bool neg = k != kp;
+      for (int m = 0; m < w.n; ++m) {
+        int a = w.da[m], b = w.db[m];
+        // E at g: z_E(g)(a,b); E at -g: z_E(g)(a,-b); W: x-mirror of E
+        D.z[R][0][k][m] = (Real)w.z[0][kp][sidx(w, a, neg ? -b : b)];
+        D.z[R][1][k][m] = (Real)w.z[0][kp][sidx(w, -a, neg ? -b : b)];
+        // N at g: z_N(g)(a,b); N at -g: z_N(g)(-a,b); S: y-mirror of N
+        D.z[R][2][k][m] = (Real)w.z[1][kp][sidx(w, neg ? -a : a, b)];
+        D.z[R][3][k][m] = (Real)w.z[1][kp][sidx(w, neg ? -a : a, -b)];
+      }
+    }
+  }
+  // parity coefficients of the top radius
+  const int R = top;
+  if (R == 0) {
+    P.cx[0][0] = P.cy[0][0] = Real(1);
+    P.w[0] = Real(1);
+    return;
+  }
+  const gpw_radius& w = wr[R];
+  const int q = w.q, ns = (q + 1) / 2;
+  for (int k = 0; k < q; ++k) P.w[k] = (Real)w.w[k];
+  for (int kk = 0; kk < ns; ++kk) {
+    const bool middle = (q & 1) && kk == q / 2;
+    for (int c = 0; c < stencil_n(R); ++c) {
+      Comp cm = comp_at(R, c);
+      double ex = 0.0, ny = 0.0;
+      int cnt = 0;
+      for (int sa = 1; sa >= -1; sa -= 2) {
+        if (cm.a == 0 && sa < 0) continue;
+        for (int sb = 1; sb >= -1; sb -= 2) {
+          if (cm.b == 0 && sb < 0) continue;
+          double chi = (cm.px && sa < 0 ? -1.0 : 1.0) * (cm.py && sb < 0 ? -1.0 : 1.0);
+          ex += chi * w.z[0][kk][sidx(w, sa * cm.a, sb * cm.b)];
+          ny += chi * w.z[1][kk][sidx(w, sa * cm.a, sb * cm.b)];
+          ++cnt;
+        }
+      }
+      ex /= cnt;
+      ny /= cnt;
+      // at g = 0 the odd components across the face vanish exactly
+      if (middle && cm.py) ex = 0.0;
+      if (middle && cm.px) ny = 0.0;
+      P.cx[kk][c] = (Real)ex;
+      P.cy[kk][c] = (Real)ny;
+    }
+  }
+}
+
+int set_err(gpmood_t h, int code) {
+  if (h) h->last_status = code;
+  return code;
+}
+
+#define CK(call)                                \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return set_err(h, GPMOOD_E_CUDA); \
+  } while (0)
+
+void free_all(gpmood_t h) {
+  for (int k = 0; k < 128; ++k)
+    if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+  for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
+  cudaFree(h->Fx);
+  cudaFree(h->Fy);
+  cudaFree(h->cad);
+  cudaFree(h->ord);
+  cudaFree(h->first);
+  cudaFree(h->stamp);
+  cudaFree(h->queue[0]);
+  cudaFree(h->queue[1]);
+  cudaFree(h->sc);
+  if (h->hsc) cudaFreeHost(h->hsc);
+}
+
+template <class Real>
+StageArgs<Real> stage_args(gpmood_t h, int s, int ia, int ix, int io) {
+  StageArgs<Real> A;
+  const size_t nc = (size_t)h->g.nx * h->g.ny;
+  A.X = h->U[ix];
+  A.U0 = h->U[ia];
+  A.out = h->U[io];
+  A.Fx = (Real*)h->Fx;
+  A.Fy = (Real*)h->Fy;
+  A.cad = h->cad;
+  A.ord = h->ord + s * nc;
+  A.first = h->first + s * nc;
+  A.queue = h->queue[0];
+  A.qcount = &h->sc->count[0];
+  A.sc = h->sc;
+  A.scw = h->sc;
+  A.stage = s;
+  return A;
+}
+
+// event timing: resolve the recorded pairs once the stream has drained
+void prof_resolve(gpmood_t h) {
+  for (int k = 0; k < h->npend; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) == cudaSuccess)
+      h->prof_ms[h->pend_cls[k]] += ms;
+  }
+  h->npend = 0;
+}
+
+void prof_begin(gpmood_t h) {
+  if (h->prof_on) cudaEventRecord(h->ev[2 * h->npend], h->stream);
+}
+
+void prof_end(gpmood_t h, int cls, int nlaunch) {
+  h->launches += nlaunch;
+  if (!h->prof_on) return;
+  cudaEventRecord(h->ev[2 * h->npend + 1], h->stream);
+  h->pend_cls[h->npend] = cls;
+  h->prof_n[cls] += nlaunch;
+  if (++h->npend == 64) {
+    cudaStreamSynchronize(h->stream);
+    prof_resolve(h);
+  }
+}
+
+// read the device scalars (synchronises the stream)
+int pull_scalars(gpmood_t h) {
+  CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  prof_resolve(h);
+  return 0;
+}
+
+template <class Real>
+int run_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
+              const DirectW<Real>& D) {
+  static const double tfrac[3] = {0.0, 1.0, 0.5};
+  prof_begin(h);
+  CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], h->stream));
+  prof_end(h, GPMOOD_K_GHOST, 1);
+  StageArgs<Real> A = stage_args<Real>(h, s, ia, ix, io);
+  prof_begin(h);
+  CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, h->stream));
+  prof_end(h, GPMOOD_K_FACES_X, 1);
+  prof_begin(h);
+  CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, h->stream));
+  prof_end(h, GPMOOD_K_FACES_Y, 1);
+  prof_begin(h);
+  CK(Launch<Real>::update_first(A, h->g, h->det, D, h->stream));
+  CK(launch_account(h->sc, s, 0, 1, h->stream));
+  prof_end(h, GPMOOD_K_UPDATE, 2);
+  int slot = 0, it = 0;
+  for (;;) {
+    int rc = pull_scalars(h);
+    if (rc) return rc;
+    const int n = h->hsc->count[slot];
+    if (n == 0) break;
+    if (it >= h->max_iters) return set_err(h, GPMOOD_E_MOOD_CAP);
+    ++it;
+    MoodArgs M;
+    M.queue = h->queue[slot];
+    M.qcount = &h->sc->count[slot];
+    M.next_queue = h->queue[slot ^ 1];
+    M.next_count = &h->sc->count[slot ^ 1];
+    M.stamp = h->stamp;
+    M.cur = ++h->stamp_ctr;
+    prof_begin(h);
+    CK(launch_lower(M, A.ord, h->cas, n, h->stream));
+    CK(Launch<Real>::mood_faces(A, M, h->g, D, h->cas, n, h->stream));
+    CK(Launch<Real>::mood_update(A, M, h->g, h->det, D, n, h->stream));
+    CK(launch_account(h->sc, s, slot ^ 1, 0, h->stream));
+    prof_end(h, GPMOOD_K_MOOD, 4);
+    slot ^= 1;
+  }
+  return 0;
+}
+
+int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+  if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
+  h->launches = 0;
+  const int a = h->cur, b = (a + 1) % 3, c = (a + 2) % 3;
+  prof_begin(h);
+  CK(launch_dt(h->U[a], h->g, h->sc, cfl, fixed_dt, clip, t_end, h->stream));
+  prof_end(h, GPMOOD_K_DT, fixed_dt > 0.0 ? 1 : 2);
+  const int in[3] = {a, b, c}, out[3] = {b, c, b};
+  for (int s = 0; s < 3; ++s) {
+    int rc = h->precision == GPMOOD_FP32
+                 ? run_stage<float>(h, s, a, in[s], out[s], h->pw32, h->dw32)
+                 : run_stage<double>(h, s, a, in[s], out[s], h->pw64, h->dw64);
+    if (rc) return rc;
+    if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
+  }
+  prof_begin(h);
+  CK(launch_finish(h->sc, h->stream));
+  prof_end(h, GPMOOD_K_DT, 1);
+  h->cur = b;
+  h->last_status = GPMOOD_OK;
+  return GPMOOD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers of the precision-independent kernels
+// ---------------------------------------------------------------------------
+namespace gpm {
+
+cudaError_t launch_fill(double* X, const Grid& g, const Scalars* sc, double tfrac,
+                        cudaStream_t st) {
+  long long n = (long long)g.ny * 2 * g.H + (long long)2 * g.H * (g.nx + 2 * g.H);
+  int blocks = (int)((n + 255) / 256);
+  k_fill_ghosts<<<blocks, 256, 0, st>>>(X, g, sc, tfrac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, double cfl, double fixed_dt,
+                      int clip, double t_end, cudaStream_t st) {
+  long long n = (long long)g.nx * g.ny;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (fixed_dt <= 0.0) k_dt_reduce<<<blocks, 256, 0, st>>>(X, g, sc);
+  k_dt_finalize<<<1, 32, 0, st>>>(sc, cfl, fixed_dt, clip, t_end);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(Scalars* sc, cudaStream_t st) {
+  k_finish_step<<<1, 32, 0, st>>>(sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_account(Scalars* sc, int stage, int slot, int first, cudaStream_t st) {
+  k_mood_account<<<1, 32, 0, st>>>(sc, stage, slot, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, int n,
+                         cudaStream_t st) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_mood_lower<<<blocks, 256, 0, st>>>(M, ord, C);
+  return cudaGetLastError();
+}
+
+}  // namespace gpm
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* gpmood_strerror(int code) {
+  switch (code) {
+    case GPMOOD_OK: return "ok";
+    case GPMOOD_E_INVAL: return "invalid argument";
+    case GPMOOD_E_CUDA: return "CUDA error";
+    case GPMOOD_E_OOM: return "device allocation failed";
+    case GPMOOD_E_WEIGHTS: return "GP covariance matrix not positive definite";
+    case GPMOOD_E_MOOD_CAP: return "MOOD iteration cap reached";
+    case GPMOOD_E_DT: return "time step not positive or not finite";
+    case GPMOOD_E_NOSTATE: return "no state set";
+    default: return "unknown error";
+  }
+}
+
+int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
+                  const gpmood_options* opts, gpmood_t* out) {
+  if (!out) return GPMOOD_E_INVAL;
+  *out = nullptr;
+  if (!grid || R_max < 0 || R_max > 3 || !(gamma > 1.0) || !(ell > 0.0)) return GPMOOD_E_INVAL;
+  gpmood_options o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  // cascade
+  int cascade[4], nc = 0;
+  if (o.ncascade == 0) {
+    for (int r = R_max; r >= 0; --r) cascade[nc++] = r;
+  } else {
+    if (o.ncascade < 1 || o.ncascade > 4) return GPMOOD_E_INVAL;
+    nc = o.ncascade;
+    for (int k = 0; k < nc; ++k) cascade[k] = o.cascade[k];
+    if (cascade[0] != R_max || cascade[nc - 1] != 0) return GPMOOD_E_INVAL;
+    for (int k = 0; k + 1 < nc; ++k)
+      if (!(cascade[k] > cascade[k + 1])) return GPMOOD_E_INVAL;
+  }
+  const int H = R_max + 1 > 2 ? R_max + 1 : 2;
+  const int minn = H > 3 ? H : 3;
+  if (grid->nx < minn || grid->ny < minn) return GPMOOD_E_INVAL;
+  if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0)) return GPMOOD_E_INVAL;
+  for (int s = 0; s < 4; ++s) {
+    int k = grid->bc[s];
+    if (k < 0 || k > 5) return GPMOOD_E_INVAL;
+    if (k == GPMOOD_BC_DMR_BOTTOM && s != 2) return GPMOOD_E_INVAL;
+    if (k == GPMOOD_BC_DMR_TOP && s != 3) return GPMOOD_E_INVAL;
+  }
+  if ((grid->bc[0] == 0) != (grid->bc[1] == 0)) return GPMOOD_E_INVAL;
+  if ((grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
+  if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
+
+  gpmood_t h = new (std::nothrow) gpmood_s;
+  if (!h) return GPMOOD_E_OOM;
+  memset(h, 0, sizeof(*h));
+  Grid& g = h->g;
+  g.nx = grid->nx;
+  g.ny = grid->ny;
+  g.H = H;
+  g.pitch = round_up(g.nx + 2 * H, 32);
+  g.gy = g.ny + 2 * H;
+  g.vstride = (long long)g.pitch * g.gy;
+  g.dx = (grid->x1 - grid->x0) / g.nx;
+  g.dy = (grid->y1 - grid->y0) / g.ny;
+  g.inv_dx = 1.0 / g.dx;
+  g.inv_dy = 1.0 / g.dy;
+  g.x0 = grid->x0;
+  g.y0 = grid->y0;
+  g.gamma = gamma;
+  for (int s = 0; s < 4; ++s) {
+    g.bc[s] = grid->bc[s];
+    prim_to_cons(grid->bc_prim[s], gamma, g.bcU[s]);
+  }
+  g.periodic_x = grid->bc[0] == GPMOOD_BC_PERIODIC;
+  g.periodic_y = grid->bc[2] == GPMOOD_BC_PERIODIC;
+  prim_to_cons(grid->dmr_post, gamma, g.dmr_post);
+  prim_to_cons(grid->dmr_pre, gamma, g.dmr_pre);
+  g.dmr_wall_x0 = grid->dmr_wall_x0;
+  g.dmr_xs0 = grid->dmr_xs0;
+  g.dmr_xs_speed = grid->dmr_xs_speed;
+
+  for (int r = 0; r < 4; ++r) h->cas.next[r] = h->cas.prev[r] = r;
+  for (int k = 0; k + 1 < nc; ++k) {
+    h->cas.next[cascade[k]] = cascade[k + 1];
+    h->cas.prev[cascade[k + 1]] = cascade[k];
+  }
+  h->cas.top = R_max;
+  h->det.sigma_v = o.sigma_v > 0 ? o.sigma_v : 5.0;
+  h->det.sigma_p = o.sigma_p > 0 ? o.sigma_p : 5.0;
+  h->det.csd_on = o.csd_off ? 0 : 1;
+  h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
+  h->det.delta = fmin(g.dx, g.dy);
+  h->precision = o.precision;
+  h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters : 64;
+
+  // GP weights of every radius of the cascade, binary128 -> double / float
+  gpw_radius wr[4];
+  memset(wr, 0, sizeof(wr));
+  for (int k = 0; k < nc; ++k) {
+    int R = cascade[k];
+    if (R == 0) continue;
+    if (gpw_solve(R, g.dx, g.dy, ell, &wr[R]) != 0) {
+      delete h;
+      return GPMOOD_E_WEIGHTS;
+    }
+  }
+  int da[25], db[25];
+  double d2x[25], d2y[25];
+  if (gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y) != 5) {
+    delete h;
+    return GPMOOD_E_WEIGHTS;
+  }
+  fill_weights<double>(wr, R_max, d2x, d2y, h->pw64, h->dw64);
+  fill_weights<float>(wr, R_max, d2x, d2y, h->pw32, h->dw32);
+
+  // device buffers
+  const size_t ncell = (size_t)g.nx * g.ny;
+  const size_t fsz = h->precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  bool ok = true;
+  for (int k = 0; k < 3; ++k)
+    ok = ok && cudaMalloc(&h->U[k], sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->Fx, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->Fy, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->cad, ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ord, 3 * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->first, 3 * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->stamp, sizeof(uint32_t) * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->queue[0], sizeof(int) * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->queue[1], sizeof(int) * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->sc, sizeof(Scalars)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&h->hsc, sizeof(Scalars)) == cudaSuccess;
+  if (!ok) {
+    free_all(h);
+    delete h;
+    cudaGetLastError();
+    return GPMOOD_E_OOM;
+  }
+  ok = cudaMemset(h->cad, 0, ncell) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
+       cudaMemset(h->ord, 0, 3 * ncell) == cudaSuccess &&
+       cudaMemset(h->first, 0, 3 * ncell) == cudaSuccess;
+  for (int k = 0; k < 3 && ok; ++k)
+    ok = cudaMemset(h->U[k], 0, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess;
+  if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return GPMOOD_E_CUDA;
+  }
+  for (int k = 0; k < 128; ++k)
+    if (cudaEventCreate(&h->ev[k]) != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return GPMOOD_E_CUDA;
+    }
+  h->stream = nullptr;
+  h->last_status = GPMOOD_OK;
+  *out = h;
+  return GPMOOD_OK;
+}
+
+int gpmood_set_stream(gpmood_t h, void* stream) {
+  if (!h) return GPMOOD_E_INVAL;
+  h->stream = (cudaStream_t)stream;
+  return GPMOOD_OK;
+}
+
+int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
+  if (!h || !U) return GPMOOD_E_INVAL;
+  const Grid& g = h->g;
+  h->cur = 0;
+  for (int v = 0; v < 4; ++v) {
+    double* dst = h->U[0] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
+    const double* src = U + (size_t)v * g.nx * g.ny;
+    CK(cudaMemcpy2DAsync(dst, sizeof(double) * g.pitch, src, sizeof(double) * g.nx,
+                         sizeof(double) * g.nx, g.ny,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         h->stream));
+  }
+  Scalars z;
+  memset(&z, 0, sizeof(z));
+  z.dtmin_bits = 0x7ff0000000000000ull;
+  *h->hsc = z;
+  CK(cudaMemcpyAsync(h->sc, h->hsc, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->has_state = 1;
+  return GPMOOD_OK;
+}
+
+int gpmood_set_time(gpmood_t h, double t) {
+  if (!h || !isfinite(t)) return GPMOOD_E_INVAL;
+  if (!h->has_state) return GPMOOD_E_NOSTATE;
+  CK(cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return GPMOOD_OK;
+}
+
+int gpmood_get_state(gpmood_t h, double* U, int on_device) {
+  if (!h || !U) return GPMOOD_E_INVAL;
+  if (!h->has_state) return GPMOOD_E_NOSTATE;
+  const Grid& g = h->g;
+  for (int v = 0; v < 4; ++v) {
+    const double* src = h->U[h->cur] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
+    double* dst = U + (size_t)v * g.nx * g.ny;
+    CK(cudaMemcpy2DAsync(dst, sizeof(double) * g.nx, src, sizeof(double) * g.pitch,
+                         sizeof(double) * g.nx, g.ny,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return GPMOOD_OK;
+}
+
+int gpmood_step(gpmood_t h, double cfl, double* dt_out) {
+  if (!h || !(cfl > 0.0)) return GPMOOD_E_INVAL;
+  int rc = do_step(h, cfl, 0.0, 0, 0.0);
+  if (rc) return rc;
+  if (dt_out) {
+    rc = pull_scalars(h);
+    if (rc) return rc;
+    *dt_out = h->hsc->dt;
+  }
+  return GPMOOD_OK;
+}
+
+int gpmood_step_dt(gpmood_t h, double dt) {
+  if (!h || !(dt > 0.0)) return GPMOOD_E_INVAL;
+  return do_step(h, 1.0, dt, 0, 0.0);
+}
+
+int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out) {
+  if (!h || !(cfl > 0.0)) return GPMOOD_E_INVAL;
+  if (!h->has_state) return GPMOOD_E_NOSTATE;
+  long long n = 0;
+  int rc = pull_scalars(h);
+  if (rc) return rc;
+  while (h->hsc->t < t_end * (1.0 - 1e-14)) {
+    rc = do_step(h, cfl, 0.0, 1, t_end);
+    if (rc) return rc;
+    ++n;
+    rc = pull_scalars(h);
+    if (rc) return rc;
+  }
+  if (nsteps_out) *nsteps_out = n;
+  return GPMOOD_OK;
+}
+
+int gpmood_flags(gpmood_t h, uint8_t* order_out, uint8_t* first_out, gpmood_stats* stats_out) {
+  if (!h) return GPMOOD_E_INVAL;
+  const size_t nc = (size_t)h->g.nx * h->g.ny;
+  if (order_out) CK(cudaMemcpyAsync(order_out, h->ord, 3 * nc, cudaMemcpyDeviceToHost, h->stream));
+  if (first_out) CK(cudaMemcpyAsync(first_out, h->first, 3 * nc, cudaMemcpyDeviceToHost, h->stream));
+  int rc = pull_scalars(h);
+  if (rc) return rc;
+  if (stats_out) {
+    const Scalars& s = *h->hsc;
+    stats_out->t = s.t;
+    stats_out->dt = s.dt;
+    stats_out->nsteps = s.nsteps;
+    for (int k = 0; k < 3; ++k) {
+      stats_out->iters[k] = s.iters[k];
+      stats_out->nbad_first[k] = s.nbad_first[k];
+      stats_out->nbad_total[k] = s.nbad_total[k];
+      stats_out->nfog_pad[k] = s.nfog_pad[k];
+    }
+    stats_out->status = h->last_status;
+  }
+  return GPMOOD_OK;
+}
+
+int gpmood_destroy(gpmood_t h) {
+  if (!h) return GPMOOD_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return GPMOOD_OK;
+}
+
+int gpmood_last_launches(gpmood_t h) { return h ? h->launches : 0; }
+
+int gpmood_profile(gpmood_t h, int enable) {
+  if (!h) return GPMOOD_E_INVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  prof_resolve(h);
+  h->prof_on = enable ? 1 : 0;
+  if (enable)
+    for (int k = 0; k < GPMOOD_NKCLASS; ++k) {
+      h->prof_ms[k] = 0.0;
+      h->prof_n[k] = 0;
+    }
+  return GPMOOD_OK;
+}
+
+int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
+  if (!h) return GPMOOD_E_INVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  prof_resolve(h);
+  for (int k = 0; k < GPMOOD_NKCLASS; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (launches) launches[k] = h->prof_n[k];
+  }
+  return GPMOOD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// gpmood_internal.h -- types shared by the host driver and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpm {
+
+constexpr int kNV = 4;        // conservative variables (rho, rho u, rho v, rho E)
+constexpr int kMaxN = 25;     // stencil size of the largest radius (R = 3)
+constexpr int kMaxQ = 4;      // Gauss points of the largest radius
+constexpr int kSegCells = 32; // cells per warp segment in the face kernels
+constexpr int kSegFaces = kSegCells - 1;
+constexpr int kFaceWarps = 8; // warps per face-kernel block
+
+// geometry and boundary data, passed by value to every kernel
+struct Grid {
+  int nx, ny, H;          // interior cells and ghost layers
+  int pitch, gy;          // ghosted row length (elements) and ghosted rows
+  long long vstride;      // elements per variable plane of a ghosted state
+  double dx, dy, inv_dx, inv_dy;
+  double x0, y0;
+  double gamma;
+  int bc[4];              // W, E, S, N
+  int periodic_x, periodic_y;
+  double bcU[4][4];       // conservative Dirichlet state per side
+  double dmr_post[4], dmr_pre[4];  // conservative states
+  double dmr_wall_x0, dmr_xs0, dmr_xs_speed;
+};
+
+// scalars living on the device (one per handle)
+struct Scalars {
+  double t;                     // time at the start of the current step
+  double dt;                    // current step
+  unsigned long long dtmin_bits;  // running min of dx/(|u|+c) as ordered bits
+  int err;                      // error bits (kErr*)
+  int count[2];                 // queue lengths (double buffered)
+  int iters[3], nbad_first[3], nbad_total[3], nfog_pad[3];
+  long long nsteps;
+};
+
+constexpr int kErrDt = 1;       // non-finite or non-positive time step
+constexpr int kErrCap = 2;      // MOOD iteration cap reached
+
+// parity-decomposed prediction weights of one radius for the first pass
+// (see the stencil-symmetry note in the face kernels)
+template <class Real>
+struct ParityW {
+  Real cx[2][kMaxN];  // x faces (east-face weights), per g slot, per component
+  Real cy[2][kMaxN];  // y faces (north-face weights)
+  Real w[kMaxQ];      // Gauss weights of the rule of this radius
+};
+
+// full prediction weights z[R][face][g][m] (face E, W, N, S), for the MOOD
+// recompute at any radius, stencil order: b = -R..R, a = -R..R, |a|+|b| <= R
+template <class Real>
+struct DirectW {
+  Real z[4][4][kMaxQ][kMaxN];
+  Real w[4][kMaxQ];     // Gauss weights per radius (index 0: FOG, one point)
+  Real d2x[5], d2y[5];  // App. B second-derivative weights on the R=1 stencil
+  int top;
+};
+
+// the cascade of radii: next lower and next higher level of each radius
+struct Cascade {
+  int next[4];
+  int prev[4];
+  int top;
+};
+
+struct Detect {
+  double sigma_v, sigma_p;
+  int csd_on;
+  double plateau_thr;   // min(dx^3, dy^3)
+  double delta;         // min(dx, dy)
+};
+
+template <class Real>
+struct StageArgs {
+  const double* X;   // ghosted stage input
+  const double* U0;  // ghosted U^n (combination)
+  double* out;       // ghosted stage output
+  Real* Fx;
+  Real* Fy;
+  uint8_t* cad;
+  uint8_t* ord;      // radius per cell, this stage
+  uint8_t* first;    // first-pass troubled map, this stage
+  int* queue;        // troubled cells (first pass output)
+  int* qcount;
+  const Scalars* sc;
+  Scalars* scw;
+  int stage;
+};
+
+struct MoodArgs {
+  const int* queue;   // cells troubled in the previous pass
+  const int* qcount;
+  int* next_queue;
+  int* next_count;
+  uint32_t* stamp;    // stamp[c] == cur: c is in the current queue
+  uint32_t cur;
+};
+
+}  // namespace gpm

@@ -1,0 +1,728 @@
+// gpmood_kernels.cuh -- CUDA kernels of the GP-MOOD stage (sm_103a).
+//
+// One RK stage (Sec. 4, Steps 3-10) runs as
+//   fill_ghosts -> x_faces -> y_faces -> update_first    (first pass, all cells)
+//   [mood_lower -> mood_faces -> mood_update]*            (troubled cells only)
+// x_faces / y_faces reconstruct the pointwise Riemann states of eq.
+// gp_reconstructor at the Gauss points of Table QR, apply face-state CAD
+// (Sec. 3.3.1), solve HLLC and store the face-averaged flux of eq. fvm_F.
+// update_first forms the candidate of eq. fvm_discrete, runs Steps 4-9,
+// writes the SSP-RK3 combination (eq. rk3) and appends troubled cells to a
+// queue with one atomic per warp.  The MOOD kernels lower the order of queued
+// cells by one cascade level, recompute the faces whose EDP1 order changed
+// (Sec. 3.6) and re-update + re-detect the queued cells and their face
+// neighbours.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gpmood_internal.h"
+
+namespace gpm {
+
+// ---------------------------------------------------------------------------
+// indexing
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long gidx(const Grid& g, int v, int i, int j) {
+  return (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
+}
+// x-face i (0..nx) of row j: between cells i-1 and i
+__device__ __forceinline__ long long fxidx(const Grid& g, int v, int i, int j) {
+  return ((long long)v * g.ny + j) * (g.nx + 1) + i;
+}
+// y-face j (0..ny) of column i: between cells j-1 and j
+__device__ __forceinline__ long long fyidx(const Grid& g, int v, int i, int j) {
+  return ((long long)v * (g.ny + 1) + j) * g.nx + i;
+}
+__device__ __forceinline__ int cidx(const Grid& g, int i, int j) { return j * g.nx + i; }
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// stencil algebra at compile time.
+// The blocky diamond |a|+|b| <= R is invariant under x -> -x and y -> -y, and
+// so is the SE kernel; hence the west-face weights are the x-mirror of the
+// east-face ones, the point -g the mirror of +g, and the same for north /
+// south.  Grouping the stencil into mirror orbits {(+-a, +-b)} and using the
+// even/odd combinations of each orbit ("parity sums") turns the 2q face
+// states of one axis into q dot products of length N plus butterflies,
+// instead of 2q dot products.  The parity sums of one cell are shared by all
+// four faces.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int stencil_n(int R) { return 2 * R * R + 2 * R + 1; }
+__host__ __device__ constexpr int rule_q(int R) { return R == 0 ? 1 : R + 1; }
+
+struct Comp {
+  int a, b, px, py;
+};
+
+// k-th parity component: reps (a,b) with a,b >= 0, a+b <= R in order b-major,
+// and for each rep the types ee, oe (a>0), eo (b>0), oo (a,b>0)
+__host__ __device__ constexpr Comp comp_at(int R, int k) {
+  int n = 0;
+  for (int b = 0; b <= R; ++b)
+    for (int a = 0; a + b <= R; ++a) {
+      if (n == k) return Comp{a, b, 0, 0};
+      ++n;
+      if (a > 0) {
+        if (n == k) return Comp{a, b, 1, 0};
+        ++n;
+      }
+      if (b > 0) {
+        if (n == k) return Comp{a, b, 0, 1};
+        ++n;
+      }
+      if (a > 0 && b > 0) {
+        if (n == k) return Comp{a, b, 1, 1};
+        ++n;
+      }
+    }
+  return Comp{0, 0, 0, 0};
+}
+
+// parity sums of one variable around a cell; ld(a, b) loads the cell (i+a, j+b)
+template <int R, class Real, class Load>
+__device__ __forceinline__ void parity_sums(const Load& ld, Real* s) {
+  int k = 0;
+#pragma unroll
+  for (int b = 0; b <= R; ++b) {
+#pragma unroll
+    for (int a = 0; a + b <= R; ++a) {
+      if (a == 0 && b == 0) {
+        s[k++] = ld(0, 0);
+      } else if (b == 0) {
+        Real p = ld(a, 0), m = ld(-a, 0);
+        s[k++] = p + m;
+        s[k++] = p - m;
+      } else if (a == 0) {
+        Real p = ld(0, b), m = ld(0, -b);
+        s[k++] = p + m;
+        s[k++] = p - m;
+      } else {
+        Real q1 = ld(a, b), q2 = ld(-a, b), q3 = ld(a, -b), q4 = ld(-a, -b);
+        Real p1 = q1 + q2, m1 = q1 - q2, p2 = q3 + q4, m2 = q3 - q4;
+        s[k++] = p1 + p2;  // ee
+        s[k++] = m1 + m2;  // oe
+        s[k++] = p1 - p2;  // eo
+        s[k++] = m1 - m2;  // oo
+      }
+    }
+  }
+}
+
+// T[px][py] = sum over components of that parity of c[k] s[k]
+template <int R, class Real>
+__device__ __forceinline__ void parity_dot(const Real* c, const Real* s, Real T[2][2]) {
+  T[0][0] = T[0][1] = T[1][0] = T[1][1] = Real(0);
+#pragma unroll
+  for (int k = 0; k < stencil_n(R); ++k) {
+    const Comp cm = comp_at(R, k);
+    T[cm.px][cm.py] = fma(c[k], s[k], T[cm.px][cm.py]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Euler equations (eq. euler_eqn) and HLLC (Toro et al. 1994) in Real
+// ---------------------------------------------------------------------------
+template <class Real>
+__device__ __forceinline__ Real pressure_of(const Real* U, Real gm1) {
+  Real ir = Real(1) / U[0];
+  return gm1 * (U[3] - Real(0.5) * (U[1] * U[1] + U[2] * U[2]) * ir);
+}
+
+template <class Real>
+__device__ __forceinline__ bool finite_r(Real x) {
+  return isfinite(x);
+}
+
+// x-direction HLLC flux; pL/pR return the pressures of the two states so the
+// caller can run face-state CAD without another EoS evaluation.
+// wave speeds S_L = min(uL-cL, uR-cR), S_R = max(uL+cL, uR+cR); the star
+// state is taken on the side of the contact speed S*.
+template <class Real>
+__device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam, Real* F,
+                                       Real& pL, Real& pR) {
+  const Real gm1 = gam - Real(1);
+  Real rL = UL[0], rR = UR[0];
+  Real irL = Real(1) / rL, irR = Real(1) / rR;
+  Real uL = UL[1] * irL, vL = UL[2] * irL;
+  Real uR = UR[1] * irR, vR = UR[2] * irR;
+  pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
+  pR = gm1 * (UR[3] - Real(0.5) * (UR[1] * uR + UR[2] * vR));
+  Real cL = sqrt(gam * pL * irL), cR = sqrt(gam * pR * irR);
+  Real aL = uL - cL, bL = uR - cR;
+  Real SL = aL < bL ? aL : bL;
+  Real aR = uL + cL, bR = uR + cR;
+  Real SR = aR > bR ? aR : bR;
+  Real dL = SL - uL, dR = SR - uR;
+  Real num = pR - pL + rL * uL * dL - rR * uR * dR;
+  Real den = rL * dL - rR * dR;
+  Real Ss = num / den;
+  bool left = Ss >= Real(0);
+  Real FL[4] = {rL * uL, rL * uL * uL + pL, rL * uL * vL, uL * (UL[3] + pL)};
+  Real FR[4] = {rR * uR, rR * uR * uR + pR, rR * uR * vR, uR * (UR[3] + pR)};
+  // star state on side K of the contact
+  Real rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR;
+  Real EK = left ? UL[3] : UR[3], pK = left ? pL : pR, SK = left ? SL : SR;
+  Real irK = left ? irL : irR, dK = left ? dL : dR;
+  Real fK = rK * dK / (SK - Ss);
+  Real eK = EK * irK + (Ss - uK) * (Ss + pK * irK / dK);
+  Real UKs[4] = {fK, fK * Ss, fK * vK, fK * eK};
+  Real Fs[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    Real FK = left ? FL[v] : FR[v];
+    Real UK = left ? UL[v] : UR[v];
+    Fs[v] = FK + SK * (UKs[v] - UK);
+  }
+  bool useL = SL >= Real(0);
+  bool useS = left || (SR > Real(0));
+#pragma unroll
+  for (int v = 0; v < 4; ++v) F[v] = useL ? FL[v] : (useS ? Fs[v] : FR[v]);
+}
+
+// ---------------------------------------------------------------------------
+// ghost cells: one kernel over all ghost cells.  The x-ghosts of interior rows
+// are set from the W/E rule; the y-ghost rows (corners included) from the S/N
+// rule applied to the (possibly x-ghost) cell they copy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_cell(const double* X, const Grid& g, int i, int j,
+                                          double* S) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) S[v] = X[gidx(g, v, i, j)];
+}
+
+// value of the x-ghost (i outside [0,nx)) of interior row j
+__device__ __forceinline__ void xghost(const double* X, const Grid& g, int i, int j, double* S) {
+  int side = i < 0 ? 0 : 1;
+  int k = i < 0 ? -i : i - g.nx + 1;  // ghost layer 1..H
+  int kind = g.bc[side];
+  if (kind == 3) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) S[v] = g.bcU[side][v];
+    return;
+  }
+  int src;
+  if (kind == 0) src = wrapi(i, g.nx);
+  else if (kind == 2) src = side == 0 ? k - 1 : g.nx - k;
+  else src = side == 0 ? 0 : g.nx - 1;
+  load_cell(X, g, src, j, S);
+  if (kind == 2) S[1] = -S[1];
+}
+
+__device__ __forceinline__ void column_cell(const double* X, const Grid& g, int i, int j,
+                                            double* S) {
+  if (i < 0 || i >= g.nx) xghost(X, g, i, j, S);
+  else load_cell(X, g, i, j, S);
+}
+
+// ---------------------------------------------------------------------------
+// time step: min over cells of min(dx/(|u|+c), dy/(|v|+c)), per-direction
+// CFL form; positive doubles order like their bit patterns
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// face-state CAD flag on a possibly-ghost cell
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void flag_cad(uint8_t* cad, const Grid& g, int i, int j) {
+  if (i < 0 || i >= g.nx) {
+    if (!g.periodic_x) return;
+    i = wrapi(i, g.nx);
+  }
+  if (j < 0 || j >= g.ny) {
+    if (!g.periodic_y) return;
+    j = wrapi(j, g.ny);
+  }
+  cad[cidx(g, i, j)] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// first-pass faces at the top radius R.  One warp covers 32 consecutive
+// cells of a row (x_faces) or a column (y_faces) and produces the 31 faces
+// between them; the left/lower states come from the neighbouring lane.
+// ---------------------------------------------------------------------------
+template <int R, class Real, int DIR>
+__global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
+                                               const __grid_constant__ ParityW<Real> W) {
+  constexpr int N = stencil_n(R);
+  constexpr int Q = rule_q(R);
+  constexpr int NS = (Q + 1) / 2;
+  const int lane = threadIdx.x;
+  // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
+  int i, j, nlen;
+  if (DIR == 0) {
+    j = blockIdx.y * kFaceWarps + threadIdx.y;
+    i = blockIdx.x * kSegFaces - 1 + lane;
+    if (j >= g.ny) return;
+    nlen = g.nx;
+  } else {
+    i = blockIdx.x * kFaceWarps + threadIdx.y;
+    j = blockIdx.y * kSegFaces - 1 + lane;
+    if (i >= g.nx) return;
+    nlen = g.ny;
+  }
+  const int pos = DIR == 0 ? i : j;  // position along the sweep, -1 .. nlen
+  const bool live = pos <= nlen;
+  // states on the two faces of this cell across the sweep direction:
+  // P = +1/2 side (east / north), M = -1/2 side (west / south)
+  Real SP[Q][4], SM[Q][4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    Real s[N];
+    if (live) {
+      const double* Xv = A.X + (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
+      const int pitch = g.pitch;
+      auto ld = [&](int a, int b) -> Real { return (Real)__ldg(Xv + b * pitch + a); };
+      parity_sums<R, Real>(ld, s);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) s[k] = Real(0);
+    }
+#pragma unroll
+    for (int kk = 0; kk < NS; ++kk) {
+      Real T[2][2];
+      parity_dot<R, Real>(DIR == 0 ? W.cx[kk] : W.cy[kk], s, T);
+      const bool middle = (Q & 1) && kk == Q / 2;
+      if (DIR == 0) {
+        // east / west at +g and -g
+        if (middle) {
+          SP[kk][v] = T[0][0] + T[1][0];
+          SM[kk][v] = T[0][0] - T[1][0];
+        } else {
+          Real e = T[0][0] + T[0][1], o = T[1][0] + T[1][1];
+          Real e2 = T[0][0] - T[0][1], o2 = T[1][0] - T[1][1];
+          SP[kk][v] = e + o;           // E(+g)
+          SM[kk][v] = e - o;           // W(+g)
+          SP[Q - 1 - kk][v] = e2 + o2; // E(-g)
+          SM[Q - 1 - kk][v] = e2 - o2; // W(-g)
+        }
+      } else {
+        // north / south at +g and -g
+        if (middle) {
+          SP[kk][v] = T[0][0] + T[0][1];
+          SM[kk][v] = T[0][0] - T[0][1];
+        } else {
+          Real e = T[0][0] + T[1][0], o = T[0][1] + T[1][1];
+          Real e2 = T[0][0] - T[1][0], o2 = T[0][1] - T[1][1];
+          SP[kk][v] = e + o;           // N(+g)
+          SM[kk][v] = e - o;           // S(+g)
+          SP[Q - 1 - kk][v] = e2 + o2; // N(-g)
+          SM[Q - 1 - kk][v] = e2 - o2; // S(-g)
+        }
+      }
+    }
+  }
+  // left/lower state of the face between this cell and the previous one
+  Real SL[Q][4];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) SL[q][v] = __shfl_up_sync(0xffffffffu, SP[q][v], 1);
+  // face index = pos (between pos-1 and pos)
+  if (lane == 0 || pos < 0 || pos > nlen) return;
+  const Real gam = (Real)g.gamma;
+  Real F[4] = {0, 0, 0, 0};
+  bool badL = false, badR = false;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    Real f[4], pl, pr;
+    if (DIR == 0) {
+      hllc_x<Real>(SL[q], SM[q], gam, f, pl, pr);
+    } else {
+      Real a[4] = {SL[q][0], SL[q][2], SL[q][1], SL[q][3]};
+      Real b[4] = {SM[q][0], SM[q][2], SM[q][1], SM[q][3]};
+      Real h[4];
+      hllc_x<Real>(a, b, gam, h, pl, pr);
+      f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
+    }
+    badL |= !(finite_r(SL[q][0]) && finite_r(pl));
+    badR |= !(finite_r(SM[q][0]) && finite_r(pr));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = fma(W.w[q], f[v], F[v]);
+  }
+  if (DIR == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, i, j)] = F[v];
+    if (badL) flag_cad(A.cad, g, i - 1, j);
+    if (badR) flag_cad(A.cad, g, i, j);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, i, j)] = F[v];
+    if (badL) flag_cad(A.cad, g, i, j - 1);
+    if (badR) flag_cad(A.cad, g, i, j);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// detection, Steps 4-9 (eqs. CAD, PAD, divV, gradP, plateau, DMP_RK,
+// u2_curvature, u2_a, u2_b) on the candidate Y of cell (i,j) with the ghosted
+// stage input X.  Returns true for a troubled cell.
+// ---------------------------------------------------------------------------
+template <class Real>
+__device__ __forceinline__ Real xload(const double* X, const Grid& g, int v, int i, int j) {
+  return (Real)__ldg(X + gidx(g, v, i, j));
+}
+
+template <class Real>
+__device__ bool troubled(const double* X, const Grid& g, const Detect& D, const Real* d2x,
+                         const Real* d2y, int i, int j, const double* Yd) {
+  const Real gm1 = (Real)(g.gamma - 1.0);
+  Real Y[4] = {(Real)Yd[0], (Real)Yd[1], (Real)Yd[2], (Real)Yd[3]};
+  Real rho = Y[0];
+  Real p = gm1 * (Y[3] - Real(0.5) * (Y[1] * Y[1] + Y[2] * Y[2]) / Y[0]);
+  if (!finite_r(rho) || !finite_r(p)) return true;   // Step 4, CAD
+  if (!(rho > Real(0)) || !(p > Real(0))) return true; // Step 5, PAD
+  if (D.csd_on) {                                      // Step 6, CSD
+    Real rE = xload<Real>(X, g, 0, i + 1, j), rW = xload<Real>(X, g, 0, i - 1, j);
+    Real rN = xload<Real>(X, g, 0, i, j + 1), rS = xload<Real>(X, g, 0, i, j - 1);
+    Real mxE = xload<Real>(X, g, 1, i + 1, j), mxW = xload<Real>(X, g, 1, i - 1, j);
+    Real myE = xload<Real>(X, g, 2, i + 1, j), myW = xload<Real>(X, g, 2, i - 1, j);
+    Real mxN = xload<Real>(X, g, 1, i, j + 1), mxS = xload<Real>(X, g, 1, i, j - 1);
+    Real myN = xload<Real>(X, g, 2, i, j + 1), myS = xload<Real>(X, g, 2, i, j - 1);
+    Real eE = xload<Real>(X, g, 3, i + 1, j), eW = xload<Real>(X, g, 3, i - 1, j);
+    Real eN = xload<Real>(X, g, 3, i, j + 1), eS = xload<Real>(X, g, 3, i, j - 1);
+    Real uE = mxE / rE, uW = mxW / rW, vN = myN / rN, vS = myS / rS;
+    Real pE = gm1 * (eE - Real(0.5) * (mxE * mxE + myE * myE) / rE);
+    Real pW = gm1 * (eW - Real(0.5) * (mxW * mxW + myW * myW) / rW);
+    Real pN = gm1 * (eN - Real(0.5) * (mxN * mxN + myN * myN) / rN);
+    Real pS = gm1 * (eS - Real(0.5) * (mxS * mxS + myS * myS) / rS);
+    const Real dx = (Real)g.dx, dy = (Real)g.dy;
+    Real divV = (uE - uW) / (Real(2) * dx) + (vN - vS) / (Real(2) * dy);
+    Real mx_ = pE < pW ? pE : pW, my_ = pN < pS ? pN : pS;
+    Real gradP = fabs(pE - pW) / (Real(2) * dx * mx_) + fabs(pN - pS) / (Real(2) * dy * my_);
+    if (divV >= -(Real)D.sigma_v && gradP <= (Real)D.sigma_p) return false;
+  }
+  Real r0 = xload<Real>(X, g, 0, i, j);
+  Real rmin = r0, rmax = r0;
+  const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, 1, -1};
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    Real r = xload<Real>(X, g, 0, i + di[m], j + dj[m]);
+    rmin = r < rmin ? r : rmin;
+    rmax = r > rmax ? r : rmax;
+  }
+  if (rmax - rmin < (Real)D.plateau_thr) return false;  // Step 7, plateau
+  if (rmin <= rho && rho <= rmax) return false;          // Step 8, DMP
+  // Step 9, u2 with the App. B second-derivative weights (R=1 stencil in
+  // the order b=-1: (0,-1); b=0: (-1,0),(0,0),(1,0); b=1: (0,1))
+  const int ci[5] = {0, -1, 1, 0, 0}, cj[5] = {0, 0, 0, 1, -1};
+  const Real delta = (Real)D.delta;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const Real* w = d == 0 ? d2x : d2y;
+    Real cmin = Real(0), cmax = Real(0);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      int ii = i + ci[m], jj = j + cj[m];
+      Real k = w[0] * xload<Real>(X, g, 0, ii, jj - 1) + w[1] * xload<Real>(X, g, 0, ii - 1, jj) +
+               w[2] * xload<Real>(X, g, 0, ii, jj) + w[3] * xload<Real>(X, g, 0, ii + 1, jj) +
+               w[4] * xload<Real>(X, g, 0, ii, jj + 1);
+      if (m == 0) {
+        cmin = k;
+        cmax = k;
+      } else {
+        cmin = k < cmin ? k : cmin;
+        cmax = k > cmax ? k : cmax;
+      }
+    }
+    bool same = cmin * cmax > -delta;
+    Real acmax = fabs(cmax), acmin = fabs(cmin);
+    bool ua = same && (acmax > acmin ? acmax : acmin) < delta;
+    // |Cmin|/|Cmax| >= 1/2 written without the division; equal for every
+    // non-NaN input once (a) is taken into account
+    bool ub = same && acmin >= Real(0.5) * acmax;
+    if (!(ua || ub)) return true;
+  }
+  return false;
+}
+
+// candidate of eq. fvm_discrete and the SSP-RK3 combination (eq. rk3) of cell (i,j)
+template <class Real>
+__device__ __forceinline__ void candidate(const StageArgs<Real>& A, const Grid& g, int i, int j,
+                                          double dt, double* Y) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double fe = (double)A.Fx[fxidx(g, v, i + 1, j)], fw = (double)A.Fx[fxidx(g, v, i, j)];
+    double gn = (double)A.Fy[fyidx(g, v, i, j + 1)], gs = (double)A.Fy[fyidx(g, v, i, j)];
+    Y[v] = A.X[gidx(g, v, i, j)] - dt * ((fe - fw) * g.inv_dx + (gn - gs) * g.inv_dy);
+  }
+}
+
+template <class Real>
+__device__ __forceinline__ void combine_store(const StageArgs<Real>& A, const Grid& g, int i,
+                                              int j, const double* Y) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    long long k = gidx(g, v, i, j);
+    double o;
+    if (A.stage == 0) o = Y[v];
+    else if (A.stage == 1) o = 0.25 * (3.0 * A.U0[k] + Y[v]);
+    else o = (A.U0[k] + 2.0 * Y[v]) / 3.0;
+    A.out[k] = o;
+  }
+}
+
+// append to a queue with one atomic per warp
+__device__ __forceinline__ void queue_push(bool flag, int cell, int* queue, int* count) {
+  unsigned act = __activemask();
+  unsigned m = __ballot_sync(act, flag);
+  if (m == 0) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(act, base, leader);
+  if (flag) queue[base + __popc(m & ((1u << lane) - 1u))] = cell;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g, Detect D,
+                                                      const __grid_constant__ DirectW<Real> Wd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool in = i < g.nx && j < g.ny;
+  bool bad = false;
+  int c = 0;
+  if (in) {
+    c = cidx(g, i, j);
+    const double dt = A.sc->dt;
+    double Y[4];
+    candidate<Real>(A, g, i, j, dt, Y);
+    const int top = Wd.top;
+    if (top != 0) {
+      bad = A.cad[c] != 0 || troubled<Real>(A.X, g, D, Wd.d2x, Wd.d2y, i, j, Y);
+    } else {
+      Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
+      Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
+      if (!(y[0] > Real(0)) || !(p > Real(0))) atomicAdd(&A.scw->nfog_pad[A.stage], 1);
+    }
+    A.cad[c] = 0;
+    A.ord[c] = (uint8_t)top;
+    A.first[c] = (uint8_t)bad;
+    combine_store<Real>(A, g, i, j, Y);
+  }
+  queue_push(bad, c, A.queue, A.qcount);
+}
+
+// ---------------------------------------------------------------------------
+// MOOD iteration kernels
+// ---------------------------------------------------------------------------
+// neighbour of (i,j) in direction d (0 W, 1 E, 2 S, 3 N) with periodic wrap;
+// returns -1 beyond a non-periodic boundary
+__device__ __forceinline__ int neighbour(const Grid& g, int i, int j, int d) {
+  int a = i + (d == 0 ? -1 : d == 1 ? 1 : 0);
+  int b = j + (d == 2 ? -1 : d == 3 ? 1 : 0);
+  if (a < 0 || a >= g.nx) {
+    if (!g.periodic_x) return -1;
+    a = wrapi(a, g.nx);
+  }
+  if (b < 0 || b >= g.ny) {
+    if (!g.periodic_y) return -1;
+    b = wrapi(b, g.ny);
+  }
+  return cidx(g, a, b);
+}
+
+// radius of a possibly-ghost cell now and before this iteration's lowering
+__device__ __forceinline__ void radius_pair(const Grid& g, const uint8_t* ord, const uint32_t* stamp,
+                                            uint32_t cur, const Cascade& C, int i, int j,
+                                            int& now, int& before) {
+  const int top = C.top;
+  if (i < 0 || i >= g.nx) {
+    if (!g.periodic_x) { now = before = top; return; }
+    i = wrapi(i, g.nx);
+  }
+  if (j < 0 || j >= g.ny) {
+    if (!g.periodic_y) { now = before = top; return; }
+    j = wrapi(j, g.ny);
+  }
+  int c = cidx(g, i, j);
+  now = ord[c];
+  before = stamp[c] == cur ? C.prev[now] : now;
+}
+
+// direct reconstruction of one face state at radius K (eq. gp_reconstructor)
+template <int K, class Real>
+__device__ __forceinline__ void recon_direct(const double* X, const Grid& g, const Real* z, int i,
+                                             int j, Real* S) {
+  constexpr int N = stencil_n(K);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const double* Xv = X + (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
+    Real s = Real(0);
+    int m = 0;
+#pragma unroll
+    for (int b = -K; b <= K; ++b)
+#pragma unroll
+      for (int a = -K; a <= K; ++a)
+        if ((a < 0 ? -a : a) + (b < 0 ? -b : b) <= K) {
+          s = fma(z[m], (Real)__ldg(Xv + b * g.pitch + a), s);
+          ++m;
+        }
+    S[v] = s;
+  }
+}
+
+// face between cell (iL,jL) and its neighbour (iR,jR) in direction DIR at radius K
+template <int K, class Real, int DIR>
+__device__ void face_at(const double* X, const Grid& g, const DirectW<Real>& Wd, int iL, int jL,
+                        Real* F, bool& badL, bool& badR) {
+  constexpr int Q = rule_q(K);
+  const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
+  const Real gam = (Real)g.gamma;
+  F[0] = F[1] = F[2] = F[3] = Real(0);
+  badL = badR = false;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    Real UL[4], UR[4];
+    if (K == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        UL[v] = (Real)__ldg(X + gidx(g, v, iL, jL));
+        UR[v] = (Real)__ldg(X + gidx(g, v, iR, jR));
+      }
+    } else {
+      // faces: 0 E, 1 W, 2 N, 3 S
+      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
+      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
+    }
+    Real f[4], pl, pr;
+    if (DIR == 0) {
+      hllc_x<Real>(UL, UR, gam, f, pl, pr);
+    } else {
+      Real a[4] = {UL[0], UL[2], UL[1], UL[3]};
+      Real b[4] = {UR[0], UR[2], UR[1], UR[3]};
+      Real h[4];
+      hllc_x<Real>(a, b, gam, h, pl, pr);
+      f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
+    }
+    badL |= !(finite_r(UL[0]) && finite_r(pl));
+    badR |= !(finite_r(UR[0]) && finite_r(pr));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) F[v] = fma(Wd.w[K][q], f[v], F[v]);
+  }
+}
+
+template <class Real, int DIR>
+__device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const DirectW<Real>& Wd,
+                               int iL, int jL, int K) {
+  Real F[4];
+  bool bl, br;
+  switch (K) {
+    case 0: face_at<0, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    case 1: face_at<1, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    case 2: face_at<2, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    default: face_at<3, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+  }
+  const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
+  if (DIR == 0) {
+    int f = iR;  // face index
+#pragma unroll
+    for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, f, jL)] = F[v];
+    if (g.periodic_x && (f == 0 || f == g.nx)) {
+      int f2 = f == 0 ? g.nx : 0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, f2, jL)] = F[v];
+    }
+  } else {
+    int f = jR;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, iL, f)] = F[v];
+    if (g.periodic_y && (f == 0 || f == g.ny)) {
+      int f2 = f == 0 ? g.ny : 0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, iL, f2)] = F[v];
+    }
+  }
+  if (bl) flag_cad(A.cad, g, iL, jL);
+  if (br) flag_cad(A.cad, g, iR, jR);
+}
+
+// one thread per (queued cell, face); faces: 0 W, 1 E, 2 S, 3 N
+template <class Real>
+__global__ void __launch_bounds__(128) k_mood_faces(StageArgs<Real> A, MoodArgs M, Grid g,
+                                                    const __grid_constant__ DirectW<Real> Wd,
+                                                    Cascade C) {
+  const int n = *M.qcount;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4LL * n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = M.queue[t >> 2];
+    const int f = (int)(t & 3);
+    const int i = c % g.nx, j = c / g.nx;
+    // the face shared with another queued cell is done by the west/south one
+    if (f == 0 || f == 2) {
+      int nb = neighbour(g, i, j, f);
+      if (nb >= 0 && M.stamp[nb] == M.cur) continue;
+    }
+    int iL = i, jL = j;
+    if (f == 0) iL = i - 1;
+    if (f == 2) jL = j - 1;
+    const int iR = iL + (f < 2), jR = jL + (f >= 2);
+    int nl, bl, nr, br;
+    radius_pair(g, A.ord, M.stamp, M.cur, C, iL, jL, nl, bl);
+    radius_pair(g, A.ord, M.stamp, M.cur, C, iR, jR, nr, br);
+    int Knew = nl < nr ? nl : nr, Kold = bl < br ? bl : br;
+    if (Knew == Kold) continue;  // EDP1 order of this face unchanged
+    if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, Knew);
+    else recompute_face<Real, 1>(A, g, Wd, iL, jL, Knew);
+  }
+}
+
+// queued cells and their face neighbours: each affected cell is handled by
+// the first queued cell of its list (itself, W, E, S, N)
+template <class Real>
+__global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs M, Grid g,
+                                                     Detect D,
+                                                     const __grid_constant__ DirectW<Real> Wd) {
+  const int n = *M.qcount;
+  const int nthreads = gridDim.x * blockDim.x;
+  const int rounds = (n + nthreads - 1) / nthreads;
+  for (int r = 0; r < rounds; ++r) {
+    const int q = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < n;
+    const int c = live ? M.queue[q] : 0;
+    const int i = c % g.nx, j = c / g.nx;
+    for (int k = 0; k < 5; ++k) {
+      bool flag = false;
+      int d = -1;
+      if (live) {
+        d = k == 0 ? c : neighbour(g, i, j, k - 1);
+        bool mine = d >= 0;
+        if (mine && k > 0) {
+          const int di = d % g.nx, dj = d / g.nx;
+          if (M.stamp[d] == M.cur) mine = false;
+          // earlier entries of d's own list: W, E, S (in that order) before c
+          const int back = k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 3 : 2;  // direction from d to c
+          for (int e = 0; mine && e < back; ++e) {
+            int o = neighbour(g, di, dj, e);
+            if (o >= 0 && M.stamp[o] == M.cur) mine = false;
+          }
+        } else if (mine && k == 0) {
+          mine = true;
+        }
+        if (mine) {
+          const int di = d % g.nx, dj = d / g.nx;
+          double Y[4];
+          candidate<Real>(A, g, di, dj, A.sc->dt, Y);
+          if (A.ord[d] != 0) {
+            flag = A.cad[d] != 0 || troubled<Real>(A.X, g, D, Wd.d2x, Wd.d2y, di, dj, Y);
+          } else {
+            Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
+            Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
+            if (!(y[0] > Real(0)) || !(p > Real(0))) atomicAdd(&A.scw->nfog_pad[A.stage], 1);
+          }
+          A.cad[d] = 0;
+          combine_store<Real>(A, g, di, dj, Y);
+        }
+      }
+      queue_push(flag, d, M.next_queue, M.next_count);
+    }
+  }
+}
+
+// bookkeeping between iterations: counts of the just-finished pass
+}  // namespace gpm

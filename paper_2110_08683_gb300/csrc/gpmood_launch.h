@@ -1,0 +1,29 @@
+// gpmood_launch.h -- host-side launchers of the precision-templated kernels.
+#pragma once
+
+#include "gpmood_internal.h"
+
+namespace gpm {
+
+template <class Real>
+struct Launch {
+  // first pass: x (dir 0) or y (dir 1) faces at the top radius
+  static cudaError_t faces(int top, int dir, const StageArgs<Real>& A, const Grid& g,
+                           const ParityW<Real>& W, cudaStream_t st);
+  static cudaError_t update_first(const StageArgs<Real>& A, const Grid& g, const Detect& D,
+                                  const DirectW<Real>& Wd, cudaStream_t st);
+  static cudaError_t mood_faces(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
+                                const DirectW<Real>& Wd, const Cascade& C, int n,
+                                cudaStream_t st);
+  static cudaError_t mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
+                                 const Detect& D, const DirectW<Real>& Wd, int n, cudaStream_t st);
+};
+
+cudaError_t launch_fill(double* X, const Grid& g, const Scalars* sc, double tfrac, cudaStream_t st);
+cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, double cfl, double fixed_dt,
+                      int clip, double t_end, cudaStream_t st);
+cudaError_t launch_finish(Scalars* sc, cudaStream_t st);
+cudaError_t launch_account(Scalars* sc, int stage, int slot, int first, cudaStream_t st);
+cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, int n, cudaStream_t st);
+
+}  // namespace gpm

@@ -1,0 +1,53 @@
+"""The C ABI library builds, loads and exports every entry point that
+include/gpmood.h declares (no GPU needed: nothing is called but strerror)."""
+import ctypes
+import os
+import re
+
+import paper_2110_08683_gb300 as gp
+from paper_2110_08683_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char\*|void)\s+(gpmood_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    syms = declared_symbols()
+    assert {"gpmood_create", "gpmood_set_state", "gpmood_step", "gpmood_run", "gpmood_flags",
+            "gpmood_destroy"} <= syms
+    for s in sorted(syms):
+        assert hasattr(lib, s), s
+
+
+def test_strerror_without_a_device():
+    lib = gp.load()
+    assert lib.gpmood_strerror(-5) == b"MOOD iteration cap reached"
+    assert lib.gpmood_strerror(0) == b"ok"
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    from paper_2110_08683_gb300 import inputs as I
+
+    p = I.vortex(n=16, R=3)
+    p["nx"] = 2  # fewer cells than ghost layers
+    g = gp.make_grid(p)
+    o = gp.make_options(p)
+    h = ctypes.c_void_p()
+    rc = gp.load().gpmood_create(ctypes.byref(g), 1.4, 3, 0.5, ctypes.byref(o), ctypes.byref(h))
+    assert rc == -1 and not h.value
+    p = I.vortex(n=16, R=3)
+    p["cascade"] = [3, 3, 0]
+    o = gp.make_options(p)
+    rc = gp.load().gpmood_create(ctypes.byref(gp.make_grid(p)), 1.4, 3, 0.5, ctypes.byref(o),
+                                 ctypes.byref(h))
+    assert rc == -1

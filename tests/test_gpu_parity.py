@@ -1,0 +1,213 @@
+"""GPU (CUDA, through the C ABI) against the FP64 CPU oracle on the same seeded
+inputs.  FP64 path: <= 1e-12 relative per step on smooth flows, identical
+first-pass MOOD flag maps and final orders on the first step of
+discontinuous flows, <= 1e-8 L1 density difference at t_end.  Sizes span
+several warp segments (31 faces) and block rows (8) with ragged tails."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2110_08683_gb300 as gp
+from paper_2110_08683_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+REL_STEP = 1e-12
+
+
+def relerr(a, b):
+    """max over variables of max|a-b| / max|b|"""
+    return max(np.abs(a[v] - b[v]).max() / max(np.abs(b[v]).max(), 1e-300) for v in range(4))
+
+
+def pair(prob, precision="fp64"):
+    return gp.GPMood(prob, precision), O.Oracle(prob)
+
+
+def one_step_both(g, o, U, t=0.0, dt=None):
+    g.set_state(U)
+    g.set_time(t)
+    if dt is None:
+        dtg = g.step(want_dt=True)
+        Uo, st, ordo, bado = o.step(U, t)
+        assert abs(dtg - st["dt"]) <= 1e-14 * st["dt"], (dtg, st["dt"])
+    else:
+        g.step_dt(dt)
+        Uo, st, ordo, bado = o.step(U, t, dt_fixed=dt)
+    Ug = g.get_state()
+    ordg, badg, stg = g.flags()
+    return Ug, Uo, (ordg, badg, stg), (ordo, bado, st)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "outflow", "reflect"])
+@pytest.mark.parametrize("R", [0, 1, 2, 3])
+def test_uniform_state(bc, R):
+    st = (1.0, 0.0, 0.0, 1.0) if bc == "reflect" else (1.3, 0.4, -0.25, 0.9)
+    p = I.uniform(37, 19, R=max(R, 1), state=st, bc=bc)
+    p["cascade"] = list(range(R, -1, -1))
+    g, o = pair(p)
+    Ug, Uo, (og, bg, sg), (oo, bo, so) = one_step_both(g, o, p["U0"])
+    assert relerr(Ug, Uo) <= REL_STEP
+    assert (og == oo).all()
+
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_smooth_wave_one_step(R):
+    p = I.density_wave(nx=45, ny=38, amp=0.2, R=R, ell=0.1, kx=1, ky=2)
+    g, o = pair(p)
+    Ug, Uo, (og, bg, sg), (oo, bo, so) = one_step_both(g, o, p["U0"])
+    assert relerr(Ug, Uo) <= REL_STEP
+    assert (og == R).all() and (oo == R).all()
+
+
+@pytest.mark.parametrize("cascade", [[3, 2, 1, 0], [3, 1, 0]])
+def test_vortex_steps(cascade):
+    p = I.vortex(n=50, R=3, cascade=cascade)
+    g, o = pair(p)
+    U = p["U0"]
+    t = 0.0
+    for k in range(3):
+        Ug, Uo, (og, bg, sg), (oo, bo, so) = one_step_both(g, o, U, t)
+        assert relerr(Ug, Uo) <= REL_STEP, k
+        assert (og == oo).all() and (bg == bo).all()
+        assert sg["nbad_first"] == so["nbad_first"]
+        U = Uo
+        t += so["dt"]
+
+
+def _first_step_flags(p, nsteps=1):
+    g, o = pair(p)
+    U = p["U0"]
+    t = 0.0
+    out = []
+    for k in range(nsteps):
+        Ug, Uo, (og, bg, sg), (oo, bo, so) = one_step_both(g, o, U, t)
+        out.append((Ug, Uo, og, oo, bg, bo, sg, so))
+        U = Uo
+        t += so["dt"]
+    return out
+
+
+@pytest.mark.parametrize("R", [1, 2, 3])
+def test_quadrants_first_step_flag_map(R):
+    p = I.quadrants(n=48, ny=40, R=R, seed=7)
+    ((Ug, Uo, og, oo, bg, bo, sg, so),) = _first_step_flags(p)
+    assert (bg == bo).all(), np.argwhere(bg != bo)[:10]
+    assert (og == oo).all(), np.argwhere(og != oo)[:10]
+    assert sg["nbad_first"] == so["nbad_first"]
+    assert sg["iters"] == so["iters"]
+    assert sum(so["nbad_first"]) > 0
+    assert relerr(Ug, Uo) <= 1e-11
+
+
+def test_dmr_first_steps():
+    p = I.dmr(nx=96, ny=24, R=3)
+    res = _first_step_flags(p, nsteps=3)
+    for Ug, Uo, og, oo, bg, bo, sg, so in res:
+        assert (bg == bo).all()
+        assert (og == oo).all()
+        assert relerr(Ug, Uo) <= 1e-11
+
+
+def test_sod_2d_periodic_y_and_paper_cascade():
+    p = I.sod_2d(nx=70, ny=6, R=3, cascade=[3, 1, 0])
+    p["bc"] = ["outflow", "outflow", "periodic", "periodic"]
+    res = _first_step_flags(p, nsteps=2)
+    for Ug, Uo, og, oo, bg, bo, sg, so in res:
+        assert (bg == bo).all() and (og == oo).all()
+        assert relerr(Ug, Uo) <= 1e-11
+
+
+def test_discontinuous_run_l1_at_t_end():
+    p = I.quadrants(n=40, R=3, seed=11)
+    g, o = pair(p)
+    t_end = 0.05
+    g.set_state(p["U0"])
+    ng = g.run(t_end)
+    Ug = g.get_state()
+    Uo, no, to = o.run(p["U0"], t_end)
+    assert ng == no
+    L1 = np.abs(Ug[0] - Uo[0]).mean()
+    assert L1 <= 1e-8, L1
+
+
+def test_mood_cap_is_reported_not_hung():
+    p = I.quadrants(n=32, R=3, seed=1)
+    p["max_iters"] = 1
+    g = gp.GPMood(p)
+    g.set_state(p["U0"])
+    with pytest.raises(gp.GpmoodError) as e:
+        for _ in range(3):
+            g.step()
+    assert e.value.code == -5
+    # the handle stays usable
+    g.set_state(p["U0"])
+    g.get_state()
+
+
+def test_nan_cell_cascades_to_fog_like_the_oracle():
+    p = I.vortex(n=24, R=3)
+    U = p["U0"].copy()
+    U[:, 12, 12] = np.nan
+    g, o = pair(p)
+    g.set_state(U)
+    g.step_dt(1e-3)
+    og, bg, sg = g.flags()
+    Y, oo, bo, it, tot = o.stage(U, 0.0, 1e-3)
+    assert (og[0] == oo).all()
+    assert sg["iters"][0] == it
+    assert sg["nbad_total"][0] == tot
+
+
+@pytest.mark.parametrize("R", [1, 3])
+def test_periodic_conservation(R):
+    p = I.quadrants(n=36, R=R, seed=3)
+    p["bc"] = ["periodic"] * 4
+    g = gp.GPMood(p)
+    g.set_state(p["U0"])
+    for _ in range(5):
+        g.step()
+    U = g.get_state()
+    for v in range(4):
+        assert abs(U[v].sum() - p["U0"][v].sum()) <= 1e-13 * np.abs(p["U0"][v]).sum()
+
+
+def test_bench_workload_first_step_full_size():
+    # the 512^2 isentropic vortex (R3, 7->5->3->1) that the benchmark times,
+    # one full step compared cell by cell with the oracle
+    p = I.vortex(n=512, R=3)
+    g, o = pair(p)
+    Ug, Uo, (og, bg, sg), (oo, bo, so) = one_step_both(g, o, p["U0"])
+    assert relerr(Ug, Uo) <= REL_STEP
+    assert (og == 3).all() and (oo == 3).all()
+
+
+# ---------------------------------------------------------------------------
+# FP32 path: reconstruction / Riemann / detection in float, FP64 state and sums
+# ---------------------------------------------------------------------------
+def test_fp32_vortex_error_against_oracle_and_conservation():
+    p = I.vortex(n=64, R=3)
+    g = gp.GPMood(p, "fp32")
+    o = O.Oracle(p)
+    g.set_state(p["U0"])
+    t_end = 0.5
+    n = g.run(t_end)
+    Ug = g.get_state()
+    Uo, no, _ = o.run(p["U0"], t_end)
+    rel_l1 = np.abs(Ug[0] - Uo[0]).mean() / np.abs(Uo[0]).mean()
+    assert rel_l1 < 1e-5, rel_l1
+    for v in range(4):
+        assert abs(Ug[v].sum() - p["U0"][v].sum()) <= 1e-13 * np.abs(p["U0"][v]).sum()
+
+
+def test_fp32_dmr_positivity():
+    p = I.dmr(nx=128, ny=32, R=3)
+    g = gp.GPMood(p, "fp32")
+    g.set_state(p["U0"])
+    for _ in range(10):
+        g.step()
+    U = g.get_state()
+    pr = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+    assert U[0].min() > 0 and pr.min() > 0
