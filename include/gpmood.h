@@ -56,7 +56,8 @@ enum {
   GPMOOD_E_WEIGHTS = -4,   /* covariance matrix not positive definite in the weight solve */
   GPMOOD_E_MOOD_CAP = -5,  /* the MOOD loop reached max_mood_iters with cells still flagged */
   GPMOOD_E_DT = -6,        /* the time step came out non-positive or not finite */
-  GPMOOD_E_NOSTATE = -7    /* step/run/get before set_state */
+  GPMOOD_E_NOSTATE = -7,   /* step/run/get before set_state */
+  GPMOOD_E_TOO_BIG = -8    /* grid needs more than the static scratch of gpmood_step_noalloc */
 };
 
 /* grid and boundary description (Sec. 2.1); caller-owned, copied at create */
@@ -176,6 +177,40 @@ int gpmood_profile(gpmood_t h, int enable);
 /* Accumulated milliseconds and launch counts per class (arrays of
    GPMOOD_NKCLASS entries, either may be NULL); waits for the stream. */
 int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches);
+
+/*
+ * gpmood_step_noalloc -- one SSP-RK3 step with the MOOD loop that allocates
+ * no memory at all.  The paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory while they run, for example a
+ * host framework that owns the whole device memory pool and forbids raw
+ * cudaMalloc/cudaFree (both synchronise the device and fragment the pool),
+ * or a real-time loop that must not allocate after start-up.
+ *
+ * The step runs the same kernels as gpmood_step on a temporary handle whose
+ * buffers (three ghosted states, face fluxes, flag maps, queues, counters)
+ * are carved out of one file-scope device array of
+ * GPMOOD_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads this
+ * library holds until the process exits.  That covers grids of about
+ * 256 x 256 cells at R_max = 3; a grid needing more returns
+ * GPMOOD_E_TOO_BIG without touching the device.
+ *
+ * Arguments are those of gpmood_create (grid, gamma, R_max, ell, opts) plus:
+ * U_in / U_out, device pointers to cell averages in the layout above (they
+ * may be the same array); t, the time of U_in (time-dependent boundaries);
+ * cfl > 0; dt_out (nullable, host) receives the step's Delta t; stream, a
+ * cudaStream_t or NULL.  The call waits for the stream before it returns.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress with that device current); make that first
+ * call before any stream capture.  Every call shares the one array and
+ * leaves its contents behind; the parts that must start at zero are cleared
+ * at each call.  Calls that overlap on the GPU (other threads or streams)
+ * race on the scratch, so serialise them.  Errors as for gpmood_step.
+ */
+#define GPMOOD_NOALLOC_SCRATCH_BYTES (16u << 20)
+int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_max, double ell,
+                        const gpmood_options* opts, const double* U_in, double* U_out, double t,
+                        double cfl, double* dt_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,8 @@ FP64, FP32 = 0, 1
 
 E_CODES = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "device allocation failed",
            -4: "GP covariance matrix not positive definite", -5: "MOOD iteration cap reached",
-           -6: "time step not positive or not finite", -7: "no state set"}
+           -6: "time step not positive or not finite", -7: "no state set",
+           -8: "grid too large for the static scratch"}
 
 
 class GpmoodError(RuntimeError):
@@ -88,6 +89,8 @@ def load(build_if_missing=True):
     L.gpmood_strerror.restype = C.c_char_p
     L.gpmood_last_launches.argtypes = [p]
     L.gpmood_profile.argtypes = [p, i]
+    L.gpmood_step_noalloc.argtypes = [C.POINTER(Grid), d, i, d, C.POINTER(Options), p, p, d, d,
+                                      C.POINTER(d), p]
     L.gpmood_kernel_times.argtypes = [p, p, p]
     _lib = L
     return L
@@ -207,6 +210,19 @@ def gpmood_set_stream(h, stream_ptr):
 
 def gpmood_last_launches(h):
     return load().gpmood_last_launches(h)
+
+
+def gpmood_step_noalloc(prob, U_in_ptr, U_out_ptr, t, cfl, precision=FP64, stream_ptr=0):
+    """One step through the allocation-free entry point: U_in_ptr / U_out_ptr
+    are device pointers to [4][ny][nx] float64 cell averages.  Returns dt."""
+    dt = C.c_double(0.0)
+    cas = list(prob["cascade"])
+    g, o = make_grid(prob), make_options(prob, precision)
+    _check(load().gpmood_step_noalloc(C.byref(g), prob["gamma"], cas[0], prob["ell"], C.byref(o),
+                                      C.c_void_p(U_in_ptr), C.c_void_p(U_out_ptr), t, cfl,
+                                      C.byref(dt), C.c_void_p(stream_ptr)),
+           "gpmood_step_noalloc")
+    return dt.value
 
 
 KERNEL_CLASSES = ("dt", "ghost", "faces_x", "faces_y", "update", "mood")

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "../../include/gpmood.h"
@@ -343,6 +344,7 @@ const char* gpmood_strerror(int code) {
     case GPMOOD_E_MOOD_CAP: return "MOOD iteration cap reached";
     case GPMOOD_E_DT: return "time step not positive or not finite";
     case GPMOOD_E_NOSTATE: return "no state set";
+    case GPMOOD_E_TOO_BIG: return "grid too large for the static scratch";
     default: return "unknown error";
   }
 }
@@ -633,3 +635,174 @@ int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// gpmood_step_noalloc: the step on a temporary handle whose device buffers
+// live in one file-scope device array.  In host code the array's name only
+// stands for the symbol; the device address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GPMOOD_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices];
+Scalars g_noalloc_host_sc;  // host mirror of the scalars (pageable, shared)
+
+// device address of the scratch array on the current device
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GPMOOD_E_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GPMOOD_E_CUDA;
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GPMOOD_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_max, double ell,
+                                   const gpmood_options* opts, const double* U_in, double* U_out,
+                                   double t, double cfl, double* dt_out, void* stream) {
+  if (!grid || !U_in || !U_out || !(cfl > 0.0) || !isfinite(t)) return GPMOOD_E_INVAL;
+  if (R_max < 0 || R_max > 3 || !(gamma > 1.0) || !(ell > 0.0)) return GPMOOD_E_INVAL;
+  gpmood_options o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  int cascade[4], nc = 0;
+  if (o.ncascade == 0) {
+    for (int r = R_max; r >= 0; --r) cascade[nc++] = r;
+  } else {
+    if (o.ncascade < 1 || o.ncascade > 4) return GPMOOD_E_INVAL;
+    nc = o.ncascade;
+    for (int k = 0; k < nc; ++k) cascade[k] = o.cascade[k];
+    if (cascade[0] != R_max || cascade[nc - 1] != 0) return GPMOOD_E_INVAL;
+    for (int k = 0; k + 1 < nc; ++k)
+      if (!(cascade[k] > cascade[k + 1])) return GPMOOD_E_INVAL;
+  }
+  const int H = R_max + 1 > 2 ? R_max + 1 : 2;
+  const int minn = H > 3 ? H : 3;
+  if (grid->nx < minn || grid->ny < minn) return GPMOOD_E_INVAL;
+  if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0)) return GPMOOD_E_INVAL;
+  for (int s = 0; s < 4; ++s) {
+    int k = grid->bc[s];
+    if (k < 0 || k > 5) return GPMOOD_E_INVAL;
+    if (k == GPMOOD_BC_DMR_BOTTOM && s != 2) return GPMOOD_E_INVAL;
+    if (k == GPMOOD_BC_DMR_TOP && s != 3) return GPMOOD_E_INVAL;
+  }
+  if ((grid->bc[0] == 0) != (grid->bc[1] == 0)) return GPMOOD_E_INVAL;
+  if ((grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
+  if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
+
+  // the temporary handle lives on the host stack
+  gpmood_s hs;
+  gpmood_s* h = &hs;
+  memset(h, 0, sizeof(*h));
+  Grid& g = h->g;
+  g.nx = grid->nx;
+  g.ny = grid->ny;
+  g.H = H;
+  g.pitch = round_up(g.nx + 2 * H, 32);
+  g.gy = g.ny + 2 * H;
+  g.vstride = (long long)g.pitch * g.gy;
+
+  // carve the buffers out of the scratch, 256-byte aligned each
+  const size_t ncell = (size_t)g.nx * g.ny;
+  const size_t fsz = o.precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  const size_t sz_state = align256(sizeof(double) * 4 * (size_t)g.vstride);
+  const size_t sz_fx = align256(fsz * 4 * (size_t)g.ny * (g.nx + 1));
+  const size_t sz_fy = align256(fsz * 4 * (size_t)(g.ny + 1) * g.nx);
+  const size_t sz_c = align256(ncell), sz_c3 = align256(3 * ncell);
+  const size_t sz_stamp = align256(sizeof(uint32_t) * ncell), sz_q = align256(sizeof(int) * ncell);
+  const size_t sz_sc = align256(sizeof(Scalars));
+  const size_t need =
+      3 * sz_state + sz_fx + sz_fy + sz_c + 2 * sz_c3 + sz_stamp + 2 * sz_q + sz_sc;
+  if (need > (size_t)GPMOOD_NOALLOC_SCRATCH_BYTES) return GPMOOD_E_TOO_BIG;
+
+  g.dx = (grid->x1 - grid->x0) / g.nx;
+  g.dy = (grid->y1 - grid->y0) / g.ny;
+  g.inv_dx = 1.0 / g.dx;
+  g.inv_dy = 1.0 / g.dy;
+  g.x0 = grid->x0;
+  g.y0 = grid->y0;
+  g.gamma = gamma;
+  for (int s = 0; s < 4; ++s) {
+    g.bc[s] = grid->bc[s];
+    prim_to_cons(grid->bc_prim[s], gamma, g.bcU[s]);
+  }
+  g.periodic_x = grid->bc[0] == GPMOOD_BC_PERIODIC;
+  g.periodic_y = grid->bc[2] == GPMOOD_BC_PERIODIC;
+  prim_to_cons(grid->dmr_post, gamma, g.dmr_post);
+  prim_to_cons(grid->dmr_pre, gamma, g.dmr_pre);
+  g.dmr_wall_x0 = grid->dmr_wall_x0;
+  g.dmr_xs0 = grid->dmr_xs0;
+  g.dmr_xs_speed = grid->dmr_xs_speed;
+  for (int r = 0; r < 4; ++r) h->cas.next[r] = h->cas.prev[r] = r;
+  for (int k = 0; k + 1 < nc; ++k) {
+    h->cas.next[cascade[k]] = cascade[k + 1];
+    h->cas.prev[cascade[k + 1]] = cascade[k];
+  }
+  h->cas.top = R_max;
+  h->det.sigma_v = o.sigma_v > 0 ? o.sigma_v : 5.0;
+  h->det.sigma_p = o.sigma_p > 0 ? o.sigma_p : 5.0;
+  h->det.csd_on = o.csd_off ? 0 : 1;
+  h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
+  h->det.delta = fmin(g.dx, g.dy);
+  h->precision = o.precision;
+  h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters : 64;
+
+  // GP weights: binary128 solve on the host stack
+  gpw_radius wr[4];
+  memset(wr, 0, sizeof(wr));
+  for (int k = 0; k < nc; ++k) {
+    int R = cascade[k];
+    if (R == 0) continue;
+    if (gpw_solve(R, g.dx, g.dy, ell, &wr[R]) != 0) return GPMOOD_E_WEIGHTS;
+  }
+  int da[25], db[25];
+  double d2x[25], d2y[25];
+  if (gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y) != 5) return GPMOOD_E_WEIGHTS;
+  fill_weights<double>(wr, R_max, d2x, d2y, h->pw64, h->dw64);
+  fill_weights<float>(wr, R_max, d2x, d2y, h->pw32, h->dw32);
+
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  unsigned char* p = base;
+  for (int k = 0; k < 3; ++k) {
+    h->U[k] = (double*)p;
+    p += sz_state;
+  }
+  h->Fx = p; p += sz_fx;
+  h->Fy = p; p += sz_fy;
+  h->cad = p; p += sz_c;
+  h->ord = p; p += sz_c3;
+  h->first = p; p += sz_c3;
+  h->stamp = (uint32_t*)p; p += sz_stamp;
+  h->queue[0] = (int*)p; p += sz_q;
+  h->queue[1] = (int*)p; p += sz_q;
+  h->sc = (Scalars*)p;
+  h->hsc = &g_noalloc_host_sc;
+  h->stream = (cudaStream_t)stream;
+
+  // what the kernels expect to start at zero: face-CAD flags and MOOD stamps
+  CK(cudaMemsetAsync(h->cad, 0, ncell, h->stream));
+  CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * ncell, h->stream));
+  rc = gpmood_set_state(h, U_in, 1);
+  if (rc) return rc;
+  if (t != 0.0) {
+    rc = gpmood_set_time(h, t);
+    if (rc) return rc;
+  }
+  rc = gpmood_step(h, cfl, dt_out);
+  if (rc) return rc;
+  return gpmood_get_state(h, U_out, 1);
+}
