@@ -54,12 +54,15 @@ def faces_flops_per_face(R=3):
     return recon + q * (HLLC_FLOPS + 8)
 
 
+FACE_KERNEL_SOURCES = ("gpmood_kernels.cuh", "gpmood_internal.h", "kernels_impl.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the sources that define the first-pass face kernel."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2110_08683_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in FACE_KERNEL_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 

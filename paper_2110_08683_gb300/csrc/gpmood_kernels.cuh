@@ -140,6 +140,20 @@ __device__ __forceinline__ bool finite_r(Real x) {
   return isfinite(x);
 }
 
+// reciprocal.  FP64: the hardware approximation (rcp.approx.ftz.f64) refined
+// by two Newton-Raphson steps r <- r + r (1 - x r), each of which squares the
+// relative error; non-finite or zero x give a non-finite result.  FP32: the
+// IEEE division.
+__device__ __forceinline__ double recip(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+
 // x-direction HLLC flux; pL/pR return the pressures of the two states so the
 // caller can run face-state CAD without another EoS evaluation.
 // wave speeds S_L = min(uL-cL, uR-cR), S_R = max(uL+cL, uR+cR); the star
@@ -149,7 +163,7 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
                                        Real& pL, Real& pR) {
   const Real gm1 = gam - Real(1);
   Real rL = UL[0], rR = UR[0];
-  Real irL = Real(1) / rL, irR = Real(1) / rR;
+  Real irL = recip(rL), irR = recip(rR);
   Real uL = UL[1] * irL, vL = UL[2] * irL;
   Real uR = UR[1] * irR, vR = UR[2] * irR;
   pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
@@ -162,7 +176,7 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   Real dL = SL - uL, dR = SR - uR;
   Real num = pR - pL + rL * uL * dL - rR * uR * dR;
   Real den = rL * dL - rR * dR;
-  Real Ss = num / den;
+  Real Ss = num * recip(den);
   bool left = Ss >= Real(0);
   Real FL[4] = {rL * uL, rL * uL * uL + pL, rL * uL * vL, uL * (UL[3] + pL)};
   Real FR[4] = {rR * uR, rR * uR * uR + pR, rR * uR * vR, uR * (UR[3] + pR)};
@@ -170,8 +184,8 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   Real rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR;
   Real EK = left ? UL[3] : UR[3], pK = left ? pL : pR, SK = left ? SL : SR;
   Real irK = left ? irL : irR, dK = left ? dL : dR;
-  Real fK = rK * dK / (SK - Ss);
-  Real eK = EK * irK + (Ss - uK) * (Ss + pK * irK / dK);
+  Real fK = rK * dK * recip(SK - Ss);
+  Real eK = EK * irK + (Ss - uK) * (Ss + pK * irK * recip(dK));
   Real UKs[4] = {fK, fK * Ss, fK * vK, fK * eK};
   Real Fs[4];
 #pragma unroll
@@ -251,22 +265,47 @@ __global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
   constexpr int N = stencil_n(R);
   constexpr int Q = rule_q(R);
   constexpr int NS = (Q + 1) / 2;
-  const int lane = threadIdx.x;
-  // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
-  int i, j, nlen;
-  if (DIR == 0) {
-    j = blockIdx.y * kFaceWarps + threadIdx.y;
-    i = blockIdx.x * kSegFaces - 1 + lane;
-    if (j >= g.ny) return;
-    nlen = g.nx;
-  } else {
-    i = blockIdx.x * kFaceWarps + threadIdx.y;
-    j = blockIdx.y * kSegFaces - 1 + lane;
-    if (i >= g.nx) return;
-    nlen = g.ny;
+  // the block's cells and their stencils, converted to Real once and staged
+  // in shared memory as tile[v][slow][fast]: fast runs along the sweep (the
+  // lanes), slow across it (the warps), so every stencil read of a warp is
+  // one contiguous row of shared memory
+  constexpr int TF = kSegCells + 2 * R;
+  constexpr int TS = kFaceWarps + 2 * R;
+  __shared__ Real tile[4][TS][TF];
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int seg = DIR == 0 ? blockIdx.x : blockIdx.y;
+  const int band = DIR == 0 ? blockIdx.y : blockIdx.x;
+  const int fast0 = seg * kSegFaces - 1 - R;  // first tile cell along the sweep
+  const int slow0 = band * kFaceWarps - R;    // first tile cell across it
+  for (int e = warp * 32 + lane; e < 4 * TS * TF; e += 32 * kFaceWarps) {
+    const int v = e / (TS * TF), r = e - v * (TS * TF);
+    int sl, fa;
+    if (DIR == 0) { sl = r / TF; fa = r - sl * TF; }  // consecutive threads along x
+    else { fa = r / TS; sl = r - fa * TS; }           // consecutive threads along x
+    const int i = DIR == 0 ? fast0 + fa : slow0 + sl;
+    const int j = DIR == 0 ? slow0 + sl : fast0 + fa;
+    Real val = Real(0);
+    if (i >= -g.H && i < g.nx + g.H && j >= -g.H && j < g.ny + g.H) val = (Real)__ldg(A.X + gidx(g, v, i, j));
+    tile[v][sl][fa] = val;
   }
+  __syncthreads();
+  // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
+  int i, j, nlen, across;
+  if (DIR == 0) {
+    j = band * kFaceWarps + warp;
+    i = seg * kSegFaces - 1 + lane;
+    nlen = g.nx;
+    across = g.ny;
+  } else {
+    i = band * kFaceWarps + warp;
+    j = seg * kSegFaces - 1 + lane;
+    nlen = g.ny;
+    across = g.nx;
+  }
+  if ((DIR == 0 ? j : i) >= across) return;  // whole warp
   const int pos = DIR == 0 ? i : j;  // position along the sweep, -1 .. nlen
   const bool live = pos <= nlen;
+  const int fl = lane + R, sw = warp + R;  // this cell in the tile
   // states on the two faces of this cell across the sweep direction:
   // P = +1/2 side (east / north), M = -1/2 side (west / south)
   Real SP[Q][4], SM[Q][4];
@@ -274,9 +313,10 @@ __global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
   for (int v = 0; v < 4; ++v) {
     Real s[N];
     if (live) {
-      const double* Xv = A.X + (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
-      const int pitch = g.pitch;
-      auto ld = [&](int a, int b) -> Real { return (Real)__ldg(Xv + b * pitch + a); };
+      // (a, b): offsets along x and y
+      auto ld = [&](int a, int b) -> Real {
+        return DIR == 0 ? tile[v][sw + b][fl + a] : tile[v][sw + a][fl + b];
+      };
       parity_sums<R, Real>(ld, s);
     } else {
 #pragma unroll
@@ -295,10 +335,10 @@ __global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
         } else {
           Real e = T[0][0] + T[0][1], o = T[1][0] + T[1][1];
           Real e2 = T[0][0] - T[0][1], o2 = T[1][0] - T[1][1];
-          SP[kk][v] = e + o;           // E(+g)
-          SM[kk][v] = e - o;           // W(+g)
-          SP[Q - 1 - kk][v] = e2 + o2; // E(-g)
-          SM[Q - 1 - kk][v] = e2 - o2; // W(-g)
+          SP[kk][v] = e + o;            // E(+g)
+          SM[kk][v] = e - o;            // W(+g)
+          SP[Q - 1 - kk][v] = e2 + o2;  // E(-g)
+          SM[Q - 1 - kk][v] = e2 - o2;  // W(-g)
         }
       } else {
         // north / south at +g and -g
@@ -308,10 +348,10 @@ __global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
         } else {
           Real e = T[0][0] + T[1][0], o = T[0][1] + T[1][1];
           Real e2 = T[0][0] - T[1][0], o2 = T[0][1] - T[1][1];
-          SP[kk][v] = e + o;           // N(+g)
-          SM[kk][v] = e - o;           // S(+g)
-          SP[Q - 1 - kk][v] = e2 + o2; // N(-g)
-          SM[Q - 1 - kk][v] = e2 - o2; // S(-g)
+          SP[kk][v] = e + o;            // N(+g)
+          SM[kk][v] = e - o;            // S(+g)
+          SP[Q - 1 - kk][v] = e2 + o2;  // N(-g)
+          SM[Q - 1 - kk][v] = e2 - o2;  // S(-g)
         }
       }
     }
@@ -373,7 +413,7 @@ __device__ bool troubled(const double* X, const Grid& g, const Detect& D, const 
   const Real gm1 = (Real)(g.gamma - 1.0);
   Real Y[4] = {(Real)Yd[0], (Real)Yd[1], (Real)Yd[2], (Real)Yd[3]};
   Real rho = Y[0];
-  Real p = gm1 * (Y[3] - Real(0.5) * (Y[1] * Y[1] + Y[2] * Y[2]) / Y[0]);
+  Real p = gm1 * (Y[3] - Real(0.5) * (Y[1] * Y[1] + Y[2] * Y[2]) * recip(Y[0]));
   if (!finite_r(rho) || !finite_r(p)) return true;   // Step 4, CAD
   if (!(rho > Real(0)) || !(p > Real(0))) return true; // Step 5, PAD
   if (D.csd_on) {                                      // Step 6, CSD
@@ -385,15 +425,16 @@ __device__ bool troubled(const double* X, const Grid& g, const Detect& D, const 
     Real myN = xload<Real>(X, g, 2, i, j + 1), myS = xload<Real>(X, g, 2, i, j - 1);
     Real eE = xload<Real>(X, g, 3, i + 1, j), eW = xload<Real>(X, g, 3, i - 1, j);
     Real eN = xload<Real>(X, g, 3, i, j + 1), eS = xload<Real>(X, g, 3, i, j - 1);
-    Real uE = mxE / rE, uW = mxW / rW, vN = myN / rN, vS = myS / rS;
-    Real pE = gm1 * (eE - Real(0.5) * (mxE * mxE + myE * myE) / rE);
-    Real pW = gm1 * (eW - Real(0.5) * (mxW * mxW + myW * myW) / rW);
-    Real pN = gm1 * (eN - Real(0.5) * (mxN * mxN + myN * myN) / rN);
-    Real pS = gm1 * (eS - Real(0.5) * (mxS * mxS + myS * myS) / rS);
-    const Real dx = (Real)g.dx, dy = (Real)g.dy;
-    Real divV = (uE - uW) / (Real(2) * dx) + (vN - vS) / (Real(2) * dy);
+    Real iE = recip(rE), iW = recip(rW), iN = recip(rN), iS = recip(rS);
+    Real uE = mxE * iE, uW = mxW * iW, vN = myN * iN, vS = myS * iS;
+    Real pE = gm1 * (eE - Real(0.5) * (mxE * mxE + myE * myE) * iE);
+    Real pW = gm1 * (eW - Real(0.5) * (mxW * mxW + myW * myW) * iW);
+    Real pN = gm1 * (eN - Real(0.5) * (mxN * mxN + myN * myN) * iN);
+    Real pS = gm1 * (eS - Real(0.5) * (mxS * mxS + myS * myS) * iS);
+    const Real hx = Real(0.5) * (Real)g.inv_dx, hy = Real(0.5) * (Real)g.inv_dy;
+    Real divV = (uE - uW) * hx + (vN - vS) * hy;
     Real mx_ = pE < pW ? pE : pW, my_ = pN < pS ? pN : pS;
-    Real gradP = fabs(pE - pW) / (Real(2) * dx * mx_) + fabs(pN - pS) / (Real(2) * dy * my_);
+    Real gradP = fabs(pE - pW) * hx * recip(mx_) + fabs(pN - pS) * hy * recip(my_);
     if (divV >= -(Real)D.sigma_v && gradP <= (Real)D.sigma_p) return false;
   }
   Real r0 = xload<Real>(X, g, 0, i, j);
