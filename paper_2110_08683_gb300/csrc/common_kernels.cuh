@@ -66,6 +66,7 @@ __global__ void k_fill_ghosts(double* X, Grid g, const Scalars* sc, double tfrac
 
 
 __global__ void k_dt_reduce(const double* X, Grid g, Scalars* sc) {
+  if (sc->ctl.fixed_dt > 0.0) return;
   double best = INFINITY;
   bool bad = false;
   const long long n = (long long)g.nx * g.ny;
@@ -95,16 +96,17 @@ __global__ void k_dt_reduce(const double* X, Grid g, Scalars* sc) {
   }
 }
 
-// fixed_dt > 0 takes that step; otherwise the CFL step, clipped to t_end
-// when clip != 0
-__global__ void k_dt_finalize(Scalars* sc, double cfl, double fixed_dt, int clip, double t_end) {
+// the step: a given dt (ctl.fixed_dt > 0) or the CFL step, clipped to
+// ctl.t_end when ctl.clip != 0; zeroes the per-step counters
+__global__ void k_dt_finalize(Scalars* sc) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Control c = sc->ctl;
   double dt;
-  if (fixed_dt > 0.0) {
-    dt = fixed_dt;
+  if (c.fixed_dt > 0.0) {
+    dt = c.fixed_dt;
   } else {
-    dt = cfl * __longlong_as_double((long long)sc->dtmin_bits);
-    if (clip && sc->t + dt > t_end) dt = t_end - sc->t;
+    dt = c.cfl * __longlong_as_double((long long)sc->dtmin_bits);
+    if (c.clip && sc->t + dt > c.t_end) dt = c.t_end - sc->t;
   }
   if (!(dt > 0.0) || !isfinite(dt)) sc->err |= kErrDt;
   sc->dt = dt;
@@ -126,24 +128,53 @@ __global__ void k_finish_step(Scalars* sc) {
 
 
 __global__ void k_mood_lower(MoodArgs M, uint8_t* ord, Cascade C) {
-  const int n = *M.qcount;
+  const int slot = M.sc->slot;
+  const int n = M.sc->count[slot];
+  const int* queue = M.queue[slot];
+  const uint32_t cur = M.sc->stamp_cur;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    int c = M.queue[q];
+    int c = queue[q];
     ord[c] = (uint8_t)C.next[ord[c]];
-    M.stamp[c] = M.cur;
+    M.stamp[c] = cur;
   }
 }
 
-
-// bookkeeping after a pass that filled queue slot cur_slot
-__global__ void k_mood_account(Scalars* sc, int stage, int cur_slot, int first) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int n = sc->count[cur_slot];
-  if (first) sc->nbad_first[stage] = n;
-  sc->nbad_total[stage] += n;
-  if (!first) sc->iters[stage] += 1;
-  sc->count[cur_slot ^ 1] = 0;
+// decide whether another MOOD iteration runs; mirrors it into sc->go and,
+// inside a captured graph, into the WHILE node's condition
+__device__ __forceinline__ void mood_decide(Scalars* sc, int stage, int n,
+                                            cudaGraphConditionalHandle hc, int use_graph) {
+  int go = n > 0;
+  if (go && sc->iters[stage] >= sc->ctl.max_iters) {
+    sc->err |= kErrCap;
+    go = 0;
+  }
+  if (go) sc->stamp_cur += 1;  // fresh stamp for the queue about to be worked on
+  sc->go = go;
+  if (use_graph) cudaGraphSetConditional(hc, go ? 1u : 0u);
 }
 
+// after the first pass (which filled queue 0)
+__global__ void k_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n = sc->count[0];
+  sc->slot = 0;
+  sc->count[1] = 0;
+  sc->nbad_first[stage] = n;
+  sc->nbad_total[stage] = n;
+  sc->iters[stage] = 0;
+  mood_decide(sc, stage, n, hc, use_graph);
+}
+
+// after one MOOD iteration (which filled the other queue)
+__global__ void k_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int s = sc->slot, ns = s ^ 1;
+  const int n = sc->count[ns];
+  sc->nbad_total[stage] += n;
+  sc->iters[stage] += 1;
+  sc->count[s] = 0;
+  sc->slot = ns;
+  mood_decide(sc, stage, n, hc, use_graph);
+}
 
 }  // namespace gpm

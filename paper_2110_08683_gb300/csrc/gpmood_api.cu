@@ -38,16 +38,19 @@ struct gpmood_s {
   DirectW<float> dw32;
   int cur;         // buffer holding U^n
   int has_state;
-  uint32_t stamp_ctr;
   int launches;
   int last_status;
-  // optional per-class event timing
+  // optional per-class event timing (graph steps)
   int prof_on;
-  int npend;
-  int pend_cls[64];
-  cudaEvent_t ev[128];
   double prof_ms[GPMOOD_NKCLASS];
   long long prof_n[GPMOOD_NKCLASS];
+  // captured step graphs [buffer rotation][profiled] and their streams
+  Control ctl;  // host copy of the step controls
+  cudaStream_t cs, cs2;
+  cudaGraphExec_t gexec[3][2];
+  cudaEvent_t gev[64];
+  int gev_cls[32];
+  int gev_n, gev_pairs;
 };
 
 namespace {
@@ -148,8 +151,13 @@ int set_err(gpmood_t h, int code) {
   } while (0)
 
 void free_all(gpmood_t h) {
-  for (int k = 0; k < 128; ++k)
-    if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+  for (int k = 0; k < 64; ++k)
+    if (h->gev[k]) cudaEventDestroy(h->gev[k]);
+  for (int r = 0; r < 3; ++r)
+    for (int p = 0; p < 2; ++p)
+      if (h->gexec[r][p]) cudaGraphExecDestroy(h->gexec[r][p]);
+  if (h->cs) cudaStreamDestroy(h->cs);
+  if (h->cs2) cudaStreamDestroy(h->cs2);
   for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
   cudaFree(h->Fx);
   cudaFree(h->Fy);
@@ -176,110 +184,238 @@ StageArgs<Real> stage_args(gpmood_t h, int s, int ia, int ix, int io) {
   A.ord = h->ord + s * nc;
   A.first = h->first + s * nc;
   A.queue = h->queue[0];
-  A.qcount = &h->sc->count[0];
+  A.qcount = &h->sc->count[0];  // the first pass fills queue 0
   A.sc = h->sc;
   A.scw = h->sc;
   A.stage = s;
   return A;
 }
 
-// event timing: resolve the recorded pairs once the stream has drained
-void prof_resolve(gpmood_t h) {
-  for (int k = 0; k < h->npend; ++k) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]) == cudaSuccess)
-      h->prof_ms[h->pend_cls[k]] += ms;
-  }
-  h->npend = 0;
-}
-
-void prof_begin(gpmood_t h) {
-  if (h->prof_on) cudaEventRecord(h->ev[2 * h->npend], h->stream);
-}
-
-void prof_end(gpmood_t h, int cls, int nlaunch) {
-  h->launches += nlaunch;
-  if (!h->prof_on) return;
-  cudaEventRecord(h->ev[2 * h->npend + 1], h->stream);
-  h->pend_cls[h->npend] = cls;
-  h->prof_n[cls] += nlaunch;
-  if (++h->npend == 64) {
-    cudaStreamSynchronize(h->stream);
-    prof_resolve(h);
-  }
-}
-
 // read the device scalars (synchronises the stream)
 int pull_scalars(gpmood_t h) {
   CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  prof_resolve(h);
   return 0;
 }
 
+void write_control(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+  h->ctl.cfl = cfl;
+  h->ctl.fixed_dt = fixed_dt;
+  h->ctl.clip = clip;
+  h->ctl.t_end = t_end;
+  h->ctl.max_iters = h->max_iters;
+}
+
+int push_control(gpmood_t h) {
+  // pageable source: staged by the driver at the call, so the host copy may
+  // change right after
+  CK(cudaMemcpyAsync(&h->sc->ctl, &h->ctl, sizeof(Control), cudaMemcpyHostToDevice, h->stream));
+  return 0;
+}
+
+// kernels launched by one step: dt (2), per stage fill, faces x/y, update,
+// begin (5), 4 per MOOD iteration, finish (1)
+int step_launches(const Scalars& s) {
+  int n = 2 + 3 * 5 + 1;
+  for (int k = 0; k < 3; ++k) n += 4 * s.iters[k];
+  return n;
+}
+
+int step_error(gpmood_t h) {
+  if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
+  if (h->hsc->err & kErrCap) return set_err(h, GPMOOD_E_MOOD_CAP);
+  return GPMOOD_OK;
+}
+
 template <class Real>
-int run_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
-              const DirectW<Real>& D) {
+MoodArgs mood_args(gpmood_t h) {
+  MoodArgs M;
+  M.queue[0] = h->queue[0];
+  M.queue[1] = h->queue[1];
+  M.stamp = h->stamp;
+  M.sc = h->sc;
+  return M;
+}
+
+template <class Real>
+int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const ParityW<Real>& P,
+               const DirectW<Real>& D, cudaStream_t st) {
   static const double tfrac[3] = {0.0, 1.0, 0.5};
-  prof_begin(h);
-  CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], h->stream));
-  prof_end(h, GPMOOD_K_GHOST, 1);
+  CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], st));
+  CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
+  CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
+  CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
+  return 0;
+}
+
+// ---- eager step: the host reads the loop decision after every iteration.
+// Used by gpmood_step_noalloc, which must not build graphs. ----
+template <class Real>
+int eager_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
+                const DirectW<Real>& D) {
   StageArgs<Real> A = stage_args<Real>(h, s, ia, ix, io);
-  prof_begin(h);
-  CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, h->stream));
-  prof_end(h, GPMOOD_K_FACES_X, 1);
-  prof_begin(h);
-  CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, h->stream));
-  prof_end(h, GPMOOD_K_FACES_Y, 1);
-  prof_begin(h);
-  CK(Launch<Real>::update_first(A, h->g, h->det, D, h->stream));
-  CK(launch_account(h->sc, s, 0, 1, h->stream));
-  prof_end(h, GPMOOD_K_UPDATE, 2);
-  int slot = 0, it = 0;
+  int rc = first_pass<Real>(h, A, ix, s, P, D, h->stream);
+  if (rc) return rc;
+  CK(launch_mood_begin(h->sc, s, 0, 0, h->stream));
+  const MoodArgs M = mood_args<Real>(h);
   for (;;) {
-    int rc = pull_scalars(h);
+    rc = pull_scalars(h);
     if (rc) return rc;
-    const int n = h->hsc->count[slot];
-    if (n == 0) break;
-    if (it >= h->max_iters) return set_err(h, GPMOOD_E_MOOD_CAP);
-    ++it;
-    MoodArgs M;
-    M.queue = h->queue[slot];
-    M.qcount = &h->sc->count[slot];
-    M.next_queue = h->queue[slot ^ 1];
-    M.next_count = &h->sc->count[slot ^ 1];
-    M.stamp = h->stamp;
-    M.cur = ++h->stamp_ctr;
-    prof_begin(h);
-    CK(launch_lower(M, A.ord, h->cas, n, h->stream));
-    CK(Launch<Real>::mood_faces(A, M, h->g, D, h->cas, n, h->stream));
-    CK(Launch<Real>::mood_update(A, M, h->g, h->det, D, n, h->stream));
-    CK(launch_account(h->sc, s, slot ^ 1, 0, h->stream));
-    prof_end(h, GPMOOD_K_MOOD, 4);
-    slot ^= 1;
+    if (!h->hsc->go) break;
+    CK(launch_lower(M, A.ord, h->cas, h->stream));
+    CK(Launch<Real>::mood_faces(A, M, h->g, D, h->cas, h->stream));
+    CK(Launch<Real>::mood_update(A, M, h->g, h->det, D, h->stream));
+    CK(launch_mood_end(h->sc, s, 0, 0, h->stream));
   }
   return 0;
 }
 
 int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
-  h->launches = 0;
   const int a = h->cur, b = (a + 1) % 3, c = (a + 2) % 3;
-  prof_begin(h);
-  CK(launch_dt(h->U[a], h->g, h->sc, cfl, fixed_dt, clip, t_end, h->stream));
-  prof_end(h, GPMOOD_K_DT, fixed_dt > 0.0 ? 1 : 2);
+  write_control(h, cfl, fixed_dt, clip, t_end);
+  int rc = push_control(h);
+  if (rc) return rc;
+  CK(launch_dt(h->U[a], h->g, h->sc, h->stream));
   const int in[3] = {a, b, c}, out[3] = {b, c, b};
   for (int s = 0; s < 3; ++s) {
-    int rc = h->precision == GPMOOD_FP32
-                 ? run_stage<float>(h, s, a, in[s], out[s], h->pw32, h->dw32)
-                 : run_stage<double>(h, s, a, in[s], out[s], h->pw64, h->dw64);
+    rc = h->precision == GPMOOD_FP32 ? eager_stage<float>(h, s, a, in[s], out[s], h->pw32, h->dw32)
+                                     : eager_stage<double>(h, s, a, in[s], out[s], h->pw64, h->dw64);
     if (rc) return rc;
-    if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
+    rc = step_error(h);
+    if (rc) return rc;
   }
-  prof_begin(h);
   CK(launch_finish(h->sc, h->stream));
-  prof_end(h, GPMOOD_K_DT, 1);
+  rc = pull_scalars(h);
+  if (rc) return rc;
+  h->launches = step_launches(*h->hsc);
   h->cur = b;
+  h->last_status = GPMOOD_OK;
+  return GPMOOD_OK;
+}
+
+// ---- graph step: one captured graph per buffer rotation; the MOOD loop of
+// every stage is a conditional WHILE node whose body ends with the kernel
+// that decides the next iteration, so a step needs no host round trip ----
+void rec_event(gpmood_t h, int prof, int cls, int open, cudaStream_t st) {
+  if (!prof) return;
+  int k = h->gev_n;
+  cudaEventRecordWithFlags(h->gev[k], st, cudaEventRecordExternal);
+  if (!open) h->gev_cls[(k - 1) / 2] = cls;
+  h->gev_n = k + 1;
+}
+
+template <class Real>
+int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
+                  const DirectW<Real>& D, int prof) {
+  static const double tfrac[3] = {0.0, 1.0, 0.5};
+  cudaStream_t st = h->cs;
+  StageArgs<Real> A = stage_args<Real>(h, s, ia, ix, io);
+  rec_event(h, prof, GPMOOD_K_GHOST, 1, st);
+  CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], st));
+  rec_event(h, prof, GPMOOD_K_GHOST, 0, st);
+  rec_event(h, prof, GPMOOD_K_FACES_X, 1, st);
+  CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
+  rec_event(h, prof, GPMOOD_K_FACES_X, 0, st);
+  rec_event(h, prof, GPMOOD_K_FACES_Y, 1, st);
+  CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
+  rec_event(h, prof, GPMOOD_K_FACES_Y, 0, st);
+  rec_event(h, prof, GPMOOD_K_UPDATE, 1, st);
+  CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
+  // the WHILE node's condition, reset to 0 at every launch of the graph
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, graph, 0, cudaGraphCondAssignDefault));
+  CK(launch_mood_begin(h->sc, s, hc, 1, st));
+  rec_event(h, prof, GPMOOD_K_UPDATE, 0, st);
+  rec_event(h, prof, GPMOOD_K_MOOD, 1, st);
+  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  // the loop body, captured on the second stream into the node's graph
+  CK(cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  const MoodArgs M = mood_args<Real>(h);
+  cudaError_t e1 = launch_lower(M, A.ord, h->cas, h->cs2);
+  cudaError_t e2 = Launch<Real>::mood_faces(A, M, h->g, D, h->cas, h->cs2);
+  cudaError_t e3 = Launch<Real>::mood_update(A, M, h->g, h->det, D, h->cs2);
+  cudaError_t e4 = launch_mood_end(h->sc, s, hc, 1, h->cs2);
+  cudaGraph_t tmp;
+  CK(cudaStreamEndCapture(h->cs2, &tmp));
+  CK(e1); CK(e2); CK(e3); CK(e4);
+  CK(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  rec_event(h, prof, GPMOOD_K_MOOD, 0, st);
+  return 0;
+}
+
+int capture_step(gpmood_t h, int cur, int prof, cudaGraphExec_t* out) {
+  const int a = cur, b = (a + 1) % 3, c = (a + 2) % 3;
+  const int in[3] = {a, b, c}, outb[3] = {b, c, b};
+  cudaStream_t st = h->cs;
+  h->gev_n = 0;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = 0;
+  rec_event(h, prof, GPMOOD_K_DT, 1, st);
+  if (launch_dt(h->U[a], h->g, h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
+  rec_event(h, prof, GPMOOD_K_DT, 0, st);
+  for (int s = 0; s < 3 && !rc; ++s)
+    rc = h->precision == GPMOOD_FP32
+             ? capture_stage<float>(h, s, a, in[s], outb[s], h->pw32, h->dw32, prof)
+             : capture_stage<double>(h, s, a, in[s], outb[s], h->pw64, h->dw64, prof);
+  if (!rc && launch_finish(h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (!rc && ee != cudaSuccess) rc = GPMOOD_E_CUDA;
+  if (!rc && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) rc = GPMOOD_E_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (rc) return set_err(h, rc);
+  if (prof) h->gev_pairs = h->gev_n / 2;
+  return GPMOOD_OK;
+}
+
+int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+  if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
+  const int prof = h->prof_on ? 1 : 0;
+  cudaGraphExec_t& ge = h->gexec[h->cur][prof];
+  if (!ge) {
+    int rc = capture_step(h, h->cur, prof, &ge);
+    if (rc) return rc;
+  }
+  write_control(h, cfl, fixed_dt, clip, t_end);
+  int rc = push_control(h);
+  if (rc) return rc;
+  CK(cudaGraphLaunch(ge, h->stream));
+  rc = pull_scalars(h);
+  if (rc) return rc;
+  if (prof) {
+    for (int k = 0; k < h->gev_pairs; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->gev[2 * k], h->gev[2 * k + 1]) == cudaSuccess)
+        h->prof_ms[h->gev_cls[k]] += ms;
+    }
+    const Scalars& s = *h->hsc;
+    h->prof_n[GPMOOD_K_DT] += 3;
+    h->prof_n[GPMOOD_K_GHOST] += 3;
+    h->prof_n[GPMOOD_K_FACES_X] += 3;
+    h->prof_n[GPMOOD_K_FACES_Y] += 3;
+    h->prof_n[GPMOOD_K_UPDATE] += 6;
+    h->prof_n[GPMOOD_K_MOOD] += 4 * (s.iters[0] + s.iters[1] + s.iters[2]);
+  }
+  rc = step_error(h);
+  if (rc) return rc;
+  h->launches = step_launches(*h->hsc);
+  h->cur = (h->cur + 1) % 3;
   h->last_status = GPMOOD_OK;
   return GPMOOD_OK;
 }
@@ -299,13 +435,12 @@ cudaError_t launch_fill(double* X, const Grid& g, const Scalars* sc, double tfra
   return cudaGetLastError();
 }
 
-cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, double cfl, double fixed_dt,
-                      int clip, double t_end, cudaStream_t st) {
+cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, cudaStream_t st) {
   long long n = (long long)g.nx * g.ny;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  if (fixed_dt <= 0.0) k_dt_reduce<<<blocks, 256, 0, st>>>(X, g, sc);
-  k_dt_finalize<<<1, 32, 0, st>>>(sc, cfl, fixed_dt, clip, t_end);
+  k_dt_reduce<<<blocks, 256, 0, st>>>(X, g, sc);
+  k_dt_finalize<<<1, 32, 0, st>>>(sc);
   return cudaGetLastError();
 }
 
@@ -314,16 +449,20 @@ cudaError_t launch_finish(Scalars* sc, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_account(Scalars* sc, int stage, int slot, int first, cudaStream_t st) {
-  k_mood_account<<<1, 32, 0, st>>>(sc, stage, slot, first);
+cudaError_t launch_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
+                              cudaStream_t st) {
+  k_mood_begin<<<1, 32, 0, st>>>(sc, stage, hc, use_graph);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, int n,
-                         cudaStream_t st) {
-  int blocks = (n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  k_mood_lower<<<blocks, 256, 0, st>>>(M, ord, C);
+cudaError_t launch_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
+                            cudaStream_t st) {
+  k_mood_end<<<1, 32, 0, st>>>(sc, stage, hc, use_graph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, cudaStream_t st) {
+  k_mood_lower<<<kMoodBlocks, 256, 0, st>>>(M, ord, C);
   return cudaGetLastError();
 }
 
@@ -478,12 +617,14 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
     delete h;
     return GPMOOD_E_CUDA;
   }
-  for (int k = 0; k < 128; ++k)
-    if (cudaEventCreate(&h->ev[k]) != cudaSuccess) {
-      free_all(h);
-      delete h;
-      return GPMOOD_E_CUDA;
-    }
+  bool evok = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < 64 && evok; ++k) evok = cudaEventCreate(&h->gev[k]) == cudaSuccess;
+  if (!evok) {
+    free_all(h);
+    delete h;
+    return GPMOOD_E_CUDA;
+  }
   h->stream = nullptr;
   h->last_status = GPMOOD_OK;
   *out = h;
@@ -508,6 +649,8 @@ int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          h->stream));
   }
+  // MOOD stamps restart with the scalars
+  CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * (size_t)g.nx * g.ny, h->stream));
   Scalars z;
   memset(&z, 0, sizeof(z));
   z.dtmin_bits = 0x7ff0000000000000ull;
@@ -544,19 +687,15 @@ int gpmood_get_state(gpmood_t h, double* U, int on_device) {
 
 int gpmood_step(gpmood_t h, double cfl, double* dt_out) {
   if (!h || !(cfl > 0.0)) return GPMOOD_E_INVAL;
-  int rc = do_step(h, cfl, 0.0, 0, 0.0);
+  int rc = graph_step(h, cfl, 0.0, 0, 0.0);
   if (rc) return rc;
-  if (dt_out) {
-    rc = pull_scalars(h);
-    if (rc) return rc;
-    *dt_out = h->hsc->dt;
-  }
+  if (dt_out) *dt_out = h->hsc->dt;
   return GPMOOD_OK;
 }
 
 int gpmood_step_dt(gpmood_t h, double dt) {
   if (!h || !(dt > 0.0)) return GPMOOD_E_INVAL;
-  return do_step(h, 1.0, dt, 0, 0.0);
+  return graph_step(h, 1.0, dt, 0, 0.0);
 }
 
 int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out) {
@@ -566,11 +705,9 @@ int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out) {
   int rc = pull_scalars(h);
   if (rc) return rc;
   while (h->hsc->t < t_end * (1.0 - 1e-14)) {
-    rc = do_step(h, cfl, 0.0, 1, t_end);
+    rc = graph_step(h, cfl, 0.0, 1, t_end);
     if (rc) return rc;
     ++n;
-    rc = pull_scalars(h);
-    if (rc) return rc;
   }
   if (nsteps_out) *nsteps_out = n;
   return GPMOOD_OK;
@@ -613,7 +750,6 @@ int gpmood_last_launches(gpmood_t h) { return h ? h->launches : 0; }
 int gpmood_profile(gpmood_t h, int enable) {
   if (!h) return GPMOOD_E_INVAL;
   CK(cudaStreamSynchronize(h->stream));
-  prof_resolve(h);
   h->prof_on = enable ? 1 : 0;
   if (enable)
     for (int k = 0; k < GPMOOD_NKCLASS; ++k) {
@@ -626,7 +762,6 @@ int gpmood_profile(gpmood_t h, int enable) {
 int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
   if (!h) return GPMOOD_E_INVAL;
   CK(cudaStreamSynchronize(h->stream));
-  prof_resolve(h);
   for (int k = 0; k < GPMOOD_NKCLASS; ++k) {
     if (ms) ms[k] = h->prof_ms[k];
     if (launches) launches[k] = h->prof_n[k];
@@ -802,7 +937,9 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
     rc = gpmood_set_time(h, t);
     if (rc) return rc;
   }
-  rc = gpmood_step(h, cfl, dt_out);
+  // the eager driver: a captured graph would need driver allocations
+  rc = do_step(h, cfl, 0.0, 0, 0.0);
   if (rc) return rc;
+  if (dt_out) *dt_out = h->hsc->dt;
   return gpmood_get_state(h, U_out, 1);
 }

@@ -28,13 +28,26 @@ struct Grid {
   double dmr_wall_x0, dmr_xs0, dmr_xs_speed;
 };
 
+// step controls written by the host before every step
+struct Control {
+  double cfl;        // CFL number of the step
+  double fixed_dt;   // > 0: take this step instead of the CFL one
+  double t_end;      // clip target when clip != 0
+  int clip;
+  int max_iters;     // MOOD iteration cap per stage
+};
+
 // scalars living on the device (one per handle)
 struct Scalars {
+  Control ctl;
   double t;                     // time at the start of the current step
   double dt;                    // current step
   unsigned long long dtmin_bits;  // running min of dx/(|u|+c) as ordered bits
   int err;                      // error bits (kErr*)
   int count[2];                 // queue lengths (double buffered)
+  int slot;                     // queue holding the cells to work on
+  int go;                       // MOOD loop continues (mirrors the graph condition)
+  unsigned int stamp_cur;       // stamp of the cells in the current queue
   int iters[3], nbad_first[3], nbad_total[3], nfog_pad[3];
   long long nsteps;
 };
@@ -92,13 +105,13 @@ struct StageArgs {
   int stage;
 };
 
+// the two queues alternate: sc->slot names the one holding the cells of the
+// current iteration, the other receives the cells troubled after it;
+// stamp[c] == sc->stamp_cur marks the cells of the current queue
 struct MoodArgs {
-  const int* queue;   // cells troubled in the previous pass
-  const int* qcount;
-  int* next_queue;
-  int* next_count;
-  uint32_t* stamp;    // stamp[c] == cur: c is in the current queue
-  uint32_t cur;
+  int* queue[2];
+  uint32_t* stamp;
+  Scalars* sc;
 };
 
 }  // namespace gpm

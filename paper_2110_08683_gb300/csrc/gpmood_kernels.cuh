@@ -688,24 +688,27 @@ template <class Real>
 __global__ void __launch_bounds__(128) k_mood_faces(StageArgs<Real> A, MoodArgs M, Grid g,
                                                     const __grid_constant__ DirectW<Real> Wd,
                                                     Cascade C) {
-  const int n = *M.qcount;
+  const int slot = M.sc->slot;
+  const int n = M.sc->count[slot];
+  const int* queue = M.queue[slot];
+  const uint32_t cur = M.sc->stamp_cur;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4LL * n;
        t += (long long)gridDim.x * blockDim.x) {
-    const int c = M.queue[t >> 2];
+    const int c = queue[t >> 2];
     const int f = (int)(t & 3);
     const int i = c % g.nx, j = c / g.nx;
     // the face shared with another queued cell is done by the west/south one
     if (f == 0 || f == 2) {
       int nb = neighbour(g, i, j, f);
-      if (nb >= 0 && M.stamp[nb] == M.cur) continue;
+      if (nb >= 0 && M.stamp[nb] == cur) continue;
     }
     int iL = i, jL = j;
     if (f == 0) iL = i - 1;
     if (f == 2) jL = j - 1;
     const int iR = iL + (f < 2), jR = jL + (f >= 2);
     int nl, bl, nr, br;
-    radius_pair(g, A.ord, M.stamp, M.cur, C, iL, jL, nl, bl);
-    radius_pair(g, A.ord, M.stamp, M.cur, C, iR, jR, nr, br);
+    radius_pair(g, A.ord, M.stamp, cur, C, iL, jL, nl, bl);
+    radius_pair(g, A.ord, M.stamp, cur, C, iR, jR, nr, br);
     int Knew = nl < nr ? nl : nr, Kold = bl < br ? bl : br;
     if (Knew == Kold) continue;  // EDP1 order of this face unchanged
     if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, Knew);
@@ -719,13 +722,18 @@ template <class Real>
 __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs M, Grid g,
                                                      Detect D,
                                                      const __grid_constant__ DirectW<Real> Wd) {
-  const int n = *M.qcount;
+  const int slot = M.sc->slot;
+  const int n = M.sc->count[slot];
+  const int* queue = M.queue[slot];
+  int* next_queue = M.queue[slot ^ 1];
+  int* next_count = &M.sc->count[slot ^ 1];
+  const uint32_t cur = M.sc->stamp_cur;
   const int nthreads = gridDim.x * blockDim.x;
   const int rounds = (n + nthreads - 1) / nthreads;
   for (int r = 0; r < rounds; ++r) {
     const int q = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = q < n;
-    const int c = live ? M.queue[q] : 0;
+    const int c = live ? queue[q] : 0;
     const int i = c % g.nx, j = c / g.nx;
     for (int k = 0; k < 5; ++k) {
       bool flag = false;
@@ -735,15 +743,13 @@ __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs
         bool mine = d >= 0;
         if (mine && k > 0) {
           const int di = d % g.nx, dj = d / g.nx;
-          if (M.stamp[d] == M.cur) mine = false;
+          if (M.stamp[d] == cur) mine = false;
           // earlier entries of d's own list: W, E, S (in that order) before c
           const int back = k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 3 : 2;  // direction from d to c
           for (int e = 0; mine && e < back; ++e) {
             int o = neighbour(g, di, dj, e);
-            if (o >= 0 && M.stamp[o] == M.cur) mine = false;
+            if (o >= 0 && M.stamp[o] == cur) mine = false;
           }
-        } else if (mine && k == 0) {
-          mine = true;
         }
         if (mine) {
           const int di = d % g.nx, dj = d / g.nx;
@@ -760,10 +766,9 @@ __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs
           combine_store<Real>(A, g, di, dj, Y);
         }
       }
-      queue_push(flag, d, M.next_queue, M.next_count);
+      queue_push(flag, d, next_queue, next_count);
     }
   }
 }
 
-// bookkeeping between iterations: counts of the just-finished pass
 }  // namespace gpm

@@ -12,18 +12,23 @@ struct Launch {
                            const ParityW<Real>& W, cudaStream_t st);
   static cudaError_t update_first(const StageArgs<Real>& A, const Grid& g, const Detect& D,
                                   const DirectW<Real>& Wd, cudaStream_t st);
+  // MOOD kernels read the queue length on the device; grids are fixed
   static cudaError_t mood_faces(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
-                                const DirectW<Real>& Wd, const Cascade& C, int n,
-                                cudaStream_t st);
+                                const DirectW<Real>& Wd, const Cascade& C, cudaStream_t st);
   static cudaError_t mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
-                                 const Detect& D, const DirectW<Real>& Wd, int n, cudaStream_t st);
+                                 const Detect& D, const DirectW<Real>& Wd, cudaStream_t st);
 };
 
 cudaError_t launch_fill(double* X, const Grid& g, const Scalars* sc, double tfrac, cudaStream_t st);
-cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, double cfl, double fixed_dt,
-                      int clip, double t_end, cudaStream_t st);
+cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, cudaStream_t st);
 cudaError_t launch_finish(Scalars* sc, cudaStream_t st);
-cudaError_t launch_account(Scalars* sc, int stage, int slot, int first, cudaStream_t st);
-cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, int n, cudaStream_t st);
+cudaError_t launch_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
+                              cudaStream_t st);
+cudaError_t launch_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
+                            cudaStream_t st);
+cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, cudaStream_t st);
+
+// fixed grid of the MOOD kernels (they stride over the queue)
+constexpr int kMoodBlocks = 152 * 4;
 
 }  // namespace gpm

@@ -42,24 +42,15 @@ cudaError_t Launch<Real>::update_first(const StageArgs<Real>& A, const Grid& g, 
 
 template <class Real>
 cudaError_t Launch<Real>::mood_faces(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
-                                     const DirectW<Real>& Wd, const Cascade& C, int n,
-                                     cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  long long work = 4LL * n;
-  int blocks = (int)((work + 127) / 128);
-  if (blocks > 4096) blocks = 4096;
-  k_mood_faces<Real><<<blocks, 128, 0, st>>>(A, M, g, Wd, C);
+                                     const DirectW<Real>& Wd, const Cascade& C, cudaStream_t st) {
+  k_mood_faces<Real><<<2 * kMoodBlocks, 128, 0, st>>>(A, M, g, Wd, C);
   return cudaGetLastError();
 }
 
 template <class Real>
 cudaError_t Launch<Real>::mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
-                                      const Detect& D, const DirectW<Real>& Wd, int n,
-                                      cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  int blocks = (n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  k_mood_update<Real><<<blocks, 256, 0, st>>>(A, M, g, D, Wd);
+                                      const Detect& D, const DirectW<Real>& Wd, cudaStream_t st) {
+  k_mood_update<Real><<<kMoodBlocks, 256, 0, st>>>(A, M, g, D, Wd);
   return cudaGetLastError();
 }
 
