@@ -79,7 +79,7 @@ typedef struct {
   double sigma_v;       /* CSD threshold on -div V (0 -> 5, Sec. 3.4) */
   double sigma_p;       /* CSD threshold on the normalised |grad p| (0 -> 5) */
   int csd_off;          /* 1 disables CSD (Step 6) */
-  int max_mood_iters;   /* cap on MOOD iterations per RK stage (0 -> 64) */
+  int max_mood_iters;   /* cap on MOOD iterations per RK stage (0 -> 64 + 4 max(nx, ny)) */
 } gpmood_options;
 
 /* per-step diagnostics of the most recent step */
@@ -177,6 +177,47 @@ int gpmood_profile(gpmood_t h, int enable);
 /* Accumulated milliseconds and launch counts per class (arrays of
    GPMOOD_NKCLASS entries, either may be NULL); waits for the stream. */
 int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches);
+
+/*
+ * Batches: many independent problems of uneven sizes advanced together.
+ * Every problem has its own grid and boundaries and its own time step; all
+ * share gamma, R_max, the cascade and the options, and the GP weights, so
+ * ell/dx and ell/dy must be the same for every problem (ell = c * dx with
+ * one c, as in ell = 12 dx).  Each kernel class runs as one persistent
+ * launch that walks (problem, block) work items; a step is one captured
+ * graph whose MOOD loops run on the device.  The first step times the face
+ * kernel variants (4 or 8 warps, i.e. rows or columns, per work item) and
+ * keeps the faster per sweep.
+ *
+ * State arrays of a batch are the problems' arrays (layout above) one after
+ * the other, in problem order.  Errors as for the single-problem calls; the
+ * MOOD iteration cap applies to the whole batch.
+ */
+typedef struct gpmood_batch_s* gpmood_batch_t;
+
+/* grids[nprob], ell[nprob]: per problem; the other arguments as for
+   gpmood_create.  GPMOOD_E_INVAL if the problems need different weights. */
+int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R_max,
+                        const double* ell, const gpmood_options* opts, gpmood_batch_t* out);
+int gpmood_batch_set_stream(gpmood_batch_t b, void* stream);
+/* all problems' cell averages, concatenated; resets every problem's time */
+int gpmood_batch_set_state(gpmood_batch_t b, const double* U, int on_device);
+int gpmood_batch_get_state(gpmood_batch_t b, double* U, int on_device);
+/* one SSP-RK3 step of every problem with its own CFL time step (waits) */
+int gpmood_batch_step(gpmood_batch_t b, double cfl);
+/* step until every problem has reached t_end (each clips its last step);
+   nsteps_out gets the number of batch steps */
+int gpmood_batch_run(gpmood_batch_t b, double t_end, double cfl, long long* nsteps_out);
+/* per-problem time, last step and step count (arrays of nprob, nullable);
+   total (nullable) gets the summed MOOD statistics of the last step */
+int gpmood_batch_info(gpmood_batch_t b, double* t, double* dt, long long* nsteps,
+                      gpmood_stats* total);
+/* the autotuner's choice per sweep (x, y): warps per block and the number
+   of work items (blocks); GPMOOD_E_NOSTATE before the first step */
+int gpmood_batch_tuning(gpmood_batch_t b, int* warps, int* blocks);
+int gpmood_batch_profile(gpmood_batch_t b, int enable);
+int gpmood_batch_kernel_times(gpmood_batch_t b, double* ms, long long* launches);
+int gpmood_batch_destroy(gpmood_batch_t b);
 
 /*
  * gpmood_step_noalloc -- one SSP-RK3 step with the MOOD loop that allocates

@@ -161,7 +161,7 @@ def make_config(prob):
     cfg.ell = prob["ell"]
     cfg.sigma_v, cfg.sigma_p = prob["sigma_v"], prob["sigma_p"]
     cfg.csd_on = int(prob["csd_on"])
-    cfg.max_iters = int(prob.get("max_iters", 64))
+    cfg.max_iters = int(prob.get("max_iters", 0)) or 1000000
     for k in range(4):
         cfg.dmr_post[k] = prob["dmr_post"][k]
         cfg.dmr_pre[k] = prob["dmr_pre"][k]

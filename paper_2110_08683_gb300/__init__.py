@@ -89,6 +89,18 @@ def load(build_if_missing=True):
     L.gpmood_strerror.restype = C.c_char_p
     L.gpmood_last_launches.argtypes = [p]
     L.gpmood_profile.argtypes = [p, i]
+    L.gpmood_batch_create.argtypes = [C.POINTER(Grid), i, d, i, C.POINTER(d), C.POINTER(Options),
+                                      C.POINTER(p)]
+    L.gpmood_batch_set_stream.argtypes = [p, p]
+    L.gpmood_batch_set_state.argtypes = [p, p, i]
+    L.gpmood_batch_get_state.argtypes = [p, p, i]
+    L.gpmood_batch_step.argtypes = [p, d]
+    L.gpmood_batch_run.argtypes = [p, d, d, C.POINTER(C.c_longlong)]
+    L.gpmood_batch_info.argtypes = [p, p, p, p, C.POINTER(Stats)]
+    L.gpmood_batch_tuning.argtypes = [p, p, p]
+    L.gpmood_batch_profile.argtypes = [p, i]
+    L.gpmood_batch_kernel_times.argtypes = [p, p, p]
+    L.gpmood_batch_destroy.argtypes = [p]
     L.gpmood_step_noalloc.argtypes = [C.POINTER(Grid), d, i, d, C.POINTER(Options), p, p, d, d,
                                       C.POINTER(d), p]
     L.gpmood_kernel_times.argtypes = [p, p, p]
@@ -131,7 +143,7 @@ def make_options(prob, precision=FP64):
     o.precision = precision
     o.sigma_v, o.sigma_p = prob["sigma_v"], prob["sigma_p"]
     o.csd_off = 0 if prob["csd_on"] else 1
-    o.max_mood_iters = int(prob.get("max_iters", 64))
+    o.max_mood_iters = int(prob.get("max_iters", 0))
     return o
 
 
@@ -299,3 +311,100 @@ class GPMood:
 
     def kernel_times(self):
         return gpmood_kernel_times(self.h)
+
+
+class GPMoodBatch:
+    """Many independent problems advanced together (gpmood_batch_* ABI).
+
+    probs: problem dicts from ``inputs`` that share gamma, the cascade, the
+    options and ell/dx, ell/dy."""
+
+    def __init__(self, probs, precision="fp64"):
+        self.probs = list(probs)
+        self.n = len(self.probs)
+        self.shapes = [(int(q["ny"]), int(q["nx"])) for q in self.probs]
+        self.precision = FP32 if precision in ("fp32", FP32) else FP64
+        grids = (Grid * self.n)(*[make_grid(q) for q in self.probs])
+        ells = (C.c_double * self.n)(*[q["ell"] for q in self.probs])
+        q0 = self.probs[0]
+        opts = make_options(q0, self.precision)
+        h = C.c_void_p()
+        _check(load().gpmood_batch_create(grids, self.n, q0["gamma"], list(q0["cascade"])[0],
+                                          ells, C.byref(opts), C.byref(h)), "gpmood_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().gpmood_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        _check(load().gpmood_batch_set_stream(self.h, C.c_void_p(stream_ptr)), "set_stream")
+
+    def _flat(self, Us):
+        return np.ascontiguousarray(np.concatenate([np.asarray(U, dtype=np.float64).ravel()
+                                                    for U in Us]))
+
+    def set_state(self, Us):
+        """Us: list of (4, ny, nx) arrays, or one flat concatenated array / CUDA tensor."""
+        if hasattr(Us, "data_ptr") and getattr(Us, "is_cuda", False):
+            _check(load().gpmood_batch_set_state(self.h, C.c_void_p(Us.data_ptr()), 1), "set_state")
+            return
+        flat = Us if isinstance(Us, np.ndarray) and Us.ndim == 1 else self._flat(Us)
+        self._keep = flat
+        _check(load().gpmood_batch_set_state(self.h, flat.ctypes.data_as(C.c_void_p), 0),
+               "set_state")
+
+    def get_state(self):
+        total = sum(4 * ny * nx for ny, nx in self.shapes)
+        flat = np.zeros(total)
+        _check(load().gpmood_batch_get_state(self.h, flat.ctypes.data_as(C.c_void_p), 0),
+               "get_state")
+        out, off = [], 0
+        for ny, nx in self.shapes:
+            out.append(flat[off:off + 4 * ny * nx].reshape(4, ny, nx))
+            off += 4 * ny * nx
+        return out
+
+    def step(self, cfl=None):
+        _check(load().gpmood_batch_step(self.h, self.probs[0]["cfl"] if cfl is None else cfl),
+               "gpmood_batch_step")
+
+    def run(self, t_end, cfl=None):
+        n = C.c_longlong(0)
+        _check(load().gpmood_batch_run(self.h, t_end, self.probs[0]["cfl"] if cfl is None else cfl,
+                                       C.byref(n)), "gpmood_batch_run")
+        return n.value
+
+    def info(self):
+        t = np.zeros(self.n)
+        dt = np.zeros(self.n)
+        ns = np.zeros(self.n, dtype=np.int64)
+        st = Stats()
+        _check(load().gpmood_batch_info(self.h, t.ctypes.data_as(C.c_void_p),
+                                        dt.ctypes.data_as(C.c_void_p),
+                                        ns.ctypes.data_as(C.c_void_p), C.byref(st)), "info")
+        return t, dt, ns, dict(iters=list(st.iters), nbad_first=list(st.nbad_first),
+                               nbad_total=list(st.nbad_total))
+
+    def tuning(self):
+        w = (C.c_int * 2)()
+        b = (C.c_int * 2)()
+        rc = load().gpmood_batch_tuning(self.h, w, b)
+        return (list(w), list(b)) if rc == 0 else None
+
+    def profile(self, enable=True):
+        _check(load().gpmood_batch_profile(self.h, 1 if enable else 0), "profile")
+
+    def kernel_times(self):
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+        _check(load().gpmood_batch_kernel_times(self.h, ms.ctypes.data_as(C.c_void_p),
+                                                n.ctypes.data_as(C.c_void_p)), "kernel_times")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}

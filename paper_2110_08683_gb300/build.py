@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]
-CUDA_SOURCES = ["gpmood_api.cu", "kernels_f64.cu", "kernels_f32.cu"]
+CUDA_SOURCES = ["gpmood_api.cu", "gpmood_batch.cu", "kernels_f64.cu", "kernels_f32.cu"]
 C_SOURCES = ["gp_weights.c"]
 
 

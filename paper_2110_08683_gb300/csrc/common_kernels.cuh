@@ -7,64 +7,12 @@
 namespace gpm {
 
 __global__ void k_fill_ghosts(double* X, Grid g, const Scalars* sc, double tfrac) {
-  const int H = g.H;
-  const int nxg = g.nx + 2 * H;
-  const long long nxs = (long long)g.ny * 2 * H;  // x-ghosts of interior rows
-  const long long nys = (long long)2 * H * nxg;   // y-ghost rows
-  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= nxs + nys) return;
-  double S[4];
-  int i, j;
-  if (tid < nxs) {
-    j = (int)(tid / (2 * H));
-    int c = (int)(tid % (2 * H));
-    i = c < H ? -1 - c : g.nx + (c - H);
-    xghost(X, g, i, j, S);
-  } else {
-    long long u = tid - nxs;
-    int r = (int)(u / nxg);
-    i = (int)(u % nxg) - H;
-    int side = r < H ? 0 : 1;  // 0: south, 1: north
-    int k = r < H ? r + 1 : r - H + 1;
-    j = side == 0 ? -k : g.ny - 1 + k;
-    int kind = g.bc[2 + side];
-    double xc = g.x0 + (i + 0.5) * g.dx;
-    double t = sc->t + tfrac * sc->dt;
-    bool fixed = false, reflect = false;
-    const double* P = nullptr;
-    if (kind == 3) {
-      fixed = true;
-      P = g.bcU[2 + side];
-    } else if (kind == 4) {
-      if (xc < g.dmr_wall_x0) {
-        fixed = true;
-        P = g.dmr_post;
-      } else {
-        reflect = true;
-      }
-    } else if (kind == 5) {
-      fixed = true;
-      P = (xc < g.dmr_xs0 + g.dmr_xs_speed * t) ? g.dmr_post : g.dmr_pre;
-    } else if (kind == 2) {
-      reflect = true;
-    }
-    if (fixed) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) S[v] = P[v];
-    } else {
-      int src;
-      if (kind == 0) src = wrapi(j, g.ny);
-      else if (reflect) src = side == 0 ? k - 1 : g.ny - k;
-      else src = side == 0 ? 0 : g.ny - 1;
-      column_cell(X, g, i, src, S);
-      if (reflect) S[2] = -S[2];
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < 4; ++v) X[gidx(g, v, i, j)] = S[v];
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  fill_ghost(X, g, sc->t + tfrac * sc->dt, tid);
 }
 
-
+// time step: min over cells of min(dx/(|u|+c), dy/(|v|+c)), per-direction
+// CFL form; positive doubles order like their bit patterns
 __global__ void k_dt_reduce(const double* X, Grid g, Scalars* sc) {
   if (sc->ctl.fixed_dt > 0.0) return;
   double best = INFINITY;

@@ -12,8 +12,10 @@
 #include "common_kernels.cuh"
 #include "gp_weights.h"
 #include "gpmood_launch.h"
+#include "weight_tables.h"
 
 using namespace gpm;
+using gpm::fill_weights;
 
 struct gpmood_s {
   Grid g;
@@ -62,81 +64,6 @@ void prim_to_cons(const double* P, double gam, double* U) {
   U[1] = P[0] * P[1];
   U[2] = P[0] * P[2];
   U[3] = P[3] / (gam - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2]);
-}
-
-// index of offset (a,b) in the stencil order of gp_weights.c
-int sidx(const gpw_radius& w, int a, int b) {
-  for (int m = 0; m < w.n; ++m)
-    if (w.da[m] == a && w.db[m] == b) return m;
-  return -1;
-}
-
-template <class Real>
-void fill_weights(const gpw_radius* wr, int top, const double* d2x, const double* d2y,
-                  ParityW<Real>& P, DirectW<Real>& D) {
-  memset(&P, 0, sizeof(P));
-  memset(&D, 0, sizeof(D));
-  D.top = top;
-  D.w[0][0] = Real(1);
-  for (int m = 0; m < 5; ++m) {
-    D.d2x[m] = (Real)d2x[m];
-    D.d2y[m] = (Real)d2y[m];
-  }
-  for (int R = 1; R <= 3; ++R) {
-    const gpw_radius& w = wr[R];
-    if (w.n == 0) continue;
-    const int q = w.q;
-    for (int k = 0; k < q; ++k) D.w[R][k] = (Real)w.w[k];
-    // direct weights from the east / north solves at g >= 0 by the mirrors
-    for (int k = 0; k < q; ++k) {
-      const int kp = k < (q + 1) / 2 ? k : q - 1 - k;  // the +g point of the pair
-      const bool neg = k != kp;
-      for (int m = 0; m < w.n; ++m) {
-        int a = w.da[m], b = w.db[m];
-        // E at g: z_E(g)(a,b); E at -g: z_E(g)(a,-b); W: x-mirror of E
-        D.z[R][0][k][m] = (Real)w.z[0][kp][sidx(w, a, neg ? -b : b)];
-        D.z[R][1][k][m] = (Real)w.z[0][kp][sidx(w, -a, neg ? -b : b)];
-        // N at g: z_N(g)(a,b); N at -g: z_N(g)(-a,b); S: y-mirror of N
-        D.z[R][2][k][m] = (Real)w.z[1][kp][sidx(w, neg ? -a : a, b)];
-        D.z[R][3][k][m] = (Real)w.z[1][kp][sidx(w, neg ? -a : a, -b)];
-      }
-    }
-  }
-  // parity coefficients of the top radius
-  const int R = top;
-  if (R == 0) {
-    P.cx[0][0] = P.cy[0][0] = Real(1);
-    P.w[0] = Real(1);
-    return;
-  }
-  const gpw_radius& w = wr[R];
-  const int q = w.q, ns = (q + 1) / 2;
-  for (int k = 0; k < q; ++k) P.w[k] = (Real)w.w[k];
-  for (int kk = 0; kk < ns; ++kk) {
-    const bool middle = (q & 1) && kk == q / 2;
-    for (int c = 0; c < stencil_n(R); ++c) {
-      Comp cm = comp_at(R, c);
-      double ex = 0.0, ny = 0.0;
-      int cnt = 0;
-      for (int sa = 1; sa >= -1; sa -= 2) {
-        if (cm.a == 0 && sa < 0) continue;
-        for (int sb = 1; sb >= -1; sb -= 2) {
-          if (cm.b == 0 && sb < 0) continue;
-          double chi = (cm.px && sa < 0 ? -1.0 : 1.0) * (cm.py && sb < 0 ? -1.0 : 1.0);
-          ex += chi * w.z[0][kk][sidx(w, sa * cm.a, sb * cm.b)];
-          ny += chi * w.z[1][kk][sidx(w, sa * cm.a, sb * cm.b)];
-          ++cnt;
-        }
-      }
-      ex /= cnt;
-      ny /= cnt;
-      // at g = 0 the odd components across the face vanish exactly
-      if (middle && cm.py) ex = 0.0;
-      if (middle && cm.px) ny = 0.0;
-      P.cx[kk][c] = (Real)ex;
-      P.cy[kk][c] = (Real)ny;
-    }
-  }
 }
 
 int set_err(gpmood_t h, int code) {
@@ -563,7 +490,10 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
   h->det.delta = fmin(g.dx, g.dy);
   h->precision = o.precision;
-  h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters : 64;
+  // a safety net only: radii never rise, so the loop ends; chains of
+  // re-detected neighbours can take O(grid width) iterations
+  h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
+                                      : 64 + 4 * (grid->nx > grid->ny ? grid->nx : grid->ny);
 
   // GP weights of every radius of the cascade, binary128 -> double / float
   gpw_radius wr[4];
@@ -892,7 +822,10 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
   h->det.delta = fmin(g.dx, g.dy);
   h->precision = o.precision;
-  h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters : 64;
+  // a safety net only: radii never rise, so the loop ends; chains of
+  // re-detected neighbours can take O(grid width) iterations
+  h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
+                                      : 64 + 4 * (grid->nx > grid->ny ? grid->nx : grid->ny);
 
   // GP weights: binary128 solve on the host stack
   gpw_radius wr[4];

@@ -1,0 +1,784 @@
+// gpmood_batch.cu -- many independent GP-MOOD problems of uneven sizes
+// advanced together (include/gpmood.h, gpmood_batch_*): pooled buffers, one
+// persistent launch per kernel class walking (problem, block) work items,
+// one captured graph per step with the MOOD loops as conditional WHILE
+// nodes, per-problem time steps, and a small autotuner for the face kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/gpmood.h"
+#include "gp_weights.h"
+#include "gpmood_kernels.cuh"
+#include "gpmood_launch.h"
+#include "weight_tables.h"
+
+using namespace gpm;
+
+namespace gpm {
+
+// per-problem time-step reduction over (problem, chunk) items
+__global__ void k_dt_reduce_batch(const double* X, const Prob* probs, Scalars* psc, Scalars* gsc,
+                                  const Item* items, int nitems) {
+  if (gsc->ctl.fixed_dt > 0.0) return;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const Item w = items[it];
+    const Prob& P = probs[w.p];
+    const Grid& g = P.g;
+    const double* Xp = X + P.state_off;
+    double best = INFINITY;
+    bool bad = false;
+    const long long c0 = (long long)w.a * 4096;
+    const long long c1 = c0 + 4096 < (long long)P.ncell ? c0 + 4096 : (long long)P.ncell;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      int i = (int)(c % g.nx), j = (int)(c / g.nx);
+      double S[4];
+      load_cell(Xp, g, i, j, S);
+      double r = S[0], u = S[1] / r, v = S[2] / r;
+      double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * S[1] + S[2] * S[2]) / r);
+      double cs = sqrt(g.gamma * p / r);
+      double ax = g.dx / (fabs(u) + cs);
+      double ay = g.dy / (fabs(v) + cs);
+      double a = ax < ay ? ax : ay;
+      if (!(a > 0.0) || !isfinite(a)) bad = true;
+      else best = a < best ? a : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ob < best ? ob : best;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+      if (bad) atomicOr(&gsc->err, kErrDt);
+      if (best < INFINITY)
+        atomicMin(&psc[w.p].dtmin_bits, (unsigned long long)__double_as_longlong(best));
+    }
+  }
+}
+
+// per-problem step: given dt, or CFL clipped to t_end; a problem already at
+// t_end gets dt = 0 and only carries its state over
+__global__ void k_dt_finalize_batch(Scalars* psc, Scalars* gsc, int nprob) {
+  const Control c = gsc->ctl;
+  for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+    Scalars& s = psc[p];
+    double dt;
+    bool active = true;
+    if (c.clip && !(s.t < c.t_end * (1.0 - 1e-14))) {
+      dt = 0.0;
+      active = false;
+    } else if (c.fixed_dt > 0.0) {
+      dt = c.fixed_dt;
+    } else {
+      dt = c.cfl * __longlong_as_double((long long)s.dtmin_bits);
+      if (c.clip && s.t + dt > c.t_end) dt = c.t_end - s.t;
+    }
+    if (active && (!(dt > 0.0) || !isfinite(dt))) atomicOr(&gsc->err, kErrDt);
+    s.dt = dt;
+    s.dtmin_bits = 0x7ff0000000000000ull;
+    if (active) atomicAdd(&gsc->nactive, 1);
+  }
+}
+
+__global__ void k_batch_reset(Scalars* gsc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int s = 0; s < 3; ++s) {
+    gsc->iters[s] = 0;
+    gsc->nbad_first[s] = 0;
+    gsc->nbad_total[s] = 0;
+    gsc->nfog_pad[s] = 0;
+  }
+  gsc->count[0] = gsc->count[1] = 0;
+  gsc->nactive = 0;
+}
+
+__global__ void k_fill_batch(double* X, const Prob* probs, const Scalars* psc, double tfrac,
+                             int nprob) {
+  const int p = blockIdx.y;
+  if (p >= nprob) return;
+  const Prob& P = probs[p];
+  const double t = psc[p].t + tfrac * psc[p].dt;
+  const long long n = ghost_count(P.g);
+  for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < n;
+       tid += (long long)gridDim.x * blockDim.x)
+    fill_ghost(X + P.state_off, P.g, t, tid);
+}
+
+__global__ void k_finish_batch(Scalars* psc, int nprob) {
+  for (int p = threadIdx.x; p < nprob; p += blockDim.x) {
+    psc[p].t += psc[p].dt;
+    if (psc[p].dt > 0.0) psc[p].nsteps += 1;
+  }
+}
+
+}  // namespace gpm
+
+struct gpmood_batch_s {
+  int nprob, top, precision, max_iters;
+  Cascade cas;
+  std::vector<Prob> hprobs;
+  long long state_elems, fx_elems, fy_elems;
+  int total_cells;
+  cudaStream_t stream, cs, cs2;
+  double* U[3];
+  void *Fx, *Fy;
+  uint8_t *cad, *ord, *first;
+  uint32_t* stamp;
+  int* queue[2];
+  Prob* probs;
+  Scalars *psc, *gsc;  // device: per problem and global
+  Scalars* hgsc;       // pinned host mirror of the global scalars
+  Item *items_fx[2], *items_fy[2], *items_up, *items_dt;  // [fw 4, fw 8]
+  int n_fx[2], n_fy[2], n_up, n_dt;
+  ParityW<double> pw64;
+  ParityW<float> pw32;
+  DirectW<double> dw64;
+  DirectW<float> dw32;
+  Control ctl;
+  int cur, has_state;
+  // face-kernel variant per sweep (warps per block 4 or 8, persistent blocks)
+  int tuned, fw[2], blocks[2];
+  int up_blocks, dt_blocks, fill_blocks_x;
+  cudaGraphExec_t gexec[3][2];
+  int prof_on;
+  cudaEvent_t gev[64];
+  int gev_cls[32], gev_n, gev_pairs;
+  double prof_ms[GPMOOD_NKCLASS];
+  long long prof_n[GPMOOD_NKCLASS];
+};
+
+namespace {
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+void prim_to_cons(const double* P, double gam, double* U) {
+  U[0] = P[0];
+  U[1] = P[0] * P[1];
+  U[2] = P[0] * P[2];
+  U[3] = P[3] / (gam - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2]);
+}
+
+#define CKB(call)                               \
+  do {                                          \
+    if ((call) != cudaSuccess) return GPMOOD_E_CUDA; \
+  } while (0)
+
+void batch_free(gpmood_batch_t b) {
+  for (int k = 0; k < 64; ++k)
+    if (b->gev[k]) cudaEventDestroy(b->gev[k]);
+  for (int r = 0; r < 3; ++r)
+    for (int p = 0; p < 2; ++p)
+      if (b->gexec[r][p]) cudaGraphExecDestroy(b->gexec[r][p]);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  if (b->cs2) cudaStreamDestroy(b->cs2);
+  for (int k = 0; k < 3; ++k) cudaFree(b->U[k]);
+  void* ptrs[] = {b->Fx, b->Fy, b->cad, b->ord, b->first, b->stamp, b->queue[0], b->queue[1],
+                  b->probs, b->psc, b->gsc, b->items_fx[0], b->items_fx[1], b->items_fy[0],
+                  b->items_fy[1], b->items_up, b->items_dt};
+  for (void* p : ptrs) cudaFree(p);
+  if (b->hgsc) cudaFreeHost(b->hgsc);
+}
+
+int upload_items(const std::vector<Item>& v, Item** out, int* n) {
+  *n = (int)v.size();
+  if (v.empty()) return 0;
+  CKB(cudaMalloc(out, sizeof(Item) * v.size()));
+  CKB(cudaMemcpy(*out, v.data(), sizeof(Item) * v.size(), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+template <class Real>
+StageArgs<Real> batch_args(gpmood_batch_t b, int s, int ia, int ix, int io) {
+  StageArgs<Real> A;
+  A.X = b->U[ix];
+  A.U0 = b->U[ia];
+  A.out = b->U[io];
+  A.Fx = (Real*)b->Fx;
+  A.Fy = (Real*)b->Fy;
+  A.cad = b->cad;
+  A.ord = b->ord + (size_t)s * b->total_cells;
+  A.first = b->first + (size_t)s * b->total_cells;
+  A.queue = b->queue[0];
+  A.qcount = &b->gsc->count[0];
+  A.sc = b->psc;
+  A.scw = b->gsc;
+  A.stage = s;
+  return A;
+}
+
+int pull(gpmood_batch_t b) {
+  CKB(cudaMemcpyAsync(b->hgsc, b->gsc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream));
+  CKB(cudaStreamSynchronize(b->stream));
+  return 0;
+}
+
+int launch_dt_batch(gpmood_batch_t b, int ia, cudaStream_t st) {
+  k_batch_reset<<<1, 32, 0, st>>>(b->gsc);
+  k_dt_reduce_batch<<<b->dt_blocks, 256, 0, st>>>(b->U[ia], b->probs, b->psc, b->gsc, b->items_dt,
+                                                  b->n_dt);
+  k_dt_finalize_batch<<<1, 256, 0, st>>>(b->psc, b->gsc, b->nprob);
+  return cudaGetLastError() == cudaSuccess ? 0 : GPMOOD_E_CUDA;
+}
+
+int launch_fill_batch(gpmood_batch_t b, int ix, int s, cudaStream_t st) {
+  static const double tfrac[3] = {0.0, 1.0, 0.5};
+  k_fill_batch<<<dim3(b->fill_blocks_x, b->nprob), 256, 0, st>>>(b->U[ix], b->probs, b->psc,
+                                                                  tfrac[s], b->nprob);
+  return cudaGetLastError() == cudaSuccess ? 0 : GPMOOD_E_CUDA;
+}
+
+template <class Real>
+int launch_faces_batch(gpmood_batch_t b, int dir, const StageArgs<Real>& A,
+                       const ParityW<Real>& P, int fw, int blocks, cudaStream_t st) {
+  const int k = fw == 4 ? 0 : 1;
+  Item* items = dir == 0 ? b->items_fx[k] : b->items_fy[k];
+  int n = dir == 0 ? b->n_fx[k] : b->n_fy[k];
+  return LaunchB<Real>::faces(b->top, dir, fw, A, b->probs, b->psc, items, n, blocks, P, st) ==
+                 cudaSuccess
+             ? 0
+             : GPMOOD_E_CUDA;
+}
+
+// the autotuner: time both face-kernel variants (4 or 8 warps per block,
+// i.e. 4 or 8 rows per item) on the first stage of the current state and
+// keep the faster per sweep
+template <class Real>
+int tune(gpmood_batch_t b, const ParityW<Real>& P) {
+  int rc = launch_dt_batch(b, b->cur, b->stream);
+  if (rc) return rc;
+  rc = launch_fill_batch(b, b->cur, 0, b->stream);
+  if (rc) return rc;
+  StageArgs<Real> A = batch_args<Real>(b, 0, b->cur, b->cur, (b->cur + 1) % 3);
+  cudaEvent_t e0, e1;
+  CKB(cudaEventCreate(&e0));
+  CKB(cudaEventCreate(&e1));
+  for (int dir = 0; dir < 2; ++dir) {
+    float best = 1e30f;
+    for (int fw : {4, 8}) {
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, b->stream);
+        rc = launch_faces_batch<Real>(b, dir, A, P, fw, 0, b->stream);
+        cudaEventRecord(e1, b->stream);
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < ms_min) ms_min = ms;  // the first run warms up
+      }
+      if (rc) break;
+      if (ms_min < best) {
+        best = ms_min;
+        b->fw[dir] = fw;
+        b->blocks[dir] = dir == 0 ? b->n_fx[fw == 4 ? 0 : 1] : b->n_fy[fw == 4 ? 0 : 1];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  b->tuned = 1;
+  return 0;
+}
+
+void rec(gpmood_batch_t b, int prof, int cls, int open, cudaStream_t st) {
+  if (!prof) return;
+  int k = b->gev_n;
+  cudaEventRecordWithFlags(b->gev[k], st, cudaEventRecordExternal);
+  if (!open) b->gev_cls[(k - 1) / 2] = cls;
+  b->gev_n = k + 1;
+}
+
+template <class Real>
+int capture_stage_b(gpmood_batch_t b, int s, int ia, int ix, int io, const ParityW<Real>& P,
+                    const DirectW<Real>& D, int prof) {
+  cudaStream_t st = b->cs;
+  StageArgs<Real> A = batch_args<Real>(b, s, ia, ix, io);
+  rec(b, prof, GPMOOD_K_GHOST, 1, st);
+  if (launch_fill_batch(b, ix, s, st)) return GPMOOD_E_CUDA;
+  rec(b, prof, GPMOOD_K_GHOST, 0, st);
+  rec(b, prof, GPMOOD_K_FACES_X, 1, st);
+  if (launch_faces_batch<Real>(b, 0, A, P, b->fw[0], b->blocks[0], st)) return GPMOOD_E_CUDA;
+  rec(b, prof, GPMOOD_K_FACES_X, 0, st);
+  rec(b, prof, GPMOOD_K_FACES_Y, 1, st);
+  if (launch_faces_batch<Real>(b, 1, A, P, b->fw[1], b->blocks[1], st)) return GPMOOD_E_CUDA;
+  rec(b, prof, GPMOOD_K_FACES_Y, 0, st);
+  rec(b, prof, GPMOOD_K_UPDATE, 1, st);
+  int nb = b->up_blocks < b->n_up ? b->up_blocks : b->n_up;
+  CKB(LaunchB<Real>::update(A, b->probs, b->psc, b->items_up, b->n_up, nb, D, st));
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+  cudaGraphConditionalHandle hc;
+  CKB(cudaGraphConditionalHandleCreate(&hc, graph, 0, cudaGraphCondAssignDefault));
+  CKB(launch_mood_begin(b->gsc, s, hc, 1, st));
+  rec(b, prof, GPMOOD_K_UPDATE, 0, st);
+  rec(b, prof, GPMOOD_K_MOOD, 1, st);
+  CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CKB(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CKB(cudaStreamBeginCaptureToGraph(b->cs2, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal));
+  MoodArgs M;
+  M.queue[0] = b->queue[0];
+  M.queue[1] = b->queue[1];
+  M.stamp = b->stamp;
+  M.sc = b->gsc;
+  cudaError_t e1 = launch_lower(M, A.ord, b->cas, b->cs2);
+  cudaError_t e2 = LaunchB<Real>::mood_faces(A, M, b->probs, b->psc, b->nprob, D, b->cas, b->cs2);
+  cudaError_t e3 = LaunchB<Real>::mood_update(A, M, b->probs, b->psc, b->nprob, D, b->cs2);
+  cudaError_t e4 = launch_mood_end(b->gsc, s, hc, 1, b->cs2);
+  cudaGraph_t tmp;
+  CKB(cudaStreamEndCapture(b->cs2, &tmp));
+  CKB(e1);
+  CKB(e2);
+  CKB(e3);
+  CKB(e4);
+  CKB(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  rec(b, prof, GPMOOD_K_MOOD, 0, st);
+  return 0;
+}
+
+int capture_b(gpmood_batch_t b, int cur, int prof, cudaGraphExec_t* out) {
+  const int a = cur, bb = (a + 1) % 3, c = (a + 2) % 3;
+  const int in[3] = {a, bb, c}, outb[3] = {bb, c, bb};
+  cudaStream_t st = b->cs;
+  b->gev_n = 0;
+  CKB(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = 0;
+  rec(b, prof, GPMOOD_K_DT, 1, st);
+  rc = launch_dt_batch(b, a, st);
+  rec(b, prof, GPMOOD_K_DT, 0, st);
+  for (int s = 0; s < 3 && !rc; ++s)
+    rc = b->precision == GPMOOD_FP32
+             ? capture_stage_b<float>(b, s, a, in[s], outb[s], b->pw32, b->dw32, prof)
+             : capture_stage_b<double>(b, s, a, in[s], outb[s], b->pw64, b->dw64, prof);
+  if (!rc) {
+    k_finish_batch<<<1, 256, 0, st>>>(b->psc, b->nprob);
+    if (cudaGetLastError() != cudaSuccess) rc = GPMOOD_E_CUDA;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(st, &graph);
+  if (!rc && ee != cudaSuccess) rc = GPMOOD_E_CUDA;
+  if (!rc && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) rc = GPMOOD_E_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  if (!rc && prof) b->gev_pairs = b->gev_n / 2;
+  return rc;
+}
+
+int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t_end) {
+  if (!b->has_state) return GPMOOD_E_NOSTATE;
+  b->ctl.cfl = cfl;
+  b->ctl.fixed_dt = fixed_dt;
+  b->ctl.clip = clip;
+  b->ctl.t_end = t_end;
+  b->ctl.max_iters = b->max_iters;
+  CKB(cudaMemcpyAsync(&b->gsc->ctl, &b->ctl, sizeof(Control), cudaMemcpyHostToDevice, b->stream));
+  if (!b->tuned) {
+    int rc = b->precision == GPMOOD_FP32 ? tune<float>(b, b->pw32) : tune<double>(b, b->pw64);
+    if (rc) return rc;
+  }
+  const int prof = b->prof_on ? 1 : 0;
+  cudaGraphExec_t& ge = b->gexec[b->cur][prof];
+  if (!ge) {
+    int rc = capture_b(b, b->cur, prof, &ge);
+    if (rc) return rc;
+  }
+  CKB(cudaGraphLaunch(ge, b->stream));
+  int rc = pull(b);
+  if (rc) return rc;
+  if (prof) {
+    for (int k = 0; k < b->gev_pairs; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, b->gev[2 * k], b->gev[2 * k + 1]) == cudaSuccess)
+        b->prof_ms[b->gev_cls[k]] += ms;
+    }
+    for (int k = GPMOOD_K_GHOST; k <= GPMOOD_K_FACES_Y; ++k) b->prof_n[k] += 3;
+    b->prof_n[GPMOOD_K_DT] += 5;
+    b->prof_n[GPMOOD_K_UPDATE] += 6;
+    const Scalars& s = *b->hgsc;
+    b->prof_n[GPMOOD_K_MOOD] += 4 * (s.iters[0] + s.iters[1] + s.iters[2]);
+  }
+  if (b->hgsc->err & kErrDt) return GPMOOD_E_DT;
+  if (b->hgsc->err & kErrCap) return GPMOOD_E_MOOD_CAP;
+  b->cur = (b->cur + 1) % 3;
+  return GPMOOD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R_max,
+                        const double* ell, const gpmood_options* opts, gpmood_batch_t* out) {
+  if (!out) return GPMOOD_E_INVAL;
+  *out = nullptr;
+  if (!grids || !ell || nprob < 1 || R_max < 0 || R_max > 3 || !(gamma > 1.0))
+    return GPMOOD_E_INVAL;
+  gpmood_options o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  int cascade[4], nc = 0;
+  if (o.ncascade == 0) {
+    for (int r = R_max; r >= 0; --r) cascade[nc++] = r;
+  } else {
+    if (o.ncascade < 1 || o.ncascade > 4) return GPMOOD_E_INVAL;
+    nc = o.ncascade;
+    for (int k = 0; k < nc; ++k) cascade[k] = o.cascade[k];
+    if (cascade[0] != R_max || cascade[nc - 1] != 0) return GPMOOD_E_INVAL;
+    for (int k = 0; k + 1 < nc; ++k)
+      if (!(cascade[k] > cascade[k + 1])) return GPMOOD_E_INVAL;
+  }
+  if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
+  const int H = R_max + 1 > 2 ? R_max + 1 : 2;
+  const int minn = H > 3 ? H : 3;
+  // every problem shares the weights: the same ell/dx and ell/dy
+  double lx0 = 0, ly0 = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const gpmood_grid* gr = &grids[p];
+    if (gr->nx < minn || gr->ny < minn || !(gr->x1 > gr->x0) || !(gr->y1 > gr->y0) ||
+        !(ell[p] > 0.0))
+      return GPMOOD_E_INVAL;
+    for (int s = 0; s < 4; ++s) {
+      int k = gr->bc[s];
+      if (k < 0 || k > 5 || (k == GPMOOD_BC_DMR_BOTTOM && s != 2) ||
+          (k == GPMOOD_BC_DMR_TOP && s != 3))
+        return GPMOOD_E_INVAL;
+    }
+    if ((gr->bc[0] == 0) != (gr->bc[1] == 0) || (gr->bc[2] == 0) != (gr->bc[3] == 0))
+      return GPMOOD_E_INVAL;
+    const double lx = ell[p] * gr->nx / (gr->x1 - gr->x0), ly = ell[p] * gr->ny / (gr->y1 - gr->y0);
+    if (p == 0) {
+      lx0 = lx;
+      ly0 = ly;
+    } else if (fabs(lx - lx0) > 1e-12 * lx0 || fabs(ly - ly0) > 1e-12 * ly0) {
+      return GPMOOD_E_INVAL;
+    }
+  }
+  gpmood_batch_t b = new (std::nothrow) gpmood_batch_s();
+  if (!b) return GPMOOD_E_OOM;
+  b->nprob = nprob;
+  b->top = R_max;
+  b->precision = o.precision;
+  int widest = 0;
+  for (int p = 0; p < nprob; ++p) {
+    widest = grids[p].nx > widest ? grids[p].nx : widest;
+    widest = grids[p].ny > widest ? grids[p].ny : widest;
+  }
+  b->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters : 64 + 4 * widest;
+  for (int r = 0; r < 4; ++r) b->cas.next[r] = b->cas.prev[r] = r;
+  for (int k = 0; k + 1 < nc; ++k) {
+    b->cas.next[cascade[k]] = cascade[k + 1];
+    b->cas.prev[cascade[k + 1]] = cascade[k];
+  }
+  b->cas.top = R_max;
+  // per-problem descriptors and pooled offsets
+  b->hprobs.resize(nprob);
+  long long soff = 0, fxo = 0, fyo = 0;
+  int coff = 0;
+  const size_t fsz = b->precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  std::vector<Item> fx4, fx8, fy4, fy8, up, dtl;
+  long long max_ghost = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const gpmood_grid* gr = &grids[p];
+    Prob& P = b->hprobs[p];
+    memset(&P, 0, sizeof(P));
+    Grid& g = P.g;
+    g.nx = gr->nx;
+    g.ny = gr->ny;
+    g.H = H;
+    g.pitch = round_up(g.nx + 2 * H, 32);
+    g.gy = g.ny + 2 * H;
+    g.vstride = (long long)g.pitch * g.gy;
+    g.dx = (gr->x1 - gr->x0) / g.nx;
+    g.dy = (gr->y1 - gr->y0) / g.ny;
+    g.inv_dx = 1.0 / g.dx;
+    g.inv_dy = 1.0 / g.dy;
+    g.x0 = gr->x0;
+    g.y0 = gr->y0;
+    g.gamma = gamma;
+    for (int s = 0; s < 4; ++s) {
+      g.bc[s] = gr->bc[s];
+      prim_to_cons(gr->bc_prim[s], gamma, g.bcU[s]);
+    }
+    g.periodic_x = gr->bc[0] == GPMOOD_BC_PERIODIC;
+    g.periodic_y = gr->bc[2] == GPMOOD_BC_PERIODIC;
+    prim_to_cons(gr->dmr_post, gamma, g.dmr_post);
+    prim_to_cons(gr->dmr_pre, gamma, g.dmr_pre);
+    g.dmr_wall_x0 = gr->dmr_wall_x0;
+    g.dmr_xs0 = gr->dmr_xs0;
+    g.dmr_xs_speed = gr->dmr_xs_speed;
+    P.det.sigma_v = o.sigma_v > 0 ? o.sigma_v : 5.0;
+    P.det.sigma_p = o.sigma_p > 0 ? o.sigma_p : 5.0;
+    P.det.csd_on = o.csd_off ? 0 : 1;
+    P.det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
+    P.det.delta = fmin(g.dx, g.dy);
+    int da[25], db[25];
+    double d2x[25], d2y[25];
+    if (gpw_second_derivative(g.dx, g.dy, ell[p], da, db, d2x, d2y) != 5) {
+      delete b;
+      return GPMOOD_E_WEIGHTS;
+    }
+    for (int m = 0; m < 5; ++m) {
+      P.d2x[m] = d2x[m];
+      P.d2y[m] = d2y[m];
+      P.d2xf[m] = (float)d2x[m];
+      P.d2yf[m] = (float)d2y[m];
+    }
+    P.state_off = soff;
+    P.fx_off = fxo;
+    P.fy_off = fyo;
+    P.cell_off = coff;
+    P.ncell = g.nx * g.ny;
+    soff += 4 * g.vstride;
+    soff = (soff + 31) / 32 * 32;
+    fxo += 4LL * g.ny * (g.nx + 1);
+    fxo = (fxo + 31) / 32 * 32;
+    fyo += 4LL * (g.ny + 1) * g.nx;
+    fyo = (fyo + 31) / 32 * 32;
+    coff += P.ncell;
+    // work items
+    for (int fw : {4, 8}) {
+      auto& vx = fw == 4 ? fx4 : fx8;
+      auto& vy = fw == 4 ? fy4 : fy8;
+      const int sx = (g.nx + 1 + kSegFaces - 1) / kSegFaces, bx = (g.ny + fw - 1) / fw;
+      for (int b2 = 0; b2 < bx; ++b2)
+        for (int s2 = 0; s2 < sx; ++s2) vx.push_back(Item{p, s2, b2, 0});
+      const int sy = (g.ny + 1 + kSegFaces - 1) / kSegFaces, by = (g.nx + fw - 1) / fw;
+      for (int b2 = 0; b2 < by; ++b2)
+        for (int s2 = 0; s2 < sy; ++s2) vy.push_back(Item{p, s2, b2, 0});
+    }
+    for (int by = 0; by < (g.ny + 7) / 8; ++by)
+      for (int bx = 0; bx < (g.nx + 31) / 32; ++bx) up.push_back(Item{p, bx, by, 0});
+    for (int ch = 0; ch < (P.ncell + 4095) / 4096; ++ch) dtl.push_back(Item{p, ch, 0, 0});
+    long long ngh = (long long)g.ny * 2 * H + 2LL * H * (g.nx + 2 * H);
+    if (ngh > max_ghost) max_ghost = ngh;
+  }
+  b->state_elems = soff;
+  b->fx_elems = fxo;
+  b->fy_elems = fyo;
+  b->total_cells = coff;
+  b->fill_blocks_x = (int)((max_ghost + 255) / 256);
+  if (b->fill_blocks_x > 64) b->fill_blocks_x = 64;
+  // weights (shared): solve on the first grid
+  {
+    const Grid& g0 = b->hprobs[0].g;
+    gpw_radius wr[4];
+    memset(wr, 0, sizeof(wr));
+    for (int k = 0; k < nc; ++k) {
+      int R = cascade[k];
+      if (R == 0) continue;
+      if (gpw_solve(R, g0.dx, g0.dy, ell[0], &wr[R]) != 0) {
+        delete b;
+        return GPMOOD_E_WEIGHTS;
+      }
+    }
+    const Prob& P0 = b->hprobs[0];
+    fill_weights<double>(wr, R_max, P0.d2x, P0.d2y, b->pw64, b->dw64);
+    fill_weights<float>(wr, R_max, P0.d2x, P0.d2y, b->pw32, b->dw32);
+  }
+  const size_t nc_all = (size_t)b->total_cells;
+  bool ok = true;
+  for (int k = 0; k < 3; ++k)
+    ok = ok && cudaMalloc(&b->U[k], sizeof(double) * (size_t)b->state_elems) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->Fx, fsz * (size_t)b->fx_elems) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->Fy, fsz * (size_t)b->fy_elems) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->cad, nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->ord, 3 * nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->first, 3 * nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->stamp, 4 * nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->queue[0], 4 * nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->queue[1], 4 * nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->probs, sizeof(Prob) * nprob) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->psc, sizeof(Scalars) * nprob) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->gsc, sizeof(Scalars)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->hgsc, sizeof(Scalars)) == cudaSuccess;
+  ok = ok && upload_items(fx4, &b->items_fx[0], &b->n_fx[0]) == 0;
+  ok = ok && upload_items(fx8, &b->items_fx[1], &b->n_fx[1]) == 0;
+  ok = ok && upload_items(fy4, &b->items_fy[0], &b->n_fy[0]) == 0;
+  ok = ok && upload_items(fy8, &b->items_fy[1], &b->n_fy[1]) == 0;
+  ok = ok && upload_items(up, &b->items_up, &b->n_up) == 0;
+  ok = ok && upload_items(dtl, &b->items_dt, &b->n_dt) == 0;
+  ok = ok && cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->cs2, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < 64 && ok; ++k) ok = cudaEventCreate(&b->gev[k]) == cudaSuccess;
+  if (ok)
+    ok = cudaMemcpy(b->probs, b->hprobs.data(), sizeof(Prob) * nprob, cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemset(b->cad, 0, nc_all) == cudaSuccess &&
+         cudaMemset(b->ord, 0, 3 * nc_all) == cudaSuccess &&
+         cudaMemset(b->first, 0, 3 * nc_all) == cudaSuccess &&
+         cudaMemset(b->stamp, 0, 4 * nc_all) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+  for (int k = 0; k < 3 && ok; ++k)
+    ok = cudaMemset(b->U[k], 0, sizeof(double) * (size_t)b->state_elems) == cudaSuccess;
+  if (!ok) {
+    batch_free(b);
+    delete b;
+    cudaGetLastError();
+    return GPMOOD_E_OOM;
+  }
+  b->up_blocks = 152 * 8;
+  b->dt_blocks = b->n_dt < 152 * 4 ? b->n_dt : 152 * 4;
+  b->fw[0] = b->fw[1] = 8;
+  b->blocks[0] = b->blocks[1] = 152 * 2;
+  b->stream = nullptr;
+  *out = b;
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_set_stream(gpmood_batch_t b, void* stream) {
+  if (!b) return GPMOOD_E_INVAL;
+  b->stream = (cudaStream_t)stream;
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_set_state(gpmood_batch_t b, const double* U, int on_device) {
+  if (!b || !U) return GPMOOD_E_INVAL;
+  b->cur = 0;
+  size_t off = 0;
+  for (int p = 0; p < b->nprob; ++p) {
+    const Prob& P = b->hprobs[p];
+    const Grid& g = P.g;
+    for (int v = 0; v < 4; ++v) {
+      double* dst = b->U[0] + P.state_off + v * g.vstride + (size_t)g.H * g.pitch + g.H;
+      CKB(cudaMemcpy2DAsync(dst, sizeof(double) * g.pitch, U + off, sizeof(double) * g.nx,
+                            sizeof(double) * g.nx, g.ny,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            b->stream));
+      off += (size_t)g.nx * g.ny;
+    }
+  }
+  std::vector<Scalars> z(b->nprob);
+  for (auto& s : z) {
+    memset(&s, 0, sizeof(s));
+    s.dtmin_bits = 0x7ff0000000000000ull;
+  }
+  CKB(cudaMemcpyAsync(b->psc, z.data(), sizeof(Scalars) * b->nprob, cudaMemcpyHostToDevice,
+                      b->stream));
+  CKB(cudaMemcpyAsync(b->gsc, z.data(), sizeof(Scalars), cudaMemcpyHostToDevice, b->stream));
+  CKB(cudaMemsetAsync(b->stamp, 0, 4 * (size_t)b->total_cells, b->stream));
+  CKB(cudaStreamSynchronize(b->stream));
+  b->has_state = 1;
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_get_state(gpmood_batch_t b, double* U, int on_device) {
+  if (!b || !U) return GPMOOD_E_INVAL;
+  if (!b->has_state) return GPMOOD_E_NOSTATE;
+  size_t off = 0;
+  for (int p = 0; p < b->nprob; ++p) {
+    const Prob& P = b->hprobs[p];
+    const Grid& g = P.g;
+    for (int v = 0; v < 4; ++v) {
+      const double* src = b->U[b->cur] + P.state_off + v * g.vstride + (size_t)g.H * g.pitch + g.H;
+      CKB(cudaMemcpy2DAsync(U + off, sizeof(double) * g.nx, src, sizeof(double) * g.pitch,
+                            sizeof(double) * g.nx, g.ny,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            b->stream));
+      off += (size_t)g.nx * g.ny;
+    }
+  }
+  CKB(cudaStreamSynchronize(b->stream));
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_step(gpmood_batch_t b, double cfl) {
+  if (!b || !(cfl > 0.0)) return GPMOOD_E_INVAL;
+  return batch_step(b, cfl, 0.0, 0, 0.0);
+}
+
+int gpmood_batch_run(gpmood_batch_t b, double t_end, double cfl, long long* nsteps_out) {
+  if (!b || !(cfl > 0.0)) return GPMOOD_E_INVAL;
+  long long n = 0;
+  for (;;) {
+    int rc = batch_step(b, cfl, 0.0, 1, t_end);
+    if (rc) return rc;
+    if (b->hgsc->nactive == 0) break;
+    ++n;
+  }
+  if (nsteps_out) *nsteps_out = n;
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_info(gpmood_batch_t b, double* t, double* dt, long long* nsteps,
+                      gpmood_stats* total) {
+  if (!b) return GPMOOD_E_INVAL;
+  std::vector<Scalars> s(b->nprob);
+  CKB(cudaMemcpyAsync(s.data(), b->psc, sizeof(Scalars) * b->nprob, cudaMemcpyDeviceToHost,
+                      b->stream));
+  int rc = pull(b);
+  if (rc) return rc;
+  for (int p = 0; p < b->nprob; ++p) {
+    if (t) t[p] = s[p].t;
+    if (dt) dt[p] = s[p].dt;
+    if (nsteps) nsteps[p] = s[p].nsteps;
+  }
+  if (total) {
+    memset(total, 0, sizeof(*total));
+    const Scalars& g = *b->hgsc;
+    for (int k = 0; k < 3; ++k) {
+      total->iters[k] = g.iters[k];
+      total->nbad_first[k] = g.nbad_first[k];
+      total->nbad_total[k] = g.nbad_total[k];
+      total->nfog_pad[k] = g.nfog_pad[k];
+    }
+    total->status = GPMOOD_OK;
+  }
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_tuning(gpmood_batch_t b, int* warps, int* blocks) {
+  if (!b) return GPMOOD_E_INVAL;
+  for (int d = 0; d < 2; ++d) {
+    if (warps) warps[d] = b->fw[d];
+    if (blocks) blocks[d] = b->blocks[d];
+  }
+  return b->tuned ? GPMOOD_OK : GPMOOD_E_NOSTATE;
+}
+
+int gpmood_batch_profile(gpmood_batch_t b, int enable) {
+  if (!b) return GPMOOD_E_INVAL;
+  CKB(cudaStreamSynchronize(b->stream));
+  b->prof_on = enable ? 1 : 0;
+  if (enable)
+    for (int k = 0; k < GPMOOD_NKCLASS; ++k) {
+      b->prof_ms[k] = 0.0;
+      b->prof_n[k] = 0;
+    }
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_kernel_times(gpmood_batch_t b, double* ms, long long* launches) {
+  if (!b) return GPMOOD_E_INVAL;
+  CKB(cudaStreamSynchronize(b->stream));
+  for (int k = 0; k < GPMOOD_NKCLASS; ++k) {
+    if (ms) ms[k] = b->prof_ms[k];
+    if (launches) launches[k] = b->prof_n[k];
+  }
+  return GPMOOD_OK;
+}
+
+int gpmood_batch_destroy(gpmood_batch_t b) {
+  if (!b) return GPMOOD_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  batch_free(b);
+  delete b;
+  return GPMOOD_OK;
+}
+
+}  // extern "C"

@@ -50,6 +50,7 @@ struct Scalars {
   unsigned int stamp_cur;       // stamp of the cells in the current queue
   int iters[3], nbad_first[3], nbad_total[3], nfog_pad[3];
   long long nsteps;
+  int nactive;                  // batches: problems still advancing in this step
 };
 
 constexpr int kErrDt = 1;       // non-finite or non-positive time step
@@ -112,6 +113,24 @@ struct MoodArgs {
   int* queue[2];
   uint32_t* stamp;
   Scalars* sc;
+};
+
+// one problem of a batch: its grid, detection constants, second-derivative
+// weights (physical units, so per grid) and its place in the pooled buffers
+struct Prob {
+  Grid g;
+  Detect det;
+  double d2x[5], d2y[5];
+  float d2xf[5], d2yf[5];
+  long long state_off;  // elements into each pooled ghosted state
+  long long fx_off, fy_off;
+  int cell_off;         // cells into the pooled per-cell arrays
+  int ncell;
+};
+
+// work item of a persistent batched kernel: problem and block coordinates
+struct Item {
+  int p, a, b, pad;
 };
 
 }  // namespace gpm

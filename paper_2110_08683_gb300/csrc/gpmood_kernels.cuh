@@ -235,10 +235,69 @@ __device__ __forceinline__ void column_cell(const double* X, const Grid& g, int 
   else load_cell(X, g, i, j, S);
 }
 
-// ---------------------------------------------------------------------------
-// time step: min over cells of min(dx/(|u|+c), dy/(|v|+c)), per-direction
-// CFL form; positive doubles order like their bit patterns
-// ---------------------------------------------------------------------------
+// ghost cell number tid of the grid (x-ghosts of interior rows first, then
+// the ghost rows, corners included), at time t; tid beyond the ghost count
+// does nothing
+__device__ __forceinline__ long long ghost_count(const Grid& g) {
+  return (long long)g.ny * 2 * g.H + (long long)2 * g.H * (g.nx + 2 * g.H);
+}
+
+__device__ __forceinline__ void fill_ghost(double* X, const Grid& g, double t, long long tid) {
+  const int H = g.H;
+  const int nxg = g.nx + 2 * H;
+  const long long nxs = (long long)g.ny * 2 * H;  // x-ghosts of interior rows
+  const long long nys = (long long)2 * H * nxg;   // y-ghost rows
+  if (tid >= nxs + nys) return;
+  double S[4];
+  int i, j;
+  if (tid < nxs) {
+    j = (int)(tid / (2 * H));
+    int c = (int)(tid % (2 * H));
+    i = c < H ? -1 - c : g.nx + (c - H);
+    xghost(X, g, i, j, S);
+  } else {
+    long long u = tid - nxs;
+    int r = (int)(u / nxg);
+    i = (int)(u % nxg) - H;
+    int side = r < H ? 0 : 1;  // 0: south, 1: north
+    int k = r < H ? r + 1 : r - H + 1;
+    j = side == 0 ? -k : g.ny - 1 + k;
+    int kind = g.bc[2 + side];
+    double xc = g.x0 + (i + 0.5) * g.dx;
+    bool fixed = false, reflect = false;
+    const double* P = nullptr;
+    if (kind == 3) {
+      fixed = true;
+      P = g.bcU[2 + side];
+    } else if (kind == 4) {
+      if (xc < g.dmr_wall_x0) {
+        fixed = true;
+        P = g.dmr_post;
+      } else {
+        reflect = true;
+      }
+    } else if (kind == 5) {
+      fixed = true;
+      P = (xc < g.dmr_xs0 + g.dmr_xs_speed * t) ? g.dmr_post : g.dmr_pre;
+    } else if (kind == 2) {
+      reflect = true;
+    }
+    if (fixed) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) S[v] = P[v];
+    } else {
+      int src;
+      if (kind == 0) src = wrapi(j, g.ny);
+      else if (reflect) src = side == 0 ? k - 1 : g.ny - k;
+      else src = side == 0 ? 0 : g.ny - 1;
+      column_cell(X, g, i, src, S);
+      if (reflect) S[2] = -S[2];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) X[gidx(g, v, i, j)] = S[v];
+}
+
 // ---------------------------------------------------------------------------
 // face-state CAD flag on a possibly-ghost cell
 // ---------------------------------------------------------------------------
@@ -259,25 +318,33 @@ __device__ __forceinline__ void flag_cad(uint8_t* cad, const Grid& g, int i, int
 // cells of a row (x_faces) or a column (y_faces) and produces the 31 faces
 // between them; the left/lower states come from the neighbouring lane.
 // ---------------------------------------------------------------------------
-template <int R, class Real, int DIR>
-__global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
-                                               const __grid_constant__ ParityW<Real> W) {
+// shared-memory tile of one face block: the block's cells and their
+// stencils, converted to Real once, as tile[v][across][along]: "along" runs
+// with the sweep (the lanes), "across" with the warps, so every stencil read
+// of a warp is one contiguous row of shared memory
+template <int R, class Real, int FW>
+struct FaceTile {
+  static constexpr int TF = kSegCells + 2 * R;
+  static constexpr int TS = FW + 2 * R;
+  Real t[4][TS][TF];
+};
+
+// one block of the first-pass face sweep (DIR 0: x faces, 1: y faces) over
+// segment `seg` along the sweep and band `band` of FW rows/columns across it
+template <int R, class Real, int DIR, int FW>
+__device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid& g,
+                                            const ParityW<Real>& W, int seg, int band,
+                                            FaceTile<R, Real, FW>& T_) {
   constexpr int N = stencil_n(R);
   constexpr int Q = rule_q(R);
   constexpr int NS = (Q + 1) / 2;
-  // the block's cells and their stencils, converted to Real once and staged
-  // in shared memory as tile[v][slow][fast]: fast runs along the sweep (the
-  // lanes), slow across it (the warps), so every stencil read of a warp is
-  // one contiguous row of shared memory
-  constexpr int TF = kSegCells + 2 * R;
-  constexpr int TS = kFaceWarps + 2 * R;
-  __shared__ Real tile[4][TS][TF];
+  constexpr int TF = FaceTile<R, Real, FW>::TF;
+  constexpr int TS = FaceTile<R, Real, FW>::TS;
+  auto& tile = T_.t;
   const int lane = threadIdx.x, warp = threadIdx.y;
-  const int seg = DIR == 0 ? blockIdx.x : blockIdx.y;
-  const int band = DIR == 0 ? blockIdx.y : blockIdx.x;
   const int fast0 = seg * kSegFaces - 1 - R;  // first tile cell along the sweep
-  const int slow0 = band * kFaceWarps - R;    // first tile cell across it
-  for (int e = warp * 32 + lane; e < 4 * TS * TF; e += 32 * kFaceWarps) {
+  const int slow0 = band * FW - R;            // first tile cell across it
+  for (int e = warp * 32 + lane; e < 4 * TS * TF; e += 32 * FW) {
     const int v = e / (TS * TF), r = e - v * (TS * TF);
     int sl, fa;
     if (DIR == 0) { sl = r / TF; fa = r - sl * TF; }  // consecutive threads along x
@@ -292,12 +359,12 @@ __global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
   // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
   int i, j, nlen, across;
   if (DIR == 0) {
-    j = band * kFaceWarps + warp;
+    j = band * FW + warp;
     i = seg * kSegFaces - 1 + lane;
     nlen = g.nx;
     across = g.ny;
   } else {
-    i = band * kFaceWarps + warp;
+    i = band * FW + warp;
     j = seg * kSegFaces - 1 + lane;
     nlen = g.ny;
     across = g.nx;
@@ -395,6 +462,14 @@ __global__ void __launch_bounds__(256) k_faces(StageArgs<Real> A, Grid g,
     if (badL) flag_cad(A.cad, g, i, j - 1);
     if (badR) flag_cad(A.cad, g, i, j);
   }
+}
+
+template <int R, class Real, int DIR, int FW>
+__global__ void __launch_bounds__(32 * FW) k_faces(StageArgs<Real> A, Grid g,
+                                                   const __grid_constant__ ParityW<Real> W) {
+  __shared__ FaceTile<R, Real, FW> tile;
+  faces_block<R, Real, DIR, FW>(A, g, W, DIR == 0 ? blockIdx.x : blockIdx.y,
+                                DIR == 0 ? blockIdx.y : blockIdx.x, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -520,11 +595,14 @@ __device__ __forceinline__ void queue_push(bool flag, int cell, int* queue, int*
   if (flag) queue[base + __popc(m & ((1u << lane) - 1u))] = cell;
 }
 
+// first-pass update of cell (i,j) (if in range): candidate, detection,
+// RK combination; troubled cells go to the queue as cell_off + local index.
+// D and d2x/d2y are the detection constants and App. B weights of the grid.
 template <class Real>
-__global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g, Detect D,
-                                                      const __grid_constant__ DirectW<Real> Wd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void update_cell_w(const StageArgs<Real>& A, const Grid& g,
+                                              const Detect& D, const DirectW<Real>& Wd,
+                                              const Real* d2x, const Real* d2y, int i, int j,
+                                              int cell_off) {
   const bool in = i < g.nx && j < g.ny;
   bool bad = false;
   int c = 0;
@@ -535,7 +613,7 @@ __global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g,
     candidate<Real>(A, g, i, j, dt, Y);
     const int top = Wd.top;
     if (top != 0) {
-      bad = A.cad[c] != 0 || troubled<Real>(A.X, g, D, Wd.d2x, Wd.d2y, i, j, Y);
+      bad = A.cad[c] != 0 || troubled<Real>(A.X, g, D, d2x, d2y, i, j, Y);
     } else {
       Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
       Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
@@ -546,7 +624,14 @@ __global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g,
     A.first[c] = (uint8_t)bad;
     combine_store<Real>(A, g, i, j, Y);
   }
-  queue_push(bad, c, A.queue, A.qcount);
+  queue_push(bad, cell_off + c, A.queue, A.qcount);
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g, Detect D,
+                                                      const __grid_constant__ DirectW<Real> Wd) {
+  update_cell_w<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, blockIdx.x * blockDim.x + threadIdx.x,
+                      blockIdx.y * blockDim.y + threadIdx.y, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -683,7 +768,76 @@ __device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const Di
   if (br) flag_cad(A.cad, g, iR, jR);
 }
 
-// one thread per (queued cell, face); faces: 0 W, 1 E, 2 S, 3 N
+// face f (0 W, 1 E, 2 S, 3 N) of queued cell c: recompute it if its EDP1
+// radius changed; the face shared with another queued cell is done by the
+// west/south one
+template <class Real>
+__device__ __forceinline__ void mood_face_item(const StageArgs<Real>& A, const Grid& g,
+                                               const DirectW<Real>& Wd, const Cascade& C,
+                                               const uint32_t* stamp, uint32_t cur, int c, int f) {
+  const int i = c % g.nx, j = c / g.nx;
+  if (f == 0 || f == 2) {
+    int nb = neighbour(g, i, j, f);
+    if (nb >= 0 && stamp[nb] == cur) return;
+  }
+  int iL = i, jL = j;
+  if (f == 0) iL = i - 1;
+  if (f == 2) jL = j - 1;
+  const int iR = iL + (f < 2), jR = jL + (f >= 2);
+  int nl, bl, nr, br;
+  radius_pair(g, A.ord, stamp, cur, C, iL, jL, nl, bl);
+  radius_pair(g, A.ord, stamp, cur, C, iR, jR, nr, br);
+  int Knew = nl < nr ? nl : nr, Kold = bl < br ? bl : br;
+  if (Knew == Kold) return;  // EDP1 order of this face unchanged
+  if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, Knew);
+  else recompute_face<Real, 1>(A, g, Wd, iL, jL, Knew);
+}
+
+// entry k (0 itself, 1 W, 2 E, 3 S, 4 N) of queued cell c's neighbourhood:
+// if c is the first queued cell of that cell's own list (itself, W, E, S,
+// N), re-update it, re-detect it and return whether it is troubled; d gets
+// the cell's index (or -1)
+template <class Real>
+__device__ __forceinline__ bool mood_update_item(const StageArgs<Real>& A, const Grid& g,
+                                                 const Detect& D, const DirectW<Real>& Wd,
+                                                 const Real* d2x, const Real* d2y,
+                                                 const uint32_t* stamp, uint32_t cur, int c,
+                                                 int k, int& d) {
+  const int i = c % g.nx, j = c / g.nx;
+  d = k == 0 ? c : neighbour(g, i, j, k - 1);
+  if (d < 0) return false;
+  const int di = d % g.nx, dj = d / g.nx;
+  if (k > 0) {
+    if (stamp[d] == cur) {
+      d = -1;
+      return false;
+    }
+    // earlier entries of d's own list: W, E, S (in that order) before c
+    const int back = k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 3 : 2;
+    for (int e = 0; e < back; ++e) {
+      int o = neighbour(g, di, dj, e);
+      if (o >= 0 && stamp[o] == cur) {
+        d = -1;
+        return false;
+      }
+    }
+  }
+  double Y[4];
+  candidate<Real>(A, g, di, dj, A.sc->dt, Y);
+  bool flag = false;
+  if (A.ord[d] != 0) {
+    flag = A.cad[d] != 0 || troubled<Real>(A.X, g, D, d2x, d2y, di, dj, Y);
+  } else {
+    Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
+    Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
+    if (!(y[0] > Real(0)) || !(p > Real(0))) atomicAdd(&A.scw->nfog_pad[A.stage], 1);
+  }
+  A.cad[d] = 0;
+  combine_store<Real>(A, g, di, dj, Y);
+  return flag;
+}
+
+// one thread per (queued cell, face)
 template <class Real>
 __global__ void __launch_bounds__(128) k_mood_faces(StageArgs<Real> A, MoodArgs M, Grid g,
                                                     const __grid_constant__ DirectW<Real> Wd,
@@ -693,31 +847,11 @@ __global__ void __launch_bounds__(128) k_mood_faces(StageArgs<Real> A, MoodArgs 
   const int* queue = M.queue[slot];
   const uint32_t cur = M.sc->stamp_cur;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4LL * n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int c = queue[t >> 2];
-    const int f = (int)(t & 3);
-    const int i = c % g.nx, j = c / g.nx;
-    // the face shared with another queued cell is done by the west/south one
-    if (f == 0 || f == 2) {
-      int nb = neighbour(g, i, j, f);
-      if (nb >= 0 && M.stamp[nb] == cur) continue;
-    }
-    int iL = i, jL = j;
-    if (f == 0) iL = i - 1;
-    if (f == 2) jL = j - 1;
-    const int iR = iL + (f < 2), jR = jL + (f >= 2);
-    int nl, bl, nr, br;
-    radius_pair(g, A.ord, M.stamp, cur, C, iL, jL, nl, bl);
-    radius_pair(g, A.ord, M.stamp, cur, C, iR, jR, nr, br);
-    int Knew = nl < nr ? nl : nr, Kold = bl < br ? bl : br;
-    if (Knew == Kold) continue;  // EDP1 order of this face unchanged
-    if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, Knew);
-    else recompute_face<Real, 1>(A, g, Wd, iL, jL, Knew);
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    mood_face_item<Real>(A, g, Wd, C, M.stamp, cur, queue[t >> 2], (int)(t & 3));
 }
 
-// queued cells and their face neighbours: each affected cell is handled by
-// the first queued cell of its list (itself, W, E, S, N)
+// queued cells and their face neighbours
 template <class Real>
 __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs M, Grid g,
                                                      Detect D,
@@ -734,39 +868,168 @@ __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs
     const int q = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = q < n;
     const int c = live ? queue[q] : 0;
-    const int i = c % g.nx, j = c / g.nx;
     for (int k = 0; k < 5; ++k) {
-      bool flag = false;
       int d = -1;
-      if (live) {
-        d = k == 0 ? c : neighbour(g, i, j, k - 1);
-        bool mine = d >= 0;
-        if (mine && k > 0) {
-          const int di = d % g.nx, dj = d / g.nx;
-          if (M.stamp[d] == cur) mine = false;
-          // earlier entries of d's own list: W, E, S (in that order) before c
-          const int back = k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 3 : 2;  // direction from d to c
-          for (int e = 0; mine && e < back; ++e) {
-            int o = neighbour(g, di, dj, e);
-            if (o >= 0 && M.stamp[o] == cur) mine = false;
-          }
-        }
-        if (mine) {
-          const int di = d % g.nx, dj = d / g.nx;
-          double Y[4];
-          candidate<Real>(A, g, di, dj, A.sc->dt, Y);
-          if (A.ord[d] != 0) {
-            flag = A.cad[d] != 0 || troubled<Real>(A.X, g, D, Wd.d2x, Wd.d2y, di, dj, Y);
-          } else {
-            Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
-            Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
-            if (!(y[0] > Real(0)) || !(p > Real(0))) atomicAdd(&A.scw->nfog_pad[A.stage], 1);
-          }
-          A.cad[d] = 0;
-          combine_store<Real>(A, g, di, dj, Y);
-        }
-      }
+      bool flag = false;
+      if (live) flag = mood_update_item<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, M.stamp, cur, c, k, d);
       queue_push(flag, d, next_queue, next_count);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched kernels: many independent problems of uneven sizes in one
+// persistent launch per kernel class.  Each block walks a list of work items
+// (problem, block coordinates); the problem's grid is staged in shared
+// memory; all buffers are pooled, each problem at its own offsets.  A
+// problem with dt = 0 (finished) only carries its state over.
+// ---------------------------------------------------------------------------
+template <class Real>
+__device__ __forceinline__ StageArgs<Real> problem_args(const StageArgs<Real>& B, const Prob& P,
+                                                        const Scalars* psc, int p) {
+  StageArgs<Real> A = B;
+  A.X = B.X + P.state_off;
+  A.U0 = B.U0 + P.state_off;
+  A.out = B.out + P.state_off;
+  A.Fx = B.Fx + P.fx_off;
+  A.Fy = B.Fy + P.fy_off;
+  A.cad = B.cad + P.cell_off;
+  A.ord = B.ord + P.cell_off;
+  A.first = B.first + P.cell_off;
+  A.sc = psc + p;
+  return A;
+}
+
+template <class Real>
+__device__ __forceinline__ const Real* d2_of(const Prob& P, int d);
+template <>
+__device__ __forceinline__ const double* d2_of<double>(const Prob& P, int d) {
+  return d == 0 ? P.d2x : P.d2y;
+}
+template <>
+__device__ __forceinline__ const float* d2_of<float>(const Prob& P, int d) {
+  return d == 0 ? P.d2xf : P.d2yf;
+}
+
+// one block per work item: a software loop over items would let the
+// compiler keep all parity weights in registers across items (they are loop
+// invariant), doubling the register footprint; the block scheduler walks the
+// item list instead
+template <int R, class Real, int DIR, int FW>
+__global__ void __launch_bounds__(32 * FW) k_faces_batch(StageArgs<Real> B, const Prob* probs,
+                                                         const Scalars* psc, const Item* items,
+                                                         const __grid_constant__ ParityW<Real> W) {
+  __shared__ FaceTile<R, Real, FW> tile;
+  // the item's problem, read from shared memory on demand like kernel
+  // parameters
+  __shared__ Prob sp;
+  __shared__ StageArgs<Real> sa;
+  __shared__ int sw[3];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const Item w = items[blockIdx.x];
+    sp = probs[w.p];
+    sa = problem_args<Real>(B, sp, psc, w.p);
+    sw[0] = psc[w.p].dt == 0.0;  // finished problem
+    sw[1] = w.a;
+    sw[2] = w.b;
+  }
+  __syncthreads();
+  if (sw[0]) return;  // uniform over the block
+  faces_block<R, Real, DIR, FW>(sa, sp.g, W, sw[1], sw[2], tile);
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_update_batch(StageArgs<Real> B, const Prob* probs,
+                                                      const Scalars* psc, const Item* items,
+                                                      int nitems,
+                                                      const __grid_constant__ DirectW<Real> Wd) {
+  __shared__ Prob sp;
+  __shared__ StageArgs<Real> sa;
+  __shared__ int sw[3];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __syncthreads();
+    if (tid == 0) {
+      const Item w = items[it];
+      sp = probs[w.p];
+      sa = problem_args<Real>(B, sp, psc, w.p);
+      sw[0] = psc[w.p].dt == 0.0;
+      sw[1] = w.a;
+      sw[2] = w.b;
+    }
+    __syncthreads();
+    const int i = sw[1] * 32 + threadIdx.x, j = sw[2] * 8 + threadIdx.y;
+    if (sw[0]) {
+      // finished: carry the state over unchanged
+      if (i < sp.g.nx && j < sp.g.ny) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sa.out[gidx(sp.g, v, i, j)] = sa.X[gidx(sp.g, v, i, j)];
+      }
+      continue;
+    }
+    update_cell_w<Real>(sa, sp.g, sp.det, Wd, d2_of<Real>(sp, 0), d2_of<Real>(sp, 1), i, j,
+                        sp.cell_off);
+  }
+}
+
+// problem of a pooled cell index (probs sorted by cell_off)
+__device__ __forceinline__ int problem_of(const Prob* probs, int nprob, int gc) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].cell_off <= gc) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(128) k_mood_faces_batch(StageArgs<Real> B, MoodArgs M,
+                                                          const Prob* probs, const Scalars* psc,
+                                                          int nprob,
+                                                          const __grid_constant__ DirectW<Real> Wd,
+                                                          Cascade C) {
+  const int slot = M.sc->slot;
+  const int n = M.sc->count[slot];
+  const int* queue = M.queue[slot];
+  const uint32_t cur = M.sc->stamp_cur;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4LL * n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int gc = queue[t >> 2];
+    const int p = problem_of(probs, nprob, gc);
+    const Prob& P = probs[p];
+    const StageArgs<Real> A = problem_args<Real>(B, P, psc, p);
+    mood_face_item<Real>(A, P.g, Wd, C, M.stamp + P.cell_off, cur, gc - P.cell_off, (int)(t & 3));
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_mood_update_batch(StageArgs<Real> B, MoodArgs M,
+                                                           const Prob* probs, const Scalars* psc,
+                                                           int nprob,
+                                                           const __grid_constant__ DirectW<Real> Wd) {
+  const int slot = M.sc->slot;
+  const int n = M.sc->count[slot];
+  const int* queue = M.queue[slot];
+  int* next_queue = M.queue[slot ^ 1];
+  int* next_count = &M.sc->count[slot ^ 1];
+  const uint32_t cur = M.sc->stamp_cur;
+  const int nthreads = gridDim.x * blockDim.x;
+  const int rounds = (n + nthreads - 1) / nthreads;
+  for (int r = 0; r < rounds; ++r) {
+    const int q = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < n;
+    const int gc = live ? queue[q] : 0;
+    const int p = problem_of(probs, nprob, gc);
+    const Prob& P = probs[p];
+    const StageArgs<Real> A = problem_args<Real>(B, P, psc, p);
+    for (int k = 0; k < 5; ++k) {
+      int d = -1;
+      bool flag = false;
+      if (live)
+        flag = mood_update_item<Real>(A, P.g, P.det, Wd, d2_of<Real>(P, 0), d2_of<Real>(P, 1),
+                                      M.stamp + P.cell_off, cur, gc - P.cell_off, k, d);
+      queue_push(flag, d >= 0 ? P.cell_off + d : -1, next_queue, next_count);
     }
   }
 }

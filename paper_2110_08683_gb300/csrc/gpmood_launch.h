@@ -19,6 +19,25 @@ struct Launch {
                                  const Detect& D, const DirectW<Real>& Wd, cudaStream_t st);
 };
 
+// batched launchers: persistent grids walking work-item lists
+template <class Real>
+struct LaunchB {
+  static cudaError_t faces(int top, int dir, int fw, const StageArgs<Real>& B, const Prob* probs,
+                           const Scalars* psc, const Item* items, int nitems, int blocks,
+                           const ParityW<Real>& W, cudaStream_t st);
+  // max resident blocks per SM of a face kernel variant
+  static int faces_occupancy(int top, int dir, int fw);
+  static cudaError_t update(const StageArgs<Real>& B, const Prob* probs, const Scalars* psc,
+                            const Item* items, int nitems, int blocks, const DirectW<Real>& Wd,
+                            cudaStream_t st);
+  static cudaError_t mood_faces(const StageArgs<Real>& B, const MoodArgs& M, const Prob* probs,
+                                const Scalars* psc, int nprob, const DirectW<Real>& Wd,
+                                const Cascade& C, cudaStream_t st);
+  static cudaError_t mood_update(const StageArgs<Real>& B, const MoodArgs& M, const Prob* probs,
+                                 const Scalars* psc, int nprob, const DirectW<Real>& Wd,
+                                 cudaStream_t st);
+};
+
 cudaError_t launch_fill(double* X, const Grid& g, const Scalars* sc, double tfrac, cudaStream_t st);
 cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, cudaStream_t st);
 cudaError_t launch_finish(Scalars* sc, cudaStream_t st);

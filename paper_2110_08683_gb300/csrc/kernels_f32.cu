@@ -2,3 +2,4 @@
 // detection in float; state, candidate and RK sums in double.
 #include "kernels_impl.cuh"
 template struct gpm::Launch<float>;
+template struct gpm::LaunchB<float>;

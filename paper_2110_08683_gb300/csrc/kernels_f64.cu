@@ -1,3 +1,4 @@
 // kernels_f64.cu -- FP64 instantiation of the stage kernels.
 #include "kernels_impl.cuh"
 template struct gpm::Launch<double>;
+template struct gpm::LaunchB<double>;

@@ -12,10 +12,10 @@ static cudaError_t faces_r(int dir, const StageArgs<Real>& A, const Grid& g,
   dim3 blk(32, kFaceWarps);
   if (dir == 0) {
     dim3 gx((g.nx + 1 + kSegFaces - 1) / kSegFaces, (g.ny + kFaceWarps - 1) / kFaceWarps);
-    k_faces<R, Real, 0><<<gx, blk, 0, st>>>(A, g, W);
+    k_faces<R, Real, 0, kFaceWarps><<<gx, blk, 0, st>>>(A, g, W);
   } else {
     dim3 gy((g.nx + kFaceWarps - 1) / kFaceWarps, (g.ny + 1 + kSegFaces - 1) / kSegFaces);
-    k_faces<R, Real, 1><<<gy, blk, 0, st>>>(A, g, W);
+    k_faces<R, Real, 1, kFaceWarps><<<gy, blk, 0, st>>>(A, g, W);
   }
   return cudaGetLastError();
 }
@@ -51,6 +51,87 @@ template <class Real>
 cudaError_t Launch<Real>::mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
                                       const Detect& D, const DirectW<Real>& Wd, cudaStream_t st) {
   k_mood_update<Real><<<kMoodBlocks, 256, 0, st>>>(A, M, g, D, Wd);
+  return cudaGetLastError();
+}
+
+template <int R, class Real, int FW>
+static cudaError_t faces_batch_r(int dir, const StageArgs<Real>& B, const Prob* probs,
+                                 const Scalars* psc, const Item* items, int nitems, int blocks,
+                                 const ParityW<Real>& W, cudaStream_t st) {
+  dim3 blk(32, FW);
+  (void)blocks;  // one block per item
+  if (dir == 0) k_faces_batch<R, Real, 0, FW><<<nitems, blk, 0, st>>>(B, probs, psc, items, W);
+  else k_faces_batch<R, Real, 1, FW><<<nitems, blk, 0, st>>>(B, probs, psc, items, W);
+  return cudaGetLastError();
+}
+
+template <int R, class Real>
+static cudaError_t faces_batch_fw(int dir, int fw, const StageArgs<Real>& B, const Prob* probs,
+                                  const Scalars* psc, const Item* items, int nitems, int blocks,
+                                  const ParityW<Real>& W, cudaStream_t st) {
+  if (fw == 4) return faces_batch_r<R, Real, 4>(dir, B, probs, psc, items, nitems, blocks, W, st);
+  return faces_batch_r<R, Real, 8>(dir, B, probs, psc, items, nitems, blocks, W, st);
+}
+
+template <class Real>
+cudaError_t LaunchB<Real>::faces(int top, int dir, int fw, const StageArgs<Real>& B,
+                                 const Prob* probs, const Scalars* psc, const Item* items,
+                                 int nitems, int blocks, const ParityW<Real>& W, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  switch (top) {
+    case 0: return faces_batch_fw<0, Real>(dir, fw, B, probs, psc, items, nitems, blocks, W, st);
+    case 1: return faces_batch_fw<1, Real>(dir, fw, B, probs, psc, items, nitems, blocks, W, st);
+    case 2: return faces_batch_fw<2, Real>(dir, fw, B, probs, psc, items, nitems, blocks, W, st);
+    default: return faces_batch_fw<3, Real>(dir, fw, B, probs, psc, items, nitems, blocks, W, st);
+  }
+}
+
+template <int R, class Real>
+static int occ_r(int dir, int fw) {
+  int n = 0;
+  if (fw == 4) {
+    if (dir == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_faces_batch<R, Real, 0, 4>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_faces_batch<R, Real, 1, 4>, 128, 0);
+  } else {
+    if (dir == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_faces_batch<R, Real, 0, 8>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_faces_batch<R, Real, 1, 8>, 256, 0);
+  }
+  return n > 0 ? n : 1;
+}
+
+template <class Real>
+int LaunchB<Real>::faces_occupancy(int top, int dir, int fw) {
+  switch (top) {
+    case 0: return occ_r<0, Real>(dir, fw);
+    case 1: return occ_r<1, Real>(dir, fw);
+    case 2: return occ_r<2, Real>(dir, fw);
+    default: return occ_r<3, Real>(dir, fw);
+  }
+}
+
+template <class Real>
+cudaError_t LaunchB<Real>::update(const StageArgs<Real>& B, const Prob* probs, const Scalars* psc,
+                                  const Item* items, int nitems, int blocks,
+                                  const DirectW<Real>& Wd, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_update_batch<Real><<<blocks, dim3(32, 8), 0, st>>>(B, probs, psc, items, nitems, Wd);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t LaunchB<Real>::mood_faces(const StageArgs<Real>& B, const MoodArgs& M,
+                                      const Prob* probs, const Scalars* psc, int nprob,
+                                      const DirectW<Real>& Wd, const Cascade& C,
+                                      cudaStream_t st) {
+  k_mood_faces_batch<Real><<<2 * kMoodBlocks, 128, 0, st>>>(B, M, probs, psc, nprob, Wd, C);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t LaunchB<Real>::mood_update(const StageArgs<Real>& B, const MoodArgs& M,
+                                       const Prob* probs, const Scalars* psc, int nprob,
+                                       const DirectW<Real>& Wd, cudaStream_t st) {
+  k_mood_update_batch<Real><<<kMoodBlocks, 256, 0, st>>>(B, M, probs, psc, nprob, Wd);
   return cudaGetLastError();
 }
 

@@ -67,7 +67,7 @@ def _problem(**kw):
         sigma_v=5.0,
         sigma_p=5.0,
         csd_on=1,
-        max_iters=64,
+        max_iters=0,  # 0: the implementation's own safety cap
         cfl=0.8,
         dmr_post=[1.0, 0.0, 0.0, 1.0],
         dmr_pre=[1.0, 0.0, 0.0, 1.0],
@@ -300,3 +300,13 @@ def uniform(nx=16, ny=16, R=3, state=(1.0, 0.3, -0.2, 1.0), bc="periodic", ell=0
         name=f"uniform_{nx}x{ny}", nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
         bc=[bc] * 4, cascade=_default_cascade(R), ell=ell, t_end=None, U0=U,
     )
+
+
+def quadrant_batch(count=64, sizes=(128, 256, 512, 1024), seed=0, R=3, ell_cells=12.0):
+    """count four-quadrant problems on [0,1]^2: the grid size of each drawn
+    uniformly from `sizes` and its quadrant states from quadrant_states,
+    both with numpy's default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=count)
+    states = quadrant_states(seed=seed + 1, count=count)
+    return [quadrants(n=int(n), R=R, ell_cells=ell_cells, states=states[k]) for k, n in enumerate(ns)]

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 import paper_2110_08683_gb300 as gp
 from paper_2110_08683_gb300 import build
 
@@ -51,3 +53,16 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     rc = gp.load().gpmood_create(ctypes.byref(gp.make_grid(p)), 1.4, 3, 0.5, ctypes.byref(o),
                                  ctypes.byref(h))
     assert rc == -1
+
+
+def test_batch_binding_marshals_and_rejects_mixed_weights():
+    # problems that would need different GP weights (ell/dx differs): the
+    # library refuses before touching the device
+    from paper_2110_08683_gb300 import inputs as I
+
+    a = I.quadrants(n=16, R=2, seed=1)
+    b = I.quadrants(n=24, R=2, seed=2)
+    b["ell"] = 2.0 * b["ell"]
+    with pytest.raises(gp.GpmoodError) as e:
+        gp.GPMoodBatch([a, b])
+    assert e.value.code == -1

@@ -245,7 +245,7 @@ def test_transpose_symmetry():
 
 def test_mood_iteration_cap_reports_error():
     p = I.quadrants(n=16, R=3, seed=1)
-    p["max_iters"] = 0
+    p["max_iters"] = 1
     o = O.Oracle(p)
     with pytest.raises(RuntimeError):
         o.step(p["U0"], 0.0)
