@@ -365,6 +365,54 @@ def run_batch(args, world, rank, local):
     return line
 
 
+def run_adjoint(args, world, rank, local):
+    """Forward rollout and its reverse mode on the smooth periodic shear layer
+    (GP-R2, MOOD radii frozen from the forward, 200 steps, checkpoints every
+    20): the adjoint/forward time ratio."""
+    import torch
+
+    import paper_2110_08683_gb300 as gp
+    from paper_2110_08683_gb300 import inputs as I
+    from paper_2110_08683_gb300.autograd import rollout
+
+    torch.cuda.set_device(0 if world > 1 else local)
+    n = args.n
+    p = I.shear_layer(n=n, R=2, seed=0)
+    g = gp.GPMood(p, args.precision)
+    U0 = torch.tensor(p["U0"], device="cuda")
+    c = (torch.arange(n, dtype=torch.float64, device="cuda") + 0.5) / n
+    Yc, Xc = torch.meshgrid(c, c, indexing="ij")
+    W = torch.zeros((4, n, n), dtype=torch.float64, device="cuda")
+    W[0] = ((Xc >= 0.4) & (Xc <= 0.6) & (Yc >= 0.4) & (Yc <= 0.6)).double() / (n * n)
+    g.set_state(p["U0"])
+    for _ in range(args.warmup):
+        g.step()
+    torch.cuda.synchronize()
+    steps = args.adjoint_steps
+    U0r = U0.clone().requires_grad_()
+    t0 = time.perf_counter()
+    UN = rollout(U0r, g, steps, every=20)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J = (UN * W).sum()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    fwd, bwd = t1 - t0, t2 - t1
+    return {
+        "metric": METRIC, "value": n * n * steps / fwd, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": fwd * 1e3 / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"periodic double shear layer {n}^2 with a seeded random density "
+                               f"field, GP-R2 cascade 5->3->1, ell=12dx, {steps} steps, "
+                               "checkpoints every 20, J = integral of rho over [0.4,0.6]^2",
+                   "cells": n * n, "precision": args.precision},
+        "adjoint": {"forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
+                    "grad_norm": float(U0r.grad.norm())},
+    }
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle (the reference arm of this tier) on the host cores."""
     import oracle as O
@@ -415,6 +463,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time a rollout and its adjoint instead (shear layer, GP-R2)")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--batch", type=int, default=0,
                     help="time a batch of this many uneven four-quadrant problems instead")
     args = ap.parse_args()
@@ -423,6 +474,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    if args.adjoint:
+        line = run_adjoint(args, world, rank, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         return
     if args.batch > 0:
         line = run_batch(args, world, rank, local)

@@ -179,6 +179,35 @@ int gpmood_profile(gpmood_t h, int enable);
 int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches);
 
 /*
+ * Reverse mode (adjoint) of the step.  The paper defines only the forward
+ * scheme; these calls differentiate that scheme (eqs. fvm_discrete, fvm_F,
+ * gp_reconstructor, HLLC, rk3) with the GP radius of every cell in every
+ * stage and the time step held at the values the forward step chose (the
+ * MOOD decisions are not differentiable; holding them is the "frozen mask").
+ *
+ * gpmood_step_record: one step like gpmood_step (cfl > 0) or gpmood_step_dt
+ *   (cfl <= 0 and dt_fixed > 0) that also writes, to caller-owned device
+ *   memory, the tape its adjoint needs: tape [3][4][ny][nx] doubles = the
+ *   three stage inputs (U^n, U^(1), hat U^(2)), otape [3][ny][nx] bytes = the
+ *   final radius of every cell in each stage.  dt_out (nullable, host) gets
+ *   the step.
+ * gpmood_step_frozen: one step from the current state with the radii of
+ *   otape and the given dt, without detection (replays a recorded step; used
+ *   for finite differences of the frozen-mask map).
+ * gpmood_step_adjoint: lam_out = (dU^{n+1}/dU^n)^T lam_in for the recorded
+ *   step (tape, otape, dt, and t its start time), all device arrays in the
+ *   state layout; lam_out may not alias lam_in.  Allocates its work buffers
+ *   on the first call and waits for the stream.  Where a reconstructed state
+ *   has non-positive pressure the Riemann solver's branch is decided by NaN
+ *   comparisons; the adjoint follows the branch the forward took.
+ */
+int gpmood_step_record(gpmood_t h, double cfl, double dt_fixed, double* tape, uint8_t* otape,
+                       double* dt_out);
+int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt);
+int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
+                        const double* lam_in, double* lam_out);
+
+/*
  * Batches: many independent problems of uneven sizes advanced together.
  * Every problem has its own grid and boundaries and its own time step; all
  * share gamma, R_max, the cascade and the options, and the GP weights, so

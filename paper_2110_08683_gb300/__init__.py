@@ -89,6 +89,9 @@ def load(build_if_missing=True):
     L.gpmood_strerror.restype = C.c_char_p
     L.gpmood_last_launches.argtypes = [p]
     L.gpmood_profile.argtypes = [p, i]
+    L.gpmood_step_record.argtypes = [p, d, d, p, p, C.POINTER(d)]
+    L.gpmood_step_frozen.argtypes = [p, p, d]
+    L.gpmood_step_adjoint.argtypes = [p, p, p, d, d, p, p]
     L.gpmood_batch_create.argtypes = [C.POINTER(Grid), i, d, i, C.POINTER(d), C.POINTER(Options),
                                       C.POINTER(p)]
     L.gpmood_batch_set_stream.argtypes = [p, p]
@@ -308,6 +311,22 @@ class GPMood:
 
     def profile(self, enable=True):
         gpmood_profile(self.h, enable)
+
+    # reverse mode: device pointers (ints) of caller-owned tensors
+    def step_record(self, tape_ptr, otape_ptr, cfl=None, dt=0.0):
+        out = C.c_double(0.0)
+        cfl = (self.prob["cfl"] if cfl is None else cfl) if dt <= 0.0 else 0.0
+        _check(load().gpmood_step_record(self.h, cfl, dt, C.c_void_p(tape_ptr),
+                                         C.c_void_p(otape_ptr), C.byref(out)), "step_record")
+        return out.value
+
+    def step_frozen(self, otape_ptr, dt):
+        _check(load().gpmood_step_frozen(self.h, C.c_void_p(otape_ptr), dt), "step_frozen")
+
+    def step_adjoint(self, tape_ptr, otape_ptr, dt, t, lam_in_ptr, lam_out_ptr):
+        _check(load().gpmood_step_adjoint(self.h, C.c_void_p(tape_ptr), C.c_void_p(otape_ptr), dt,
+                                          t, C.c_void_p(lam_in_ptr), C.c_void_p(lam_out_ptr)),
+               "step_adjoint")
 
     def kernel_times(self):
         return gpmood_kernel_times(self.h)

@@ -1,0 +1,345 @@
+// adjoint_kernels.cuh -- reverse mode of one SSP-RK3 step with the GP radii
+// of every stage and the time step held at their forward values.
+//
+// For a stage Y = X - dt F(X) the vector-Jacobian product is
+//   v^T dY/dX = v - dt (dF/dX)^T v,
+// and (dF/dX)^T v is formed in three passes:
+//   1. faces: the adjoint of the face-averaged flux of eq. fvm_F is
+//      a_f = (v_L - v_R)/dx (or /dy); at every Gauss point of the face's EDP1
+//      radius the states are reconstructed again and the HLLC flux is
+//      differentiated in reverse (w_g a_f in, state adjoints out);
+//   2. gather: every cell of the ghosted grid collects z_m times the state
+//      adjoints of the faces whose reconstruction stencil contains it
+//      (eq. gp_reconstructor transposed);
+//   3. fold: ghost-cell adjoints go back to the interior cells the ghosts
+//      copied (periodic wrap-add, outflow add, reflect with the normal
+//      momentum negated, fixed states drop out).
+#pragma once
+
+#include "gpmood_kernels.cuh"
+
+namespace gpm {
+
+// reverse mode of hllc_x: given the adjoint Fb of the flux, accumulate the
+// adjoints of the two states into UbL / UbR.  The forward expressions are
+// those of hllc_x; only the branch the forward took is differentiated.
+template <class Real>
+__device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real gam,
+                                           const Real* Fb, Real* UbL, Real* UbR) {
+  const Real gm1 = gam - Real(1);
+  // ---- forward, keeping the intermediates
+  const Real rL = UL[0], rR = UR[0];
+  const Real irL = recip(rL), irR = recip(rR);
+  const Real uL = UL[1] * irL, vL = UL[2] * irL;
+  const Real uR = UR[1] * irR, vR = UR[2] * irR;
+  const Real pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
+  const Real pR = gm1 * (UR[3] - Real(0.5) * (UR[1] * uR + UR[2] * vR));
+  const Real zL = gam * pL * irL, zR = gam * pR * irR;
+  const Real cL = sqrt(zL), cR = sqrt(zR);
+  const Real aL = uL - cL, bL = uR - cR;
+  const bool selA = aL < bL;
+  const Real SL = selA ? aL : bL;
+  const Real aR = uL + cL, bR = uR + cR;
+  const bool selAR = aR > bR;
+  const Real SR = selAR ? aR : bR;
+  const Real dL = SL - uL, dR = SR - uR;
+  const Real num = pR - pL + rL * uL * dL - rR * uR * dR;
+  const Real den = rL * dL - rR * dR;
+  const Real iden = recip(den);
+  const Real Ss = num * iden;
+  const bool left = Ss >= Real(0);
+  const bool useL = SL >= Real(0);
+  const bool useS = !useL && (left || (SR > Real(0)));
+  // adjoints of the intermediates
+  Real rLb = 0, rRb = 0, uLb = 0, uRb = 0, vLb = 0, vRb = 0, pLb = 0, pRb = 0, ELb = 0, ERb = 0;
+  Real SLb = 0, SRb = 0, Ssb = 0, irLb = 0, irRb = 0, dLb = 0, dRb = 0;
+  Real FLb[4] = {0, 0, 0, 0}, FRb[4] = {0, 0, 0, 0};
+  if (useL) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) FLb[k] = Fb[k];
+  } else if (!useS) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) FRb[k] = Fb[k];
+  } else {
+    // star state of side K
+    const Real rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR;
+    const Real EK = left ? UL[3] : UR[3], pK = left ? pL : pR, SK = left ? SL : SR;
+    const Real irK = left ? irL : irR, dK = left ? dL : dR;
+    const Real iD = recip(SK - Ss);
+    const Real idK = recip(dK);
+    const Real fK = rK * dK * iD;
+    const Real t1 = Ss - uK, t2 = Ss + pK * irK * idK;
+    const Real eK = EK * irK + t1 * t2;
+    const Real UKs[4] = {fK, fK * Ss, fK * vK, fK * eK};
+    const Real* UK = left ? UL : UR;
+    // Fs[v] = FK[v] + SK (UKs[v] - UK[v])
+    Real FKb[4], UKsb[4], SKb = 0, UKb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      FKb[k] = Fb[k];
+      SKb += Fb[k] * (UKs[k] - UK[k]);
+      UKsb[k] = SK * Fb[k];
+      UKb[k] = -SK * Fb[k];
+    }
+    // UKs = fK (1, Ss, vK, eK)
+    Real fKb = UKsb[0] + UKsb[1] * Ss + UKsb[2] * vK + UKsb[3] * eK;
+    Ssb += UKsb[1] * fK;
+    Real vKb = UKsb[2] * fK;
+    Real eKb = UKsb[3] * fK;
+    // eK = EK irK + t1 t2, t1 = Ss - uK, t2 = Ss + pK irK / dK
+    Real EKb = eKb * irK;
+    Real irKb = eKb * EK;
+    const Real t1b = eKb * t2, t2b = eKb * t1;
+    Ssb += t1b + t2b;
+    Real uKb = -t1b;
+    Real pKb = t2b * irK * idK;
+    irKb += t2b * pK * idK;
+    Real dKb = -t2b * pK * irK * idK * idK;
+    // fK = rK dK / D, D = SK - Ss
+    Real rKb = fKb * dK * iD;
+    dKb += fKb * rK * iD;
+    const Real Db = -fKb * fK * iD;
+    SKb += Db;
+    Ssb -= Db;
+    if (left) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) FLb[k] += FKb[k];
+      rLb += rKb; uLb += uKb; vLb += vKb; ELb += EKb; pLb += pKb; SLb += SKb;
+      irLb += irKb; dLb += dKb;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) UbL[k] += UKb[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) FRb[k] += FKb[k];
+      rRb += rKb; uRb += uKb; vRb += vKb; ERb += EKb; pRb += pKb; SRb += SKb;
+      irRb += irKb; dRb += dKb;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) UbR[k] += UKb[k];
+    }
+    // Ss = num / den
+    const Real numb = Ssb * iden;
+    const Real denb = -Ssb * Ss * iden;
+    // den = rL dL - rR dR
+    rLb += denb * dL; dLb += denb * rL; rRb -= denb * dR; dRb -= denb * rR;
+    // num = pR - pL + rL uL dL - rR uR dR
+    pRb += numb; pLb -= numb;
+    rLb += numb * uL * dL; uLb += numb * rL * dL; dLb += numb * rL * uL;
+    rRb -= numb * uR * dR; uRb -= numb * rR * dR; dRb -= numb * rR * uR;
+  }
+  // dL = SL - uL, dR = SR - uR
+  SLb += dLb; uLb -= dLb;
+  SRb += dRb; uRb -= dRb;
+  // SL = min(aL, bL), SR = max(aR, bR) on the branch taken
+  Real cLb = 0, cRb = 0;
+  if (selA) { uLb += SLb; cLb -= SLb; } else { uRb += SLb; cRb -= SLb; }
+  if (selAR) { uLb += SRb; cLb += SRb; } else { uRb += SRb; cRb += SRb; }
+  // physical fluxes FL = (rL uL, rL uL uL + pL, rL uL vL, uL (EL + pL))
+  rLb += FLb[0] * uL + FLb[1] * uL * uL + FLb[2] * uL * vL;
+  uLb += FLb[0] * rL + FLb[1] * Real(2) * rL * uL + FLb[2] * rL * vL + FLb[3] * (UL[3] + pL);
+  vLb += FLb[2] * rL * uL;
+  pLb += FLb[1] + FLb[3] * uL;
+  ELb += FLb[3] * uL;
+  rRb += FRb[0] * uR + FRb[1] * uR * uR + FRb[2] * uR * vR;
+  uRb += FRb[0] * rR + FRb[1] * Real(2) * rR * uR + FRb[2] * rR * vR + FRb[3] * (UR[3] + pR);
+  vRb += FRb[2] * rR * uR;
+  pRb += FRb[1] + FRb[3] * uR;
+  ERb += FRb[3] * uR;
+  // c = sqrt(gam p ir)
+  const Real zLb = cLb * Real(0.5) * recip(cL), zRb = cRb * Real(0.5) * recip(cR);
+  if (cLb != Real(0)) { pLb += zLb * gam * irL; irLb += zLb * gam * pL; }
+  if (cRb != Real(0)) { pRb += zRb * gam * irR; irRb += zRb * gam * pR; }
+  // p = gm1 (E - 0.5 (m_x u + m_y v))
+  ELb += pLb * gm1;
+  Real mxLb = -Real(0.5) * gm1 * pLb * uL, myLb = -Real(0.5) * gm1 * pLb * vL;
+  uLb -= Real(0.5) * gm1 * pLb * UL[1];
+  vLb -= Real(0.5) * gm1 * pLb * UL[2];
+  ERb += pRb * gm1;
+  Real mxRb = -Real(0.5) * gm1 * pRb * uR, myRb = -Real(0.5) * gm1 * pRb * vR;
+  uRb -= Real(0.5) * gm1 * pRb * UR[1];
+  vRb -= Real(0.5) * gm1 * pRb * UR[2];
+  // u = m_x ir, v = m_y ir
+  mxLb += uLb * irL; myLb += vLb * irL; irLb += uLb * UL[1] + vLb * UL[2];
+  mxRb += uRb * irR; myRb += vRb * irR; irRb += uRb * UR[1] + vRb * UR[2];
+  // ir = 1 / r
+  rLb -= irLb * irL * irL;
+  rRb -= irRb * irR * irR;
+  UbL[0] += rLb; UbL[1] += mxLb; UbL[2] += myLb; UbL[3] += ELb;
+  UbR[0] += rRb; UbR[1] += mxRb; UbR[2] += myRb; UbR[3] += ERb;
+}
+
+// EDP1 radius of the face between (iL,jL) and (iR,jR) from a radius map
+__device__ __forceinline__ int face_radius(const Grid& g, const uint8_t* ord, int top, int iL,
+                                           int jL, int iR, int jR) {
+  auto rad = [&](int i, int j) -> int {
+    if (i < 0 || i >= g.nx) {
+      if (!g.periodic_x) return top;
+      i = wrapi(i, g.nx);
+    }
+    if (j < 0 || j >= g.ny) {
+      if (!g.periodic_y) return top;
+      j = wrapi(j, g.ny);
+    }
+    return ord[cidx(g, i, j)];
+  };
+  const int a = rad(iL, jL), b = rad(iR, jR);
+  return a < b ? a : b;
+}
+
+template <int K, class Real, int DIR>
+__device__ void adj_face_at(const double* X, const Grid& g, const DirectW<Real>& Wd, int iL,
+                            int jL, const Real* a, Real* AL, Real* AR, long long f,
+                            long long nf) {
+  constexpr int Q = rule_q(K);
+  const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
+  const Real gam = (Real)g.gamma;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    Real UL[4], UR[4];
+    if (K == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        UL[v] = (Real)__ldg(X + gidx(g, v, iL, jL));
+        UR[v] = (Real)__ldg(X + gidx(g, v, iR, jR));
+      }
+    } else {
+      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
+      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
+    }
+    Real Fb[4], bL[4] = {0, 0, 0, 0}, bR[4] = {0, 0, 0, 0};
+    const Real w = Wd.w[K][q];
+    if (DIR == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Fb[v] = w * a[v];
+      hllc_x_vjp<Real>(UL, UR, gam, Fb, bL, bR);
+    } else {
+      // y faces: HLLC on (rho, rho v, rho u, E); the flux comes back swapped
+      Real sL[4] = {UL[0], UL[2], UL[1], UL[3]}, sR[4] = {UR[0], UR[2], UR[1], UR[3]};
+      Real sFb[4] = {w * a[0], w * a[2], w * a[1], w * a[3]};
+      Real tL[4] = {0, 0, 0, 0}, tR[4] = {0, 0, 0, 0};
+      hllc_x_vjp<Real>(sL, sR, gam, sFb, tL, tR);
+      bL[0] = tL[0]; bL[1] = tL[2]; bL[2] = tL[1]; bL[3] = tL[3];
+      bR[0] = tR[0]; bR[1] = tR[2]; bR[2] = tR[1]; bR[3] = tR[3];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      AL[((long long)v * kMaxQ + q) * nf + f] = bL[v];
+      AR[((long long)v * kMaxQ + q) * nf + f] = bR[v];
+    }
+  }
+}
+
+// pass 1: one thread per face of direction DIR
+template <class Real, int DIR>
+__global__ void __launch_bounds__(128) k_adj_faces(const double* X, const double* vin,
+                                                   const uint8_t* ord, Grid g,
+                                                   const __grid_constant__ DirectW<Real> Wd,
+                                                   AdjFaces A) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= A.nf) return;
+  int iL, jL, iR, jR;
+  if (DIR == 0) {  // x face i (0..nx) of row j
+    const int i = (int)(f % (g.nx + 1)), j = (int)(f / (g.nx + 1));
+    iL = i - 1; jL = j; iR = i; jR = j;
+  } else {         // y face j (0..ny) of column i
+    const int i = (int)(f % g.nx), j = (int)(f / g.nx);
+    iL = i; jL = j - 1; iR = i; jR = j;
+  }
+  const int K = face_radius(g, ord, Wd.top, iL, jL, iR, jR);
+  A.K[f] = (uint8_t)K;
+  const long long nc = (long long)g.nx * g.ny;
+  const bool inL = iL >= 0 && iL < g.nx && jL >= 0 && jL < g.ny;
+  const bool inR = iR >= 0 && iR < g.nx && jR >= 0 && jR < g.ny;
+  const Real inv = (Real)(DIR == 0 ? g.inv_dx : g.inv_dy);
+  Real a[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const double vl = inL ? vin[v * nc + cidx(g, iL, jL)] : 0.0;
+    const double vr = inR ? vin[v * nc + cidx(g, iR, jR)] : 0.0;
+    a[v] = (Real)((vl - vr) * (DIR == 0 ? g.inv_dx : g.inv_dy));
+  }
+  (void)inv;
+  Real* AL = (Real*)A.L;
+  Real* AR = (Real*)A.R;
+  switch (K) {
+    case 0: adj_face_at<0, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
+    case 1: adj_face_at<1, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
+    case 2: adj_face_at<2, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
+    default: adj_face_at<3, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
+  }
+}
+
+// index of offset (a,b) in the radius-K stencil (order b = -K..K, a = -K..K)
+__device__ __forceinline__ int stencil_index(int K, int a, int b) {
+  int m = 0;
+  for (int bb = -K; bb < b; ++bb) m += 2 * (K - (bb < 0 ? -bb : bb)) + 1;
+  const int hb = K - (b < 0 ? -b : b);
+  return m + a + hb;
+}
+
+template <class Real>
+__device__ __forceinline__ void gather_face(const DirectW<Real>& Wd, int face, int a, int b,
+                                            int K, const Real* S, long long f, long long nf,
+                                            double* acc) {
+  const int ab = (a < 0 ? -a : a) + (b < 0 ? -b : b);
+  if (ab > K) return;
+  if (K == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] += (double)S[(long long)v * kMaxQ * nf + f];
+    return;
+  }
+  const int m = stencil_index(K, a, b);
+  const int Q = K + 1;
+  for (int q = 0; q < Q; ++q) {
+    const Real z = Wd.z[K][face][q][m];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] += (double)(z * S[((long long)v * kMaxQ + q) * nf + f]);
+  }
+}
+
+// pass 2: every cell of the ghosted grid collects from the faces whose
+// reconstruction stencils contain it
+template <class Real>
+__global__ void __launch_bounds__(256) k_adj_gather(Grid g, const __grid_constant__ DirectW<Real> Wd,
+                                                    AdjFaces Ax, AdjFaces Ay, double* G) {
+  const int gx = g.nx + 2 * g.H, gyy = g.ny + 2 * g.H;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)gx * gyy) return;
+  const int ci = (int)(t % gx) - g.H, cj = (int)(t / gx) - g.H;
+  const int top = Wd.top;
+  double acc[4] = {0, 0, 0, 0};
+  const Real* xL = (const Real*)Ax.L;
+  const Real* xR = (const Real*)Ax.R;
+  const Real* yL = (const Real*)Ay.L;
+  const Real* yR = (const Real*)Ay.R;
+  for (int b = -top; b <= top; ++b) {
+    const int hb = top - (b < 0 ? -b : b);
+    for (int a = -hb; a <= hb; ++a) {
+      // n = c - (a, b) reconstructs with c at offset (a, b)
+      const int ni = ci - a, nj = cj - b;
+      if (nj >= 0 && nj < g.ny) {
+        if (ni >= -1 && ni <= g.nx - 1) {  // east face of n: x face ni+1, left state
+          const long long f = (long long)nj * (g.nx + 1) + ni + 1;
+          gather_face<Real>(Wd, 0, a, b, Ax.K[f], xL, f, Ax.nf, acc);
+        }
+        if (ni >= 0 && ni <= g.nx) {  // west face of n: x face ni, right state
+          const long long f = (long long)nj * (g.nx + 1) + ni;
+          gather_face<Real>(Wd, 1, a, b, Ax.K[f], xR, f, Ax.nf, acc);
+        }
+      }
+      if (ni >= 0 && ni < g.nx) {
+        if (nj >= -1 && nj <= g.ny - 1) {  // north face of n: y face nj+1, lower state
+          const long long f = (long long)(nj + 1) * g.nx + ni;
+          gather_face<Real>(Wd, 2, a, b, Ay.K[f], yL, f, Ay.nf, acc);
+        }
+        if (nj >= 0 && nj <= g.ny) {  // south face of n: y face nj, upper state
+          const long long f = (long long)nj * g.nx + ni;
+          gather_face<Real>(Wd, 3, a, b, Ay.K[f], yR, f, Ay.nf, acc);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) G[gidx(g, v, ci, cj)] = acc[v];
+}
+
+}  // namespace gpm

@@ -125,4 +125,85 @@ __global__ void k_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc
   mood_decide(sc, stage, n, hc, use_graph);
 }
 
+// ---------------------------------------------------------------------------
+// adjoint helpers
+// ---------------------------------------------------------------------------
+__global__ void k_fill_ghosts_at(double* X, Grid g, double t) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  fill_ghost(X, g, t, tid);
+}
+
+// transpose of the ghost fill: every ghost cell's adjoint goes to the
+// interior cell it was copied from (y rule first, then the x rule, the
+// reverse of the fill's composition); fixed states drop out
+__global__ void k_adj_fold(double* G, Grid g) {
+  const int H = g.H;
+  const int nxg = g.nx + 2 * H;
+  const long long nxs = (long long)g.ny * 2 * H;
+  const long long nys = (long long)2 * H * nxg;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= nxs + nys) return;
+  int i, j;
+  if (tid < nxs) {
+    j = (int)(tid / (2 * H));
+    const int c = (int)(tid % (2 * H));
+    i = c < H ? -1 - c : g.nx + (c - H);
+  } else {
+    const long long u = tid - nxs;
+    const int r = (int)(u / nxg);
+    i = (int)(u % nxg) - H;
+    j = r < H ? -(r + 1) : g.ny - 1 + (r - H + 1);
+  }
+  double s[4] = {1.0, 1.0, 1.0, 1.0};
+  int sj = j, si = i;
+  if (j < 0 || j >= g.ny) {
+    const int side = j < 0 ? 0 : 1;
+    const int k = j < 0 ? -j : j - g.ny + 1;
+    const int kind = g.bc[2 + side];
+    const double xc = g.x0 + (i + 0.5) * g.dx;
+    bool reflect = kind == 2;
+    if (kind == 3 || kind == 5) return;
+    if (kind == 4) {
+      if (xc < g.dmr_wall_x0) return;
+      reflect = true;
+    }
+    if (kind == 0) sj = wrapi(j, g.ny);
+    else if (reflect) sj = side == 0 ? k - 1 : g.ny - k;
+    else sj = side == 0 ? 0 : g.ny - 1;
+    if (reflect) s[2] = -s[2];
+  }
+  if (i < 0 || i >= g.nx) {
+    const int side = i < 0 ? 0 : 1;
+    const int k = i < 0 ? -i : i - g.nx + 1;
+    const int kind = g.bc[side];
+    if (kind == 3) return;
+    if (kind == 0) si = wrapi(i, g.nx);
+    else if (kind == 2) si = side == 0 ? k - 1 : g.nx - k;
+    else si = side == 0 ? 0 : g.nx - 1;
+    if (kind == 2) s[1] = -s[1];
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) atomicAdd(&G[gidx(g, v, si, sj)], s[v] * G[gidx(g, v, i, j)]);
+}
+
+// w = v - dt G (interior of the ghosted G)
+__global__ void k_adj_stage_out(double* w, const double* v, const double* G, Grid g, double dt) {
+  const long long nc = (long long)g.nx * g.ny;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4 * nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int vv = (int)(t / nc);
+    const long long c = t - vv * nc;
+    const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+    w[t] = v[t] - dt * G[gidx(g, vv, i, j)];
+  }
+}
+
+// out = a x + b y (b = 0: y unused)
+__global__ void k_lincomb(double* out, double a, const double* x, double b, const double* y,
+                          long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = b == 0.0 ? a * x[t] : a * x[t] + b * y[t];
+}
+
 }  // namespace gpm

@@ -53,6 +53,12 @@ struct gpmood_s {
   cudaEvent_t gev[64];
   int gev_cls[32];
   int gev_n, gev_pairs;
+  // adjoint work buffers (allocated on first use)
+  double* aX;     // ghosted stage input
+  double* aG;     // ghosted state adjoint
+  double *av, *aw, *amu;  // interior vectors
+  AdjFaces ax, ay;
+  uint8_t* aord;
 };
 
 namespace {
@@ -85,6 +91,9 @@ void free_all(gpmood_t h) {
       if (h->gexec[r][p]) cudaGraphExecDestroy(h->gexec[r][p]);
   if (h->cs) cudaStreamDestroy(h->cs);
   if (h->cs2) cudaStreamDestroy(h->cs2);
+  void* adj[] = {h->aX, h->aG, h->av, h->aw, h->amu, h->ax.L, h->ax.R, h->ax.K,
+                 h->ay.L, h->ay.R, h->ay.K, h->aord};
+  for (void* p : adj) cudaFree(p);
   for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
   cudaFree(h->Fx);
   cudaFree(h->Fy);
@@ -197,7 +206,21 @@ int eager_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& 
   return 0;
 }
 
-int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+// copy the interior of a ghosted state to an interior array (device)
+int copy_interior(gpmood_t h, const double* Xg, double* out) {
+  const Grid& g = h->g;
+  for (int v = 0; v < 4; ++v)
+    CK(cudaMemcpy2DAsync(out + (size_t)v * g.nx * g.ny, sizeof(double) * g.nx,
+                         Xg + v * g.vstride + (size_t)g.H * g.pitch + g.H,
+                         sizeof(double) * g.pitch, sizeof(double) * g.nx, g.ny,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  return 0;
+}
+
+// the eager step; with a tape it also records the three stage inputs
+// (interior, [3][4][ny][nx]) and the final radii of the three stages
+int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
+            double* tape = nullptr, uint8_t* otape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
   const int a = h->cur, b = (a + 1) % 3, c = (a + 2) % 3;
   write_control(h, cfl, fixed_dt, clip, t_end);
@@ -205,12 +228,19 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
   if (rc) return rc;
   CK(launch_dt(h->U[a], h->g, h->sc, h->stream));
   const int in[3] = {a, b, c}, out[3] = {b, c, b};
+  const size_t nc = (size_t)h->g.nx * h->g.ny;
   for (int s = 0; s < 3; ++s) {
+    if (tape) {
+      rc = copy_interior(h, h->U[in[s]], tape + (size_t)s * 4 * nc);
+      if (rc) return rc;
+    }
     rc = h->precision == GPMOOD_FP32 ? eager_stage<float>(h, s, a, in[s], out[s], h->pw32, h->dw32)
                                      : eager_stage<double>(h, s, a, in[s], out[s], h->pw64, h->dw64);
     if (rc) return rc;
     rc = step_error(h);
     if (rc) return rc;
+    if (otape) CK(cudaMemcpyAsync(otape + s * nc, h->ord + s * nc, nc, cudaMemcpyDeviceToDevice,
+                                  h->stream));
   }
   CK(launch_finish(h->sc, h->stream));
   rc = pull_scalars(h);
@@ -697,6 +727,142 @@ int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
     if (launches) launches[k] = h->prof_n[k];
   }
   return GPMOOD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// recorded steps, replay with given radii, and the adjoint
+// ---------------------------------------------------------------------------
+int gpmood_step_record(gpmood_t h, double cfl, double dt_fixed, double* tape, uint8_t* otape,
+                       double* dt_out) {
+  if (!h || !tape || !otape || (!(cfl > 0.0) && !(dt_fixed > 0.0))) return GPMOOD_E_INVAL;
+  int rc = do_step(h, cfl > 0.0 ? cfl : 1.0, dt_fixed > 0.0 ? dt_fixed : 0.0, 0, 0.0, tape, otape);
+  if (rc) return rc;
+  if (dt_out) *dt_out = h->hsc->dt;
+  return GPMOOD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <class Real>
+int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>& D) {
+  const int a = h->cur, b = (a + 1) % 3, c = (a + 2) % 3;
+  write_control(h, 1.0, dt, 0, 0.0);
+  int rc = push_control(h);
+  if (rc) return rc;
+  CK(launch_dt(h->U[a], h->g, h->sc, h->stream));
+  const int in[3] = {a, b, c}, out[3] = {b, c, b};
+  const size_t nc = (size_t)h->g.nx * h->g.ny;
+  static const double tfrac[3] = {0.0, 1.0, 0.5};
+  for (int s = 0; s < 3; ++s) {
+    CK(launch_fill(h->U[in[s]], h->g, h->sc, tfrac[s], h->stream));
+    StageArgs<Real> A = stage_args<Real>(h, s, a, in[s], out[s]);
+    CK(cudaMemcpyAsync(A.ord, otape + s * nc, nc, cudaMemcpyDeviceToDevice, h->stream));
+    CK(LaunchA<Real>::frozen_stage(A, h->g, D, h->stream));
+  }
+  CK(launch_finish(h->sc, h->stream));
+  rc = pull_scalars(h);
+  if (rc) return rc;
+  if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
+  h->cur = b;
+  return GPMOOD_OK;
+}
+
+int adj_buffers(gpmood_t h) {
+  if (h->aX) return 0;
+  const Grid& g = h->g;
+  const size_t nc = (size_t)g.nx * g.ny;
+  const size_t rs = h->precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  h->ax.nf = (long long)(g.nx + 1) * g.ny;
+  h->ay.nf = (long long)g.nx * (g.ny + 1);
+  bool ok = cudaMalloc(&h->aX, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess &&
+            cudaMalloc(&h->aG, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess &&
+            cudaMalloc(&h->av, sizeof(double) * 4 * nc) == cudaSuccess &&
+            cudaMalloc(&h->aw, sizeof(double) * 4 * nc) == cudaSuccess &&
+            cudaMalloc(&h->amu, sizeof(double) * 4 * nc) == cudaSuccess &&
+            cudaMalloc(&h->ax.L, rs * 4 * kMaxQ * (size_t)h->ax.nf) == cudaSuccess &&
+            cudaMalloc(&h->ax.R, rs * 4 * kMaxQ * (size_t)h->ax.nf) == cudaSuccess &&
+            cudaMalloc(&h->ax.K, (size_t)h->ax.nf) == cudaSuccess &&
+            cudaMalloc(&h->ay.L, rs * 4 * kMaxQ * (size_t)h->ay.nf) == cudaSuccess &&
+            cudaMalloc(&h->ay.R, rs * 4 * kMaxQ * (size_t)h->ay.nf) == cudaSuccess &&
+            cudaMalloc(&h->ay.K, (size_t)h->ay.nf) == cudaSuccess &&
+            cudaMalloc(&h->aord, 3 * nc) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return set_err(h, GPMOOD_E_OOM);
+  }
+  CK(cudaMemset(h->aX, 0, sizeof(double) * 4 * (size_t)g.vstride));
+  return 0;
+}
+
+// w = v - dt (dF/dX)^T v at the stage input X (interior) with radii ords
+template <class Real>
+int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, double dt,
+              const double* v, double* w, const DirectW<Real>& D) {
+  const Grid& g = h->g;
+  for (int c = 0; c < 4; ++c)
+    CK(cudaMemcpy2DAsync(h->aX + c * g.vstride + (size_t)g.H * g.pitch + g.H,
+                         sizeof(double) * g.pitch, X + (size_t)c * g.nx * g.ny,
+                         sizeof(double) * g.nx, sizeof(double) * g.nx, g.ny,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  const long long ngh = (long long)g.ny * 2 * g.H + 2LL * g.H * (g.nx + 2 * g.H);
+  const int gb = (int)((ngh + 255) / 256);
+  k_fill_ghosts_at<<<gb, 256, 0, h->stream>>>(h->aX, g, ts);
+  CK(cudaGetLastError());
+  CK(LaunchA<Real>::adj_faces(h->aX, v, ords, g, D, h->ax, h->ay, h->stream));
+  CK(LaunchA<Real>::adj_gather(g, D, h->ax, h->ay, h->aG, h->stream));
+  k_adj_fold<<<gb, 256, 0, h->stream>>>(h->aG, g);
+  k_adj_stage_out<<<152 * 8, 256, 0, h->stream>>>(w, v, h->aG, g, dt);
+  CK(cudaGetLastError());
+  return 0;
+}
+
+template <class Real>
+int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
+                 const double* lam, double* out, const DirectW<Real>& D) {
+  const size_t nc = (size_t)h->g.nx * h->g.ny, n4 = 4 * nc;
+  const int nb = 152 * 8;
+  double *mu = h->amu, *v = h->av, *w = h->aw;
+  // U^{n+1} = (U^n + 2 Y3)/3
+  k_lincomb<<<nb, 256, 0, h->stream>>>(mu, 1.0 / 3.0, lam, 0.0, nullptr, (long long)n4);
+  k_lincomb<<<nb, 256, 0, h->stream>>>(v, 2.0 / 3.0, lam, 0.0, nullptr, (long long)n4);
+  // Y3 = X3 - dt F(X3), X3 = (3 U^n + Y2)/4
+  int rc = adj_stage<Real>(h, tape + 2 * n4, otape + 2 * nc, t + 0.5 * dt, dt, v, w, D);
+  if (rc) return rc;
+  k_lincomb<<<nb, 256, 0, h->stream>>>(mu, 1.0, mu, 0.75, w, (long long)n4);
+  k_lincomb<<<nb, 256, 0, h->stream>>>(v, 0.25, w, 0.0, nullptr, (long long)n4);
+  // Y2 = X2 - dt F(X2), X2 = Y1
+  rc = adj_stage<Real>(h, tape + n4, otape + nc, t + dt, dt, v, w, D);
+  if (rc) return rc;
+  // Y1 = X1 - dt F(X1), X1 = U^n
+  rc = adj_stage<Real>(h, tape, otape, t, dt, w, v, D);
+  if (rc) return rc;
+  k_lincomb<<<nb, 256, 0, h->stream>>>(out, 1.0, mu, 1.0, v, (long long)n4);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return GPMOOD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
+  if (!h || !otape || !(dt > 0.0)) return GPMOOD_E_INVAL;
+  if (!h->has_state) return GPMOOD_E_NOSTATE;
+  return h->precision == GPMOOD_FP32 ? frozen_step<float>(h, otape, dt, h->dw32)
+                                     : frozen_step<double>(h, otape, dt, h->dw64);
+}
+
+int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
+                        const double* lam_in, double* lam_out) {
+  if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0)) return GPMOOD_E_INVAL;
+  int rc = adj_buffers(h);
+  if (rc) return rc;
+  return h->precision == GPMOOD_FP32
+             ? step_adjoint<float>(h, tape, otape, dt, t, lam_in, lam_out, h->dw32)
+             : step_adjoint<double>(h, tape, otape, dt, t, lam_in, lam_out, h->dw64);
 }
 
 }  // extern "C"

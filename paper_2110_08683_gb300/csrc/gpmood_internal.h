@@ -115,6 +115,14 @@ struct MoodArgs {
   Scalars* sc;
 };
 
+// state adjoints of the faces, [v][g][face]; faces of one direction
+struct AdjFaces {
+  void* L;        // Real, state adjoints of the left/lower cell
+  void* R;        // Real, of the right/upper cell
+  uint8_t* K;     // EDP1 radius per face
+  long long nf;   // faces of this direction
+};
+
 // one problem of a batch: its grid, detection constants, second-derivative
 // weights (physical units, so per grid) and its place in the pooled buffers
 struct Prob {

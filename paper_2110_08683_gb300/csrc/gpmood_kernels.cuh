@@ -878,6 +878,63 @@ __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs
 }
 
 // ---------------------------------------------------------------------------
+// replay of a step with given radii (no detection): every face at the EDP1
+// radius of a radius map, then candidate + RK combination
+// ---------------------------------------------------------------------------
+template <class Real, int DIR>
+__global__ void __launch_bounds__(128) k_faces_frozen(StageArgs<Real> A, Grid g,
+                                                      const __grid_constant__ DirectW<Real> Wd) {
+  const long long nf = DIR == 0 ? (long long)(g.nx + 1) * g.ny : (long long)g.nx * (g.ny + 1);
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  int iL, jL;
+  if (DIR == 0) {
+    iL = (int)(f % (g.nx + 1)) - 1;
+    jL = (int)(f / (g.nx + 1));
+  } else {
+    iL = (int)(f % g.nx);
+    jL = (int)(f / g.nx) - 1;
+  }
+  const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
+  auto rad = [&](int i, int j) -> int {
+    if (i < 0 || i >= g.nx) {
+      if (!g.periodic_x) return Wd.top;
+      i = wrapi(i, g.nx);
+    }
+    if (j < 0 || j >= g.ny) {
+      if (!g.periodic_y) return Wd.top;
+      j = wrapi(j, g.ny);
+    }
+    return A.ord[cidx(g, i, j)];
+  };
+  const int a = rad(iL, jL), b = rad(iR, jR);
+  const int K = a < b ? a : b;
+  Real F[4];
+  bool bl, br;
+  switch (K) {
+    case 0: face_at<0, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    case 1: face_at<1, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    case 2: face_at<2, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    default: face_at<3, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    if (DIR == 0) A.Fx[fxidx(g, v, iR, jL)] = F[v];
+    else A.Fy[fyidx(g, v, iL, jR)] = F[v];
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_update_frozen(StageArgs<Real> A, Grid g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  double Y[4];
+  candidate<Real>(A, g, i, j, A.sc->dt, Y);
+  combine_store<Real>(A, g, i, j, Y);
+}
+
+// ---------------------------------------------------------------------------
 // batched kernels: many independent problems of uneven sizes in one
 // persistent launch per kernel class.  Each block walks a list of work items
 // (problem, block coordinates); the problem's grid is staged in shared

@@ -19,6 +19,18 @@ struct Launch {
                                  const Detect& D, const DirectW<Real>& Wd, cudaStream_t st);
 };
 
+// replay with given radii, and the reverse-mode passes of the adjoint
+template <class Real>
+struct LaunchA {
+  static cudaError_t frozen_stage(const StageArgs<Real>& A, const Grid& g,
+                                  const DirectW<Real>& Wd, cudaStream_t st);
+  static cudaError_t adj_faces(const double* X, const double* v, const uint8_t* ord,
+                               const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
+                               const AdjFaces& Ay, cudaStream_t st);
+  static cudaError_t adj_gather(const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
+                                const AdjFaces& Ay, double* G, cudaStream_t st);
+};
+
 // batched launchers: persistent grids walking work-item lists
 template <class Real>
 struct LaunchB {

@@ -3,3 +3,4 @@
 #include "kernels_impl.cuh"
 template struct gpm::Launch<float>;
 template struct gpm::LaunchB<float>;
+template struct gpm::LaunchA<float>;

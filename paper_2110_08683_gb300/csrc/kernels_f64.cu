@@ -2,3 +2,4 @@
 #include "kernels_impl.cuh"
 template struct gpm::Launch<double>;
 template struct gpm::LaunchB<double>;
+template struct gpm::LaunchA<double>;

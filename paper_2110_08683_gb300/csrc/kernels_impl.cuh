@@ -1,6 +1,7 @@
 // kernels_impl.cuh -- launcher bodies, instantiated once per precision.
 #pragma once
 
+#include "adjoint_kernels.cuh"
 #include "gpmood_kernels.cuh"
 #include "gpmood_launch.h"
 
@@ -132,6 +133,33 @@ cudaError_t LaunchB<Real>::mood_update(const StageArgs<Real>& B, const MoodArgs&
                                        const Prob* probs, const Scalars* psc, int nprob,
                                        const DirectW<Real>& Wd, cudaStream_t st) {
   k_mood_update_batch<Real><<<kMoodBlocks, 256, 0, st>>>(B, M, probs, psc, nprob, Wd);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t LaunchA<Real>::frozen_stage(const StageArgs<Real>& A, const Grid& g,
+                                        const DirectW<Real>& Wd, cudaStream_t st) {
+  const long long nfx = (long long)(g.nx + 1) * g.ny, nfy = (long long)g.nx * (g.ny + 1);
+  k_faces_frozen<Real, 0><<<(int)((nfx + 127) / 128), 128, 0, st>>>(A, g, Wd);
+  k_faces_frozen<Real, 1><<<(int)((nfy + 127) / 128), 128, 0, st>>>(A, g, Wd);
+  k_update_frozen<Real><<<dim3((g.nx + 31) / 32, (g.ny + 7) / 8), dim3(32, 8), 0, st>>>(A, g);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t LaunchA<Real>::adj_faces(const double* X, const double* v, const uint8_t* ord,
+                                     const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
+                                     const AdjFaces& Ay, cudaStream_t st) {
+  k_adj_faces<Real, 0><<<(int)((Ax.nf + 127) / 128), 128, 0, st>>>(X, v, ord, g, Wd, Ax);
+  k_adj_faces<Real, 1><<<(int)((Ay.nf + 127) / 128), 128, 0, st>>>(X, v, ord, g, Wd, Ay);
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t LaunchA<Real>::adj_gather(const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
+                                      const AdjFaces& Ay, double* G, cudaStream_t st) {
+  const long long n = (long long)(g.nx + 2 * g.H) * (g.ny + 2 * g.H);
+  k_adj_gather<Real><<<(int)((n + 255) / 256), 256, 0, st>>>(g, Wd, Ax, Ay, G);
   return cudaGetLastError();
 }
 

@@ -258,11 +258,13 @@ def gaussian_random_field(n, corr=0.05, rms=1e-2, seed=0):
 
 
 def shear_layer(n=1024, R=2, ell_cells=12.0, cascade=None, seed=0, width=0.05, u0=0.5,
-                p0=2.5):
+                p0=2.5, ub=0.3, vb=0.2):
     """Periodic double shear layer on [0,1]^2: rho = 1 + 0.1 * prof(y),
-    u = u0 * prof(y), v = 0, p = p0, with prof = (tanh((y-1/4)/w) -
+    u = ub + u0 * prof(y), v = vb, p = p0, with prof = (tanh((y-1/4)/w) -
     tanh((y-3/4)/w))/2, plus a seeded Gaussian random field (RMS 1e-2,
-    correlation 0.05) added to the density cell averages."""
+    correlation 0.05) added to the density cell averages.  The uniform
+    background flow (ub, vb) keeps the contact speed of every face away from
+    zero, where the HLLC flux is not differentiable."""
     gamma = 1.4
 
     def prof(y):
@@ -270,7 +272,7 @@ def shear_layer(n=1024, R=2, ell_cells=12.0, cascade=None, seed=0, width=0.05, u
 
     def prim(x, y):
         pr = prof(y)
-        return 1.0 + 0.1 * pr, u0 * pr, np.zeros_like(x), p0 * np.ones_like(x)
+        return (1.0 + 0.1 * pr, ub + u0 * pr, vb * np.ones_like(x), p0 * np.ones_like(x))
 
     U = cell_average(prim, n, n, 0.0, 1.0, 0.0, 1.0, gamma)
     drho = gaussian_random_field(n, seed=seed)
