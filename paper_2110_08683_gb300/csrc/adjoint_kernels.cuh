@@ -186,7 +186,7 @@ __device__ __forceinline__ int face_radius(const Grid& g, const uint8_t* ord, in
 }
 
 template <int K, class Real, int DIR>
-__device__ void adj_face_at(const double* X, const Grid& g, const DirectW<Real>& Wd, int iL,
+__device__ void adj_face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, int iL,
                             int jL, const Real* a, Real* AL, Real* AR, long long f,
                             long long nf) {
   constexpr int Q = rule_q(K);
@@ -198,12 +198,12 @@ __device__ void adj_face_at(const double* X, const Grid& g, const DirectW<Real>&
     if (K == 0) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        UL[v] = (Real)__ldg(X + gidx(g, v, iL, jL));
-        UR[v] = (Real)__ldg(X + gidx(g, v, iR, jR));
+        UL[v] = __ldg(X + gidx(g, v, iL, jL));
+        UR[v] = __ldg(X + gidx(g, v, iR, jR));
       }
     } else {
-      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
-      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
+      recon_direct<K, Real, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
+      recon_direct<K, Real, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
     }
     Real Fb[4], bL[4] = {0, 0, 0, 0}, bR[4] = {0, 0, 0, 0};
     const Real w = Wd.w[K][q];
@@ -230,7 +230,7 @@ __device__ void adj_face_at(const double* X, const Grid& g, const DirectW<Real>&
 
 // pass 1: one thread per face of direction DIR
 template <class Real, int DIR>
-__global__ void __launch_bounds__(128) k_adj_faces(const double* X, const double* vin,
+__global__ void __launch_bounds__(128) k_adj_faces(const Real* X, const double* vin,
                                                    const uint8_t* ord, Grid g,
                                                    const __grid_constant__ DirectW<Real> Wd,
                                                    AdjFaces A) {
@@ -279,12 +279,12 @@ __device__ __forceinline__ int stencil_index(int K, int a, int b) {
 template <class Real>
 __device__ __forceinline__ void gather_face(const DirectW<Real>& Wd, int face, int a, int b,
                                             int K, const Real* S, long long f, long long nf,
-                                            double* acc) {
+                                            Real* acc) {
   const int ab = (a < 0 ? -a : a) + (b < 0 ? -b : b);
   if (ab > K) return;
   if (K == 0) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[v] += (double)S[(long long)v * kMaxQ * nf + f];
+    for (int v = 0; v < 4; ++v) acc[v] += S[(long long)v * kMaxQ * nf + f];
     return;
   }
   const int m = stencil_index(K, a, b);
@@ -292,7 +292,7 @@ __device__ __forceinline__ void gather_face(const DirectW<Real>& Wd, int face, i
   for (int q = 0; q < Q; ++q) {
     const Real z = Wd.z[K][face][q][m];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[v] += (double)(z * S[((long long)v * kMaxQ + q) * nf + f]);
+    for (int v = 0; v < 4; ++v) acc[v] = fma(z, S[((long long)v * kMaxQ + q) * nf + f], acc[v]);
   }
 }
 
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(Grid g, const __grid_constan
   if (t >= (long long)gx * gyy) return;
   const int ci = (int)(t % gx) - g.H, cj = (int)(t / gx) - g.H;
   const int top = Wd.top;
-  double acc[4] = {0, 0, 0, 0};
+  Real acc[4] = {0, 0, 0, 0};
   const Real* xL = (const Real*)Ax.L;
   const Real* xR = (const Real*)Ax.R;
   const Real* yL = (const Real*)Ay.L;
@@ -339,7 +339,15 @@ __global__ void __launch_bounds__(256) k_adj_gather(Grid g, const __grid_constan
     }
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) G[gidx(g, v, ci, cj)] = acc[v];
+  for (int v = 0; v < 4; ++v) G[gidx(g, v, ci, cj)] = (double)acc[v];
+}
+
+// Real copy of a ghosted state (the FP32 adjoint reads float stencils)
+template <class Real>
+__global__ void k_to_real(const double* X, Real* Y, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    Y[t] = (Real)X[t];
 }
 
 }  // namespace gpm

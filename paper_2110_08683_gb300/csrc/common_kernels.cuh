@@ -198,6 +198,30 @@ __global__ void k_adj_stage_out(double* w, const double* v, const double* G, Gri
   }
 }
 
+// tape of a recorded step: the interior of stage input s, and the radii
+// of stage s, into the destinations the step's controls name
+__global__ void k_tape_state(const double* X, Grid g, const Scalars* sc, int s) {
+  double* dst = sc->ctl.tape;
+  if (!dst) return;
+  const long long nc = (long long)g.nx * g.ny;
+  dst += (long long)s * 4 * nc;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4 * nc;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / nc);
+    const long long c = t - v * nc;
+    dst[t] = X[gidx(g, v, (int)(c % g.nx), (int)(c / g.nx))];
+  }
+}
+
+__global__ void k_tape_ord(const uint8_t* ord, const Scalars* sc, int s, long long nc) {
+  uint8_t* dst = sc->ctl.otape;
+  if (!dst) return;
+  dst += s * nc;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = ord[t];
+}
+
 // out = a x + b y (b = 0: y unused)
 __global__ void k_lincomb(double* out, double a, const double* x, double b, const double* y,
                           long long n) {

@@ -49,12 +49,13 @@ struct gpmood_s {
   // captured step graphs [buffer rotation][profiled] and their streams
   Control ctl;  // host copy of the step controls
   cudaStream_t cs, cs2;
-  cudaGraphExec_t gexec[3][2];
+  cudaGraphExec_t gexec[3][3];  // [rotation][plain, profiled, recording]
   cudaEvent_t gev[64];
   int gev_cls[32];
   int gev_n, gev_pairs;
   // adjoint work buffers (allocated on first use)
   double* aX;     // ghosted stage input
+  void* aXr;      // its float copy (FP32 adjoint)
   double* aG;     // ghosted state adjoint
   double *av, *aw, *amu;  // interior vectors
   AdjFaces ax, ay;
@@ -87,11 +88,11 @@ void free_all(gpmood_t h) {
   for (int k = 0; k < 64; ++k)
     if (h->gev[k]) cudaEventDestroy(h->gev[k]);
   for (int r = 0; r < 3; ++r)
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 3; ++p)
       if (h->gexec[r][p]) cudaGraphExecDestroy(h->gexec[r][p]);
   if (h->cs) cudaStreamDestroy(h->cs);
   if (h->cs2) cudaStreamDestroy(h->cs2);
-  void* adj[] = {h->aX, h->aG, h->av, h->aw, h->amu, h->ax.L, h->ax.R, h->ax.K,
+  void* adj[] = {h->aX, h->aXr, h->aG, h->av, h->aw, h->amu, h->ax.L, h->ax.R, h->ax.K,
                  h->ay.L, h->ay.R, h->ay.K, h->aord};
   for (void* p : adj) cudaFree(p);
   for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
@@ -134,7 +135,10 @@ int pull_scalars(gpmood_t h) {
   return 0;
 }
 
-void write_control(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+void write_control(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
+                   double* tape = nullptr, uint8_t* otape = nullptr) {
+  h->ctl.tape = tape;
+  h->ctl.otape = otape;
   h->ctl.cfl = cfl;
   h->ctl.fixed_dt = fixed_dt;
   h->ctl.clip = clip;
@@ -264,10 +268,14 @@ void rec_event(gpmood_t h, int prof, int cls, int open, cudaStream_t st) {
 
 template <class Real>
 int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
-                  const DirectW<Real>& D, int prof) {
+                  const DirectW<Real>& D, int prof, int record) {
   static const double tfrac[3] = {0.0, 1.0, 0.5};
   cudaStream_t st = h->cs;
   StageArgs<Real> A = stage_args<Real>(h, s, ia, ix, io);
+  if (record) {
+    k_tape_state<<<152 * 4, 256, 0, st>>>(h->U[ix], h->g, h->sc, s);
+    CK(cudaGetLastError());
+  }
   rec_event(h, prof, GPMOOD_K_GHOST, 1, st);
   CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], st));
   rec_event(h, prof, GPMOOD_K_GHOST, 0, st);
@@ -312,10 +320,14 @@ int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>
   CK(e1); CK(e2); CK(e3); CK(e4);
   CK(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
   rec_event(h, prof, GPMOOD_K_MOOD, 0, st);
+  if (record) {
+    k_tape_ord<<<152, 256, 0, st>>>(A.ord, h->sc, s, (long long)h->g.nx * h->g.ny);
+    CK(cudaGetLastError());
+  }
   return 0;
 }
 
-int capture_step(gpmood_t h, int cur, int prof, cudaGraphExec_t* out) {
+int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out) {
   const int a = cur, b = (a + 1) % 3, c = (a + 2) % 3;
   const int in[3] = {a, b, c}, outb[3] = {b, c, b};
   cudaStream_t st = h->cs;
@@ -327,8 +339,8 @@ int capture_step(gpmood_t h, int cur, int prof, cudaGraphExec_t* out) {
   rec_event(h, prof, GPMOOD_K_DT, 0, st);
   for (int s = 0; s < 3 && !rc; ++s)
     rc = h->precision == GPMOOD_FP32
-             ? capture_stage<float>(h, s, a, in[s], outb[s], h->pw32, h->dw32, prof)
-             : capture_stage<double>(h, s, a, in[s], outb[s], h->pw64, h->dw64, prof);
+             ? capture_stage<float>(h, s, a, in[s], outb[s], h->pw32, h->dw32, prof, record)
+             : capture_stage<double>(h, s, a, in[s], outb[s], h->pw64, h->dw64, prof, record);
   if (!rc && launch_finish(h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -341,15 +353,17 @@ int capture_step(gpmood_t h, int cur, int prof, cudaGraphExec_t* out) {
   return GPMOOD_OK;
 }
 
-int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
+               double* tape = nullptr, uint8_t* otape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
-  const int prof = h->prof_on ? 1 : 0;
-  cudaGraphExec_t& ge = h->gexec[h->cur][prof];
+  const int record = tape ? 1 : 0;
+  const int prof = (h->prof_on && !record) ? 1 : 0;
+  cudaGraphExec_t& ge = h->gexec[h->cur][record ? 2 : prof];
   if (!ge) {
-    int rc = capture_step(h, h->cur, prof, &ge);
+    int rc = capture_step(h, h->cur, prof, record, &ge);
     if (rc) return rc;
   }
-  write_control(h, cfl, fixed_dt, clip, t_end);
+  write_control(h, cfl, fixed_dt, clip, t_end, tape, otape);
   int rc = push_control(h);
   if (rc) return rc;
   CK(cudaGraphLaunch(ge, h->stream));
@@ -735,7 +749,8 @@ int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
 int gpmood_step_record(gpmood_t h, double cfl, double dt_fixed, double* tape, uint8_t* otape,
                        double* dt_out) {
   if (!h || !tape || !otape || (!(cfl > 0.0) && !(dt_fixed > 0.0))) return GPMOOD_E_INVAL;
-  int rc = do_step(h, cfl > 0.0 ? cfl : 1.0, dt_fixed > 0.0 ? dt_fixed : 0.0, 0, 0.0, tape, otape);
+  int rc = graph_step(h, cfl > 0.0 ? cfl : 1.0, dt_fixed > 0.0 ? dt_fixed : 0.0, 0, 0.0, tape,
+                      otape);
   if (rc) return rc;
   if (dt_out) *dt_out = h->hsc->dt;
   return GPMOOD_OK;
@@ -777,6 +792,7 @@ int adj_buffers(gpmood_t h) {
   h->ax.nf = (long long)(g.nx + 1) * g.ny;
   h->ay.nf = (long long)g.nx * (g.ny + 1);
   bool ok = cudaMalloc(&h->aX, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess &&
+            cudaMalloc(&h->aXr, rs * 4 * (size_t)g.vstride) == cudaSuccess &&
             cudaMalloc(&h->aG, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess &&
             cudaMalloc(&h->av, sizeof(double) * 4 * nc) == cudaSuccess &&
             cudaMalloc(&h->aw, sizeof(double) * 4 * nc) == cudaSuccess &&
@@ -810,7 +826,7 @@ int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, doubl
   const int gb = (int)((ngh + 255) / 256);
   k_fill_ghosts_at<<<gb, 256, 0, h->stream>>>(h->aX, g, ts);
   CK(cudaGetLastError());
-  CK(LaunchA<Real>::adj_faces(h->aX, v, ords, g, D, h->ax, h->ay, h->stream));
+  CK(LaunchA<Real>::adj_faces(h->aX, h->aXr, v, ords, g, D, h->ax, h->ay, h->stream));
   CK(LaunchA<Real>::adj_gather(g, D, h->ax, h->ay, h->aG, h->stream));
   k_adj_fold<<<gb, 256, 0, h->stream>>>(h->aG, g);
   k_adj_stage_out<<<152 * 8, 256, 0, h->stream>>>(w, v, h->aG, g, dt);

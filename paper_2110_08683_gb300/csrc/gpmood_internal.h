@@ -35,6 +35,8 @@ struct Control {
   double t_end;      // clip target when clip != 0
   int clip;
   int max_iters;     // MOOD iteration cap per stage
+  double* tape;      // recorded steps: stage inputs [3][4][ny][nx] (or null)
+  uint8_t* otape;    // and the final radii [3][ny][nx]
 };
 
 // scalars living on the device (one per handle)

@@ -672,13 +672,13 @@ __device__ __forceinline__ void radius_pair(const Grid& g, const uint8_t* ord, c
 }
 
 // direct reconstruction of one face state at radius K (eq. gp_reconstructor)
-template <int K, class Real>
-__device__ __forceinline__ void recon_direct(const double* X, const Grid& g, const Real* z, int i,
+// T: storage type of the ghosted state (double, or a float copy)
+template <int K, class Real, class T = double>
+__device__ __forceinline__ void recon_direct(const T* X, const Grid& g, const Real* z, int i,
                                              int j, Real* S) {
-  constexpr int N = stencil_n(K);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    const double* Xv = X + (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
+    const T* Xv = X + (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
     Real s = Real(0);
     int m = 0;
 #pragma unroll

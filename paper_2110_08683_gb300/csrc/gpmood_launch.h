@@ -24,7 +24,8 @@ template <class Real>
 struct LaunchA {
   static cudaError_t frozen_stage(const StageArgs<Real>& A, const Grid& g,
                                   const DirectW<Real>& Wd, cudaStream_t st);
-  static cudaError_t adj_faces(const double* X, const double* v, const uint8_t* ord,
+  // X: the ghosted stage input in Real (converted into Xr when Real is float)
+  static cudaError_t adj_faces(const double* X, void* Xr, const double* v, const uint8_t* ord,
                                const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
                                const AdjFaces& Ay, cudaStream_t st);
   static cudaError_t adj_gather(const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,

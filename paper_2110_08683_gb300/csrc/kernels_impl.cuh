@@ -147,11 +147,18 @@ cudaError_t LaunchA<Real>::frozen_stage(const StageArgs<Real>& A, const Grid& g,
 }
 
 template <class Real>
-cudaError_t LaunchA<Real>::adj_faces(const double* X, const double* v, const uint8_t* ord,
-                                     const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
-                                     const AdjFaces& Ay, cudaStream_t st) {
-  k_adj_faces<Real, 0><<<(int)((Ax.nf + 127) / 128), 128, 0, st>>>(X, v, ord, g, Wd, Ax);
-  k_adj_faces<Real, 1><<<(int)((Ay.nf + 127) / 128), 128, 0, st>>>(X, v, ord, g, Wd, Ay);
+cudaError_t LaunchA<Real>::adj_faces(const double* X, void* Xr, const double* v,
+                                     const uint8_t* ord, const Grid& g, const DirectW<Real>& Wd,
+                                     const AdjFaces& Ax, const AdjFaces& Ay, cudaStream_t st) {
+  const Real* XR;
+  if (sizeof(Real) == sizeof(double)) {
+    XR = (const Real*)X;
+  } else {
+    k_to_real<Real><<<152 * 8, 256, 0, st>>>(X, (Real*)Xr, 4 * g.vstride);
+    XR = (const Real*)Xr;
+  }
+  k_adj_faces<Real, 0><<<(int)((Ax.nf + 127) / 128), 128, 0, st>>>(XR, v, ord, g, Wd, Ax);
+  k_adj_faces<Real, 1><<<(int)((Ay.nf + 127) / 128), 128, 0, st>>>(XR, v, ord, g, Wd, Ay);
   return cudaGetLastError();
 }
 
