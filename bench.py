@@ -69,15 +69,22 @@ def kernel_source_hash():
 def ncu_traffic(precision):
     """DRAM bytes per launch of the x-face kernel from the committed ncu
     summary, or None when the kernel sources changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "faces_x_traffic.json")
+    path = os.path.join(ROOT, "profiles", "faces_x_traffic.md")
     try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
+        lines = open(path).read().splitlines()
+    except OSError:
         return None
-    ent = rec.get(precision)
-    if not ent or ent.get("kernel_sha") != kernel_source_hash():
-        return None
-    return ent.get("dram_bytes_per_launch")
+    # table rows: | precision | kernel sources sha256 | DRAM bytes per launch | ...
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == precision:
+            if cells[1] != kernel_source_hash():
+                return None
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
 
 
 class ClockSampler:
@@ -203,7 +210,7 @@ def run_ours(args, world, rank, local):
     dev_index = local
     n = args.n
     p = workload(n)
-    g = gp.GPMood(p, args.precision)
+    g = gp.GPMood(p, args.precision, eager=args.eager)
     stream = torch.cuda.Stream()
     g.set_stream(stream.cuda_stream)
     # L2 (129 MB) is flushed between timed steps by writing 256 MB
@@ -218,12 +225,13 @@ def run_ours(args, world, rank, local):
     sampler = ClockSampler(dev_index)
     # the step graphs (one per buffer rotation) of the profiled variant are
     # captured on first use: do that before the timed region, then reset
-    g.profile(True)
+    prof = not args.eager  # per-kernel events exist in the graph mode only
+    g.profile(prof)
     with torch.cuda.stream(stream):
         for _ in range(3):
             g.step()
     torch.cuda.synchronize()
-    g.profile(True)
+    g.profile(prof)
     launches = 0
     barrier(world)
     torch.cuda.synchronize()
@@ -269,14 +277,14 @@ def run_ours(args, world, rank, local):
            "h2d_bytes_per_step": int(Uh.nbytes), "d2h_bytes_per_step": int(Uo.nbytes)}
 
     # roofline of the dominant kernel: the first-pass x-face kernel
-    fx_ms, fx_n = kt["faces_x"]
+    fx_ms, fx_n = kt["faces_x"] if prof else (0.0, 0)
     per_launch_s = fx_ms / 1e3 / max(fx_n, 1)
     faces = (n + 1) * n
     flops = faces * faces_flops_per_face(3)
     real64 = args.precision == "fp64"
     peak = FP64_PEAK_TFLOPS if real64 else FP32_PEAK_TFLOPS
-    achieved = flops / per_launch_s / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
+    achieved = flops / per_launch_s / 1e12 if prof else 0.0
+    roofline = None if not prof else {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                 "traffic": ncu_traffic(args.precision),
                 "kernel": "k_faces<R=3,%s,x>" % ("double" if real64 else "float"),
@@ -300,7 +308,8 @@ def run_ours(args, world, rank, local):
                    "cells": n * n, "precision": args.precision,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
         "roofline": roofline,
-        "kernel_shares": shares,
+        "kernel_shares": shares if prof else None,
+        "launch_mode": "eager" if args.eager else "graph",
         "gpu_launches": int(allreduce_sum(launches, world)),
         "e2e": e2e,
     }
@@ -318,7 +327,7 @@ def run_batch(args, world, rank, local):
     torch.cuda.set_device(0 if world > 1 else local)
     probs = I.quadrant_batch(count=args.batch, seed=0)
     cells = sum(q["nx"] * q["ny"] for q in probs)
-    b = gp.GPMoodBatch(probs, args.precision)
+    b = gp.GPMoodBatch(probs, args.precision, eager=args.eager)
     stream = torch.cuda.Stream()
     b.set_stream(stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -367,8 +376,10 @@ def run_batch(args, world, rank, local):
 
 def run_adjoint(args, world, rank, local):
     """Forward rollout and its reverse mode on the smooth periodic shear layer
-    (GP-R2, MOOD radii frozen from the forward, 200 steps, checkpoints every
-    20): the adjoint/forward time ratio."""
+    (GP-R2, MOOD radii frozen from the forward, 200 steps), once with
+    checkpoints every 20 steps and segments stepped again in the reverse
+    pass, once with every step's tape kept resident: the reverse pass's time
+    over that of the plain forward rollout."""
     import torch
 
     import paper_2110_08683_gb300 as gp
@@ -378,7 +389,7 @@ def run_adjoint(args, world, rank, local):
     torch.cuda.set_device(0 if world > 1 else local)
     n = args.n
     p = I.shear_layer(n=n, R=2, seed=0)
-    g = gp.GPMood(p, args.precision)
+    g = gp.GPMood(p, args.precision, eager=args.eager)
     U0 = torch.tensor(p["U0"], device="cuda")
     c = (torch.arange(n, dtype=torch.float64, device="cuda") + 0.5) / n
     Yc, Xc = torch.meshgrid(c, c, indexing="ij")
@@ -387,18 +398,32 @@ def run_adjoint(args, world, rank, local):
     g.set_state(p["U0"])
     for _ in range(args.warmup):
         g.step()
+    # an untimed short rollout and its reverse mode in both tape strategies:
+    # captures the recording graphs and allocates the adjoint buffers
+    for every in (None, 20):
+        Uw = U0.clone().requires_grad_()
+        (rollout(Uw, g, max(args.warmup, 3), every=every) * W).sum().backward()
     torch.cuda.synchronize()
     steps = args.adjoint_steps
-    U0r = U0.clone().requires_grad_()
-    t0 = time.perf_counter()
-    UN = rollout(U0r, g, steps, every=20)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    J = (UN * W).sum()
-    J.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    fwd, bwd = t1 - t0, t2 - t1
+    modes = {}
+    for name, every in (("checkpoints_every_20", 20), ("resident_tapes", None)):
+        U0r = U0.clone().requires_grad_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        UN = rollout(U0r, g, steps, every=every)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J = (UN * W).sum()
+        J.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        modes[name] = {"forward_s": t1 - t0, "backward_s": t2 - t1,
+                       "grad_norm": float(U0r.grad.norm())}
+        del UN, J, U0r
+    # the forward cost: the rollout that keeps only checkpoints (plain steps)
+    fwd = modes["checkpoints_every_20"]["forward_s"]
+    for m in modes.values():
+        m["backward_over_plain_forward"] = m["backward_s"] / fwd
     return {
         "metric": METRIC, "value": n * n * steps / fwd, "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": fwd * 1e3 / steps,
@@ -406,10 +431,9 @@ def run_adjoint(args, world, rank, local):
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"periodic double shear layer {n}^2 with a seeded random density "
                                f"field, GP-R2 cascade 5->3->1, ell=12dx, {steps} steps, "
-                               "checkpoints every 20, J = integral of rho over [0.4,0.6]^2",
+                               "J = integral of rho over [0.4,0.6]^2",
                    "cells": n * n, "precision": args.precision},
-        "adjoint": {"forward_s": fwd, "backward_s": bwd, "ratio": bwd / fwd,
-                    "grad_norm": float(U0r.grad.norm())},
+        "adjoint": modes,
     }
 
 
@@ -463,6 +487,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch kernels one by one instead of the step graphs (for per-kernel "
+                         "profilers; slower, no per-kernel event timing)"),
     ap.add_argument("--adjoint", action="store_true",
                     help="time a rollout and its adjoint instead (shear layer, GP-R2)")
     ap.add_argument("--adjoint-steps", type=int, default=200)

@@ -80,6 +80,12 @@ typedef struct {
   double sigma_p;       /* CSD threshold on the normalised |grad p| (0 -> 5) */
   int csd_off;          /* 1 disables CSD (Step 6) */
   int max_mood_iters;   /* cap on MOOD iterations per RK stage (0 -> 64 + 4 max(nx, ny)) */
+  int eager;            /* 0: one captured CUDA graph per step, the MOOD loop of each stage
+                           a conditional WHILE node (no host round trip in a step);
+                           1: every kernel launched on the stream and the host reading the
+                           loop decision after each MOOD iteration.  Same kernels, same
+                           results; slower, but visible kernel by kernel to profilers
+                           that cannot look inside graphs with conditional nodes */
 } gpmood_options;
 
 /* per-step diagnostics of the most recent step */

@@ -46,7 +46,7 @@ class Options(C.Structure):
     _fields_ = [
         ("ncascade", C.c_int), ("cascade", C.c_int * 4), ("precision", C.c_int),
         ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
-        ("max_mood_iters", C.c_int),
+        ("max_mood_iters", C.c_int), ("eager", C.c_int),
     ]
 
 
@@ -137,7 +137,7 @@ def make_grid(prob):
     return g
 
 
-def make_options(prob, precision=FP64):
+def make_options(prob, precision=FP64, eager=False):
     o = Options()
     cas = list(prob["cascade"])
     o.ncascade = len(cas)
@@ -147,6 +147,7 @@ def make_options(prob, precision=FP64):
     o.sigma_v, o.sigma_p = prob["sigma_v"], prob["sigma_p"]
     o.csd_off = 0 if prob["csd_on"] else 1
     o.max_mood_iters = int(prob.get("max_iters", 0))
+    o.eager = 1 if eager else 0
     return o
 
 
@@ -258,13 +259,13 @@ def gpmood_kernel_times(h):
 class GPMood:
     """One GP-MOOD problem on the GPU: a handle of the C ABI."""
 
-    def __init__(self, prob, precision="fp64"):
+    def __init__(self, prob, precision="fp64", eager=False):
         self.prob = prob
         self.nx, self.ny = int(prob["nx"]), int(prob["ny"])
         self.precision = FP32 if precision in ("fp32", FP32) else FP64
         cas = list(prob["cascade"])
         self.h = gpmood_create(make_grid(prob), prob["gamma"], cas[0], prob["ell"],
-                               make_options(prob, self.precision))
+                               make_options(prob, self.precision, eager))
 
     def close(self):
         if getattr(self, "h", None):
@@ -338,7 +339,7 @@ class GPMoodBatch:
     probs: problem dicts from ``inputs`` that share gamma, the cascade, the
     options and ell/dx, ell/dy."""
 
-    def __init__(self, probs, precision="fp64"):
+    def __init__(self, probs, precision="fp64", eager=False):
         self.probs = list(probs)
         self.n = len(self.probs)
         self.shapes = [(int(q["ny"]), int(q["nx"])) for q in self.probs]
@@ -346,7 +347,7 @@ class GPMoodBatch:
         grids = (Grid * self.n)(*[make_grid(q) for q in self.probs])
         ells = (C.c_double * self.n)(*[q["ell"] for q in self.probs])
         q0 = self.probs[0]
-        opts = make_options(q0, self.precision)
+        opts = make_options(q0, self.precision, eager)
         h = C.c_void_p()
         _check(load().gpmood_batch_create(grids, self.n, q0["gamma"], list(q0["cascade"])[0],
                                           ells, C.byref(opts), C.byref(h)), "gpmood_batch_create")

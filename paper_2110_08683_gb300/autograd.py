@@ -1,51 +1,94 @@
 """Reverse mode of a GP-MOOD rollout as a torch.autograd.Function.
 
-Forward: N steps of the CUDA path (CFL time steps), keeping the state every
-`every` steps (checkpoints) and every step's dt.  Backward: segment by
-segment from the last, the segment is stepped again from its checkpoint with
-the recorded dt's, which reproduces the forward bit for bit (the same
-kernels, so the same MOOD decisions), recording each step's tape (stage
-inputs and radii); then the hand-written adjoint of each step runs in
-reverse with the radii and dt held at their forward values.  Torch only
-provides the device memory.
+Every step's tape is its three stage inputs and the final radii of its three
+stages (12 + 3/8 doubles a cell).  The reverse pass needs the tapes in
+reverse order; where they fit in the memory budget the forward records them
+all as it goes (the forward then costs the same as a plain rollout plus the
+tape writes), otherwise the forward keeps the state every `every` steps
+(checkpoints) and every step's dt, and the reverse pass steps each segment
+again from its checkpoint with the recorded dt's, which reproduces the
+forward bit for bit (the same kernels, so the same MOOD decisions), recording
+its tapes.  Then the hand-written adjoint of each step runs in reverse with
+the radii and dt held at their forward values.  Torch only provides the
+device memory.
 """
 from __future__ import annotations
 
 import torch
 
 
+def tape_bytes(model):
+    """device bytes of one step's tape"""
+    nc = model.nx * model.ny
+    return 3 * 4 * nc * 8 + 3 * nc
+
+
+def default_budget():
+    """half of the device memory free now"""
+    free, _ = torch.cuda.mem_get_info()
+    return free // 2
+
+
 class Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U0, model, nsteps, every, cfl):
+    def forward(ctx, U0, model, nsteps, every, cfl, budget):
         assert U0.is_cuda and U0.dtype == torch.float64 and U0.is_contiguous()
+        ny, nx = model.ny, model.nx
+        dev = U0.device
+        if budget is None:
+            budget = default_budget()
+        resident = every is None and nsteps * tape_bytes(model) <= budget
+        if every is None:
+            # checkpoints (one state each) plus one segment of tapes in the budget
+            every = max(1, min(nsteps, int(budget // max(tape_bytes(model), 1)) // 2))
         model.set_state(U0.detach())
         ckpts, dts, ts = [], [], []
+        tape = otape = None
+        if resident:
+            tape = torch.empty((nsteps, 3, 4, ny, nx), dtype=torch.float64, device=dev)
+            otape = torch.empty((nsteps, 3, ny, nx), dtype=torch.uint8, device=dev)
         t = 0.0
         for k in range(nsteps):
-            if k % every == 0:
+            if not resident and k % every == 0:
                 c = torch.empty_like(U0)
                 model.get_state(c)
                 ckpts.append((k, c, t))
-            dt = model.step(cfl, want_dt=True)
+            if resident:
+                dt = model.step_record(tape[k].data_ptr(), otape[k].data_ptr(), cfl=cfl)
+            else:
+                dt = model.step(cfl, want_dt=True)
             dts.append(dt)
             ts.append(t)
             t += dt
         out = torch.empty_like(U0)
         model.get_state(out)
-        ctx.model, ctx.nsteps, ctx.every = model, nsteps, every
+        ctx.model, ctx.nsteps, ctx.every, ctx.resident = model, nsteps, every, resident
         ctx.ckpts, ctx.dts, ctx.ts = ckpts, dts, ts
+        ctx.tape, ctx.otape = tape, otape
         return out
 
     @staticmethod
     def backward(ctx, gout):
-        model, every = ctx.model, ctx.every
-        ny, nx = model.ny, model.nx
-        dev = gout.device
+        model = ctx.model
         lam = gout.contiguous().clone()
         tmp = torch.empty_like(lam)
-        tape = torch.empty((every, 3, 4, ny, nx), dtype=torch.float64, device=dev)
-        otape = torch.empty((every, 3, ny, nx), dtype=torch.uint8, device=dev)
+
+        def reverse(tape, otape, k0, k1):
+            nonlocal lam, tmp
+            for k in reversed(range(k0, k1)):
+                model.step_adjoint(tape[k - k0].data_ptr(), otape[k - k0].data_ptr(),
+                                   ctx.dts[k], ctx.ts[k], lam.data_ptr(), tmp.data_ptr())
+                lam, tmp = tmp, lam
+
         torch.cuda.synchronize()
+        if ctx.resident:
+            reverse(ctx.tape, ctx.otape, 0, ctx.nsteps)
+            ctx.tape = ctx.otape = None
+            return lam, None, None, None, None, None
+        every = ctx.every
+        ny, nx = model.ny, model.nx
+        tape = torch.empty((every, 3, 4, ny, nx), dtype=torch.float64, device=gout.device)
+        otape = torch.empty((every, 3, ny, nx), dtype=torch.uint8, device=gout.device)
         for k0, U, t0 in reversed(ctx.ckpts):
             k1 = min(k0 + every, ctx.nsteps)
             model.set_state(U)
@@ -53,13 +96,16 @@ class Rollout(torch.autograd.Function):
             for k in range(k0, k1):
                 model.step_record(tape[k - k0].data_ptr(), otape[k - k0].data_ptr(),
                                   dt=ctx.dts[k])
-            for k in reversed(range(k0, k1)):
-                model.step_adjoint(tape[k - k0].data_ptr(), otape[k - k0].data_ptr(), ctx.dts[k],
-                                   ctx.ts[k], lam.data_ptr(), tmp.data_ptr())
-                lam, tmp = tmp, lam
-        return lam, None, None, None, None
+            reverse(tape, otape, k0, k1)
+        return lam, None, None, None, None, None
 
 
-def rollout(U0, model, nsteps, every=20, cfl=None):
-    """U_N of `nsteps` CFL steps from U0 (CUDA float64 (4, ny, nx)), differentiable."""
-    return Rollout.apply(U0, model, nsteps, every, model.prob["cfl"] if cfl is None else cfl)
+def rollout(U0, model, nsteps, every=None, cfl=None, budget=None):
+    """U_N of `nsteps` CFL steps from U0 (CUDA float64 (4, ny, nx)), differentiable.
+
+    every=None: keep all tapes resident when nsteps tapes fit in `budget`
+    bytes (default: half the free device memory), else checkpoint segments
+    sized to the budget.  every=k: checkpoints every k steps, segments
+    recomputed in the reverse pass."""
+    return Rollout.apply(U0, model, nsteps, every,
+                         model.prob["cfl"] if cfl is None else cfl, budget)

@@ -185,6 +185,35 @@ __device__ __forceinline__ int face_radius(const Grid& g, const uint8_t* ord, in
   return a < b ? a : b;
 }
 
+// reverse mode of one Gauss point q of a face: states UL / UR, flux adjoint
+// w_q a; the state adjoints go to the face's slots of A.L / A.R
+template <class Real, int DIR>
+__device__ __forceinline__ void adj_point(const Real* UL, const Real* UR, Real gam, Real w,
+                                          const Real* a, int q, Real* AL, Real* AR, long long f,
+                                          long long nf) {
+  Real bL[4] = {0, 0, 0, 0}, bR[4] = {0, 0, 0, 0};
+  if (DIR == 0) {
+    Real Fb[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Fb[v] = w * a[v];
+    hllc_x_vjp<Real>(UL, UR, gam, Fb, bL, bR);
+  } else {
+    // y faces: HLLC on (rho, rho v, rho u, E); the flux comes back swapped
+    Real sL[4] = {UL[0], UL[2], UL[1], UL[3]}, sR[4] = {UR[0], UR[2], UR[1], UR[3]};
+    Real sFb[4] = {w * a[0], w * a[2], w * a[1], w * a[3]};
+    Real tL[4] = {0, 0, 0, 0}, tR[4] = {0, 0, 0, 0};
+    hllc_x_vjp<Real>(sL, sR, gam, sFb, tL, tR);
+    bL[0] = tL[0]; bL[1] = tL[2]; bL[2] = tL[1]; bL[3] = tL[3];
+    bR[0] = tR[0]; bR[1] = tR[2]; bR[2] = tR[1]; bR[3] = tR[3];
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    AL[((long long)v * kMaxQ + q) * nf + f] = bL[v];
+    AR[((long long)v * kMaxQ + q) * nf + f] = bR[v];
+  }
+}
+
+// a face of radius K below the top: states by the direct weights
 template <int K, class Real, int DIR>
 __device__ void adj_face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, int iL,
                             int jL, const Real* a, Real* AL, Real* AR, long long f,
@@ -205,66 +234,84 @@ __device__ void adj_face_at(const Real* X, const Grid& g, const DirectW<Real>& W
       recon_direct<K, Real, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
       recon_direct<K, Real, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
     }
-    Real Fb[4], bL[4] = {0, 0, 0, 0}, bR[4] = {0, 0, 0, 0};
-    const Real w = Wd.w[K][q];
-    if (DIR == 0) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) Fb[v] = w * a[v];
-      hllc_x_vjp<Real>(UL, UR, gam, Fb, bL, bR);
-    } else {
-      // y faces: HLLC on (rho, rho v, rho u, E); the flux comes back swapped
-      Real sL[4] = {UL[0], UL[2], UL[1], UL[3]}, sR[4] = {UR[0], UR[2], UR[1], UR[3]};
-      Real sFb[4] = {w * a[0], w * a[2], w * a[1], w * a[3]};
-      Real tL[4] = {0, 0, 0, 0}, tR[4] = {0, 0, 0, 0};
-      hllc_x_vjp<Real>(sL, sR, gam, sFb, tL, tR);
-      bL[0] = tL[0]; bL[1] = tL[2]; bL[2] = tL[1]; bL[3] = tL[3];
-      bR[0] = tR[0]; bR[1] = tR[2]; bR[2] = tR[1]; bR[3] = tR[3];
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      AL[((long long)v * kMaxQ + q) * nf + f] = bL[v];
-      AR[((long long)v * kMaxQ + q) * nf + f] = bR[v];
-    }
+    adj_point<Real, DIR>(UL, UR, gam, Wd.w[K][q], a, q, AL, AR, f, nf);
   }
 }
 
-// pass 1: one thread per face of direction DIR
-template <class Real, int DIR>
-__global__ void __launch_bounds__(128) k_adj_faces(const Real* X, const double* vin,
-                                                   const uint8_t* ord, Grid g,
-                                                   const __grid_constant__ DirectW<Real> Wd,
-                                                   AdjFaces A) {
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= A.nf) return;
-  int iL, jL, iR, jR;
-  if (DIR == 0) {  // x face i (0..nx) of row j
-    const int i = (int)(f % (g.nx + 1)), j = (int)(f / (g.nx + 1));
-    iL = i - 1; jL = j; iR = i; jR = j;
-  } else {         // y face j (0..ny) of column i
-    const int i = (int)(f % g.nx), j = (int)(f / g.nx);
-    iL = i; jL = j - 1; iR = i; jR = j;
-  }
-  const int K = face_radius(g, ord, Wd.top, iL, jL, iR, jR);
-  A.K[f] = (uint8_t)K;
+// flux adjoint of the face between (iL,jL) and (iR,jR): (v_L - v_R)/dx (or
+// /dy); ghost sides carry none
+template <int DIR>
+__device__ __forceinline__ void face_cotangent(const double* vin, const Grid& g, int iL, int jL,
+                                               int iR, int jR, double* a) {
   const long long nc = (long long)g.nx * g.ny;
   const bool inL = iL >= 0 && iL < g.nx && jL >= 0 && jL < g.ny;
   const bool inR = iR >= 0 && iR < g.nx && jR >= 0 && jR < g.ny;
-  const Real inv = (Real)(DIR == 0 ? g.inv_dx : g.inv_dy);
-  Real a[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const double vl = inL ? vin[v * nc + cidx(g, iL, jL)] : 0.0;
     const double vr = inR ? vin[v * nc + cidx(g, iR, jR)] : 0.0;
-    a[v] = (Real)((vl - vr) * (DIR == 0 ? g.inv_dx : g.inv_dy));
+    a[v] = (vl - vr) * (DIR == 0 ? g.inv_dx : g.inv_dy);
   }
-  (void)inv;
+}
+
+// pass 1 on the sweep layout of the first-pass face kernel: one warp per
+// row (x faces) or column (y faces) of a 31-face segment, the stencils
+// staged in shared memory and the top-radius face states formed from the
+// parity sums of each cell; faces whose frozen radius is below the top
+// reconstruct with the direct weights of their radius
+template <int R, class Real, int DIR, int FW>
+__global__ void __launch_bounds__(32 * FW) k_adj_faces_sweep(
+    const Real* X, const double* vin, const uint8_t* ord, Grid g,
+    const __grid_constant__ ParityW<Real> W, const __grid_constant__ DirectW<Real> Wd,
+    AdjFaces A) {
+  constexpr int Q = rule_q(R);
+  __shared__ FaceTile<R, Real, FW> tile;
+  const int seg = DIR == 0 ? blockIdx.x : blockIdx.y, band = DIR == 0 ? blockIdx.y : blockIdx.x;
+  tile_load<R, Real, DIR, FW>(tile, X, g, seg, band);
+  __syncthreads();
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  int i, j, nlen, across;
+  if (DIR == 0) {
+    j = band * FW + warp;
+    i = seg * kSegFaces - 1 + lane;
+    nlen = g.nx;
+    across = g.ny;
+  } else {
+    i = band * FW + warp;
+    j = seg * kSegFaces - 1 + lane;
+    nlen = g.ny;
+    across = g.nx;
+  }
+  if ((DIR == 0 ? j : i) >= across) return;  // whole warp
+  const int pos = DIR == 0 ? i : j;
+  Real SP[Q][4], SM[Q][4];
+  tile_face_states<R, Real, DIR, FW>(tile, W, lane + R, warp + R, pos <= nlen, SP, SM);
+  Real SL[Q][4];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) SL[q][v] = __shfl_up_sync(0xffffffffu, SP[q][v], 1);
+  if (lane == 0 || pos < 0 || pos > nlen) return;
+  // the face between (iL, jL) and (i, j)
+  const int iL = DIR == 0 ? i - 1 : i, jL = DIR == 0 ? j : j - 1;
+  const long long f = DIR == 0 ? (long long)j * (g.nx + 1) + i : (long long)j * g.nx + i;
+  const int K = face_radius(g, ord, R, iL, jL, i, j);
+  A.K[f] = (uint8_t)K;
+  double ad[4];
+  face_cotangent<DIR>(vin, g, iL, jL, i, j, ad);
+  const Real a[4] = {(Real)ad[0], (Real)ad[1], (Real)ad[2], (Real)ad[3]};
   Real* AL = (Real*)A.L;
   Real* AR = (Real*)A.R;
-  switch (K) {
-    case 0: adj_face_at<0, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
-    case 1: adj_face_at<1, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
-    case 2: adj_face_at<2, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
-    default: adj_face_at<3, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf); break;
+  if (K == R) {
+    const Real gam = (Real)g.gamma;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) adj_point<Real, DIR>(SL[q], SM[q], gam, W.w[q], a, q, AL, AR, f, A.nf);
+  } else if (K == 0) {
+    adj_face_at<0, Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf);
+  } else if (K == 1) {
+    adj_face_at<(R > 1 ? 1 : 0), Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf);
+  } else {
+    adj_face_at<(R > 2 ? 2 : 0), Real, DIR>(X, g, Wd, iL, jL, a, AL, AR, f, A.nf);
   }
 }
 

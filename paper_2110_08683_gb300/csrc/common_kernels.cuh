@@ -134,56 +134,73 @@ __global__ void k_fill_ghosts_at(double* X, Grid g, double t) {
 }
 
 // transpose of the ghost fill: every ghost cell's adjoint goes to the
-// interior cell it was copied from (y rule first, then the x rule, the
-// reverse of the fill's composition); fixed states drop out
-__global__ void k_adj_fold(double* G, Grid g) {
-  const int H = g.H;
-  const int nxg = g.nx + 2 * H;
-  const long long nxs = (long long)g.ny * 2 * H;
-  const long long nys = (long long)2 * H * nxg;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= nxs + nys) return;
-  int i, j;
-  if (tid < nxs) {
-    j = (int)(tid / (2 * H));
-    const int c = (int)(tid % (2 * H));
-    i = c < H ? -1 - c : g.nx + (c - H);
-  } else {
-    const long long u = tid - nxs;
-    const int r = (int)(u / nxg);
-    i = (int)(u % nxg) - H;
-    j = r < H ? -(r + 1) : g.ny - 1 + (r - H + 1);
-  }
-  double s[4] = {1.0, 1.0, 1.0, 1.0};
-  int sj = j, si = i;
-  if (j < 0 || j >= g.ny) {
-    const int side = j < 0 ? 0 : 1;
-    const int k = j < 0 ? -j : j - g.ny + 1;
-    const int kind = g.bc[2 + side];
+// cell it was copied from, the y rule first (all columns, corners included)
+// and then the x rule (interior rows), the reverse of the fill's
+// composition; fixed states drop out.  One thread walks the ghosts of one
+// line in a fixed order, so the sums do not depend on scheduling.
+
+// source row and sign of the normal momentum of y ghost row j in column i;
+// false: a fixed state
+__device__ __forceinline__ bool fold_src_y(const Grid& g, int i, int j, int& sj, double& sgn) {
+  const int side = j < 0 ? 0 : 1;
+  const int k = j < 0 ? -j : j - g.ny + 1;
+  const int kind = g.bc[2 + side];
+  bool reflect = kind == 2;
+  if (kind == 3 || kind == 5) return false;
+  if (kind == 4) {
     const double xc = g.x0 + (i + 0.5) * g.dx;
-    bool reflect = kind == 2;
-    if (kind == 3 || kind == 5) return;
-    if (kind == 4) {
-      if (xc < g.dmr_wall_x0) return;
-      reflect = true;
-    }
-    if (kind == 0) sj = wrapi(j, g.ny);
-    else if (reflect) sj = side == 0 ? k - 1 : g.ny - k;
-    else sj = side == 0 ? 0 : g.ny - 1;
-    if (reflect) s[2] = -s[2];
+    if (xc < g.dmr_wall_x0) return false;
+    reflect = true;
   }
-  if (i < 0 || i >= g.nx) {
-    const int side = i < 0 ? 0 : 1;
-    const int k = i < 0 ? -i : i - g.nx + 1;
-    const int kind = g.bc[side];
-    if (kind == 3) return;
-    if (kind == 0) si = wrapi(i, g.nx);
-    else if (kind == 2) si = side == 0 ? k - 1 : g.nx - k;
-    else si = side == 0 ? 0 : g.nx - 1;
-    if (kind == 2) s[1] = -s[1];
-  }
+  if (kind == 0) sj = wrapi(j, g.ny);
+  else if (reflect) sj = side == 0 ? k - 1 : g.ny - k;
+  else sj = side == 0 ? 0 : g.ny - 1;
+  sgn = reflect ? -1.0 : 1.0;
+  return true;
+}
+
+__device__ __forceinline__ bool fold_src_x(const Grid& g, int i, int& si, double& sgn) {
+  const int side = i < 0 ? 0 : 1;
+  const int k = i < 0 ? -i : i - g.nx + 1;
+  const int kind = g.bc[side];
+  if (kind == 3) return false;
+  if (kind == 0) si = wrapi(i, g.nx);
+  else if (kind == 2) si = side == 0 ? k - 1 : g.nx - k;
+  else si = side == 0 ? 0 : g.nx - 1;
+  sgn = kind == 2 ? -1.0 : 1.0;
+  return true;
+}
+
+// one thread per ghosted column i in [-H, nx+H)
+__global__ void k_adj_fold_y(double* G, Grid g) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - g.H;
+  if (i >= g.nx + g.H) return;
+  for (int side = 0; side < 2; ++side)
+    for (int k = 1; k <= g.H; ++k) {
+      const int j = side == 0 ? -k : g.ny - 1 + k;
+      int sj;
+      double sgn;
+      if (!fold_src_y(g, i, j, sj, sgn)) continue;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) atomicAdd(&G[gidx(g, v, si, sj)], s[v] * G[gidx(g, v, i, j)]);
+      for (int v = 0; v < 4; ++v)
+        G[gidx(g, v, i, sj)] += (v == 2 ? sgn : 1.0) * G[gidx(g, v, i, j)];
+    }
+}
+
+// one thread per interior row j
+__global__ void k_adj_fold_x(double* G, Grid g) {
+  const int j = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= g.ny) return;
+  for (int side = 0; side < 2; ++side)
+    for (int k = 1; k <= g.H; ++k) {
+      const int i = side == 0 ? -k : g.nx - 1 + k;
+      int si;
+      double sgn;
+      if (!fold_src_x(g, i, si, sgn)) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        G[gidx(g, v, si, j)] += (v == 1 ? sgn : 1.0) * G[gidx(g, v, i, j)];
+    }
 }
 
 // w = v - dt G (interior of the ghosted G)

@@ -48,6 +48,7 @@ struct gpmood_s {
   long long prof_n[GPMOOD_NKCLASS];
   // captured step graphs [buffer rotation][profiled] and their streams
   Control ctl;  // host copy of the step controls
+  int eager;    // stream launches instead of the captured step graph
   cudaStream_t cs, cs2;
   cudaGraphExec_t gexec[3][3];  // [rotation][plain, profiled, recording]
   cudaEvent_t gev[64];
@@ -356,6 +357,7 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
 int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
                double* tape = nullptr, uint8_t* otape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
+  if (h->eager) return do_step(h, cfl, fixed_dt, clip, t_end, tape, otape);
   const int record = tape ? 1 : 0;
   const int prof = (h->prof_on && !record) ? 1 : 0;
   cudaGraphExec_t& ge = h->gexec[h->cur][record ? 2 : prof];
@@ -534,6 +536,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
   h->det.delta = fmin(g.dx, g.dy);
   h->precision = o.precision;
+  h->eager = o.eager ? 1 : 0;
   // a safety net only: radii never rise, so the loop ends; chains of
   // re-detected neighbours can take O(grid width) iterations
   h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
@@ -815,7 +818,7 @@ int adj_buffers(gpmood_t h) {
 // w = v - dt (dF/dX)^T v at the stage input X (interior) with radii ords
 template <class Real>
 int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, double dt,
-              const double* v, double* w, const DirectW<Real>& D) {
+              const double* v, double* w, const ParityW<Real>& P, const DirectW<Real>& D) {
   const Grid& g = h->g;
   for (int c = 0; c < 4; ++c)
     CK(cudaMemcpy2DAsync(h->aX + c * g.vstride + (size_t)g.H * g.pitch + g.H,
@@ -826,9 +829,10 @@ int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, doubl
   const int gb = (int)((ngh + 255) / 256);
   k_fill_ghosts_at<<<gb, 256, 0, h->stream>>>(h->aX, g, ts);
   CK(cudaGetLastError());
-  CK(LaunchA<Real>::adj_faces(h->aX, h->aXr, v, ords, g, D, h->ax, h->ay, h->stream));
+  CK(LaunchA<Real>::adj_faces(h->aX, h->aXr, v, ords, g, P, D, h->ax, h->ay, h->stream));
   CK(LaunchA<Real>::adj_gather(g, D, h->ax, h->ay, h->aG, h->stream));
-  k_adj_fold<<<gb, 256, 0, h->stream>>>(h->aG, g);
+  k_adj_fold_y<<<(g.nx + 2 * g.H + 127) / 128, 128, 0, h->stream>>>(h->aG, g);
+  k_adj_fold_x<<<(g.ny + 127) / 128, 128, 0, h->stream>>>(h->aG, g);
   k_adj_stage_out<<<152 * 8, 256, 0, h->stream>>>(w, v, h->aG, g, dt);
   CK(cudaGetLastError());
   return 0;
@@ -836,7 +840,7 @@ int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, doubl
 
 template <class Real>
 int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
-                 const double* lam, double* out, const DirectW<Real>& D) {
+                 const double* lam, double* out, const ParityW<Real>& P, const DirectW<Real>& D) {
   const size_t nc = (size_t)h->g.nx * h->g.ny, n4 = 4 * nc;
   const int nb = 152 * 8;
   double *mu = h->amu, *v = h->av, *w = h->aw;
@@ -844,15 +848,15 @@ int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt
   k_lincomb<<<nb, 256, 0, h->stream>>>(mu, 1.0 / 3.0, lam, 0.0, nullptr, (long long)n4);
   k_lincomb<<<nb, 256, 0, h->stream>>>(v, 2.0 / 3.0, lam, 0.0, nullptr, (long long)n4);
   // Y3 = X3 - dt F(X3), X3 = (3 U^n + Y2)/4
-  int rc = adj_stage<Real>(h, tape + 2 * n4, otape + 2 * nc, t + 0.5 * dt, dt, v, w, D);
+  int rc = adj_stage<Real>(h, tape + 2 * n4, otape + 2 * nc, t + 0.5 * dt, dt, v, w, P, D);
   if (rc) return rc;
   k_lincomb<<<nb, 256, 0, h->stream>>>(mu, 1.0, mu, 0.75, w, (long long)n4);
   k_lincomb<<<nb, 256, 0, h->stream>>>(v, 0.25, w, 0.0, nullptr, (long long)n4);
   // Y2 = X2 - dt F(X2), X2 = Y1
-  rc = adj_stage<Real>(h, tape + n4, otape + nc, t + dt, dt, v, w, D);
+  rc = adj_stage<Real>(h, tape + n4, otape + nc, t + dt, dt, v, w, P, D);
   if (rc) return rc;
   // Y1 = X1 - dt F(X1), X1 = U^n
-  rc = adj_stage<Real>(h, tape, otape, t, dt, w, v, D);
+  rc = adj_stage<Real>(h, tape, otape, t, dt, w, v, P, D);
   if (rc) return rc;
   k_lincomb<<<nb, 256, 0, h->stream>>>(out, 1.0, mu, 1.0, v, (long long)n4);
   CK(cudaGetLastError());
@@ -877,8 +881,8 @@ int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, do
   int rc = adj_buffers(h);
   if (rc) return rc;
   return h->precision == GPMOOD_FP32
-             ? step_adjoint<float>(h, tape, otape, dt, t, lam_in, lam_out, h->dw32)
-             : step_adjoint<double>(h, tape, otape, dt, t, lam_in, lam_out, h->dw64);
+             ? step_adjoint<float>(h, tape, otape, dt, t, lam_in, lam_out, h->pw32, h->dw32)
+             : step_adjoint<double>(h, tape, otape, dt, t, lam_in, lam_out, h->pw64, h->dw64);
 }
 
 }  // extern "C"

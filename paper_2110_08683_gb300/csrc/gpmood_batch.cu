@@ -139,6 +139,7 @@ struct gpmood_batch_s {
   DirectW<double> dw64;
   DirectW<float> dw32;
   Control ctl;
+  int eager;  // stream launches instead of the captured step graph
   int cur, has_state;
   // face-kernel variant per sweep (warps per block 4 or 8, persistent blocks)
   int tuned, fw[2], blocks[2];
@@ -379,6 +380,50 @@ int capture_b(gpmood_batch_t b, int cur, int prof, cudaGraphExec_t* out) {
   return rc;
 }
 
+// the eager stage: the same kernels on the stream, the host reading the
+// MOOD loop decision after every iteration
+template <class Real>
+int eager_stage_b(gpmood_batch_t b, int s, int ia, int ix, int io, const ParityW<Real>& P,
+                  const DirectW<Real>& D) {
+  cudaStream_t st = b->stream;
+  StageArgs<Real> A = batch_args<Real>(b, s, ia, ix, io);
+  if (launch_fill_batch(b, ix, s, st)) return GPMOOD_E_CUDA;
+  if (launch_faces_batch<Real>(b, 0, A, P, b->fw[0], b->blocks[0], st)) return GPMOOD_E_CUDA;
+  if (launch_faces_batch<Real>(b, 1, A, P, b->fw[1], b->blocks[1], st)) return GPMOOD_E_CUDA;
+  int nb = b->up_blocks < b->n_up ? b->up_blocks : b->n_up;
+  CKB(LaunchB<Real>::update(A, b->probs, b->psc, b->items_up, b->n_up, nb, D, st));
+  CKB(launch_mood_begin(b->gsc, s, 0, 0, st));
+  MoodArgs M;
+  M.queue[0] = b->queue[0];
+  M.queue[1] = b->queue[1];
+  M.stamp = b->stamp;
+  M.sc = b->gsc;
+  for (;;) {
+    int rc = pull(b);
+    if (rc) return rc;
+    if (!b->hgsc->go) break;
+    CKB(launch_lower(M, A.ord, b->cas, st));
+    CKB(LaunchB<Real>::mood_faces(A, M, b->probs, b->psc, b->nprob, D, b->cas, st));
+    CKB(LaunchB<Real>::mood_update(A, M, b->probs, b->psc, b->nprob, D, st));
+    CKB(launch_mood_end(b->gsc, s, 0, 0, st));
+  }
+  return 0;
+}
+
+int eager_step_b(gpmood_batch_t b) {
+  const int a = b->cur, bb = (a + 1) % 3, c = (a + 2) % 3;
+  const int in[3] = {a, bb, c}, outb[3] = {bb, c, bb};
+  int rc = launch_dt_batch(b, a, b->stream);
+  for (int s = 0; s < 3 && !rc; ++s)
+    rc = b->precision == GPMOOD_FP32
+             ? eager_stage_b<float>(b, s, a, in[s], outb[s], b->pw32, b->dw32)
+             : eager_stage_b<double>(b, s, a, in[s], outb[s], b->pw64, b->dw64);
+  if (rc) return rc;
+  k_finish_batch<<<1, 256, 0, b->stream>>>(b->psc, b->nprob);
+  CKB(cudaGetLastError());
+  return pull(b);
+}
+
 int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t_end) {
   if (!b->has_state) return GPMOOD_E_NOSTATE;
   b->ctl.cfl = cfl;
@@ -391,15 +436,20 @@ int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t
     int rc = b->precision == GPMOOD_FP32 ? tune<float>(b, b->pw32) : tune<double>(b, b->pw64);
     if (rc) return rc;
   }
-  const int prof = b->prof_on ? 1 : 0;
-  cudaGraphExec_t& ge = b->gexec[b->cur][prof];
-  if (!ge) {
-    int rc = capture_b(b, b->cur, prof, &ge);
+  const int prof = (b->prof_on && !b->eager) ? 1 : 0;
+  if (b->eager) {
+    int rc = eager_step_b(b);
+    if (rc) return rc;
+  } else {
+    cudaGraphExec_t& ge = b->gexec[b->cur][prof];
+    if (!ge) {
+      int rc = capture_b(b, b->cur, prof, &ge);
+      if (rc) return rc;
+    }
+    CKB(cudaGraphLaunch(ge, b->stream));
+    int rc = pull(b);
     if (rc) return rc;
   }
-  CKB(cudaGraphLaunch(ge, b->stream));
-  int rc = pull(b);
-  if (rc) return rc;
   if (prof) {
     for (int k = 0; k < b->gev_pairs; ++k) {
       float ms = 0.f;
@@ -473,6 +523,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   b->nprob = nprob;
   b->top = R_max;
   b->precision = o.precision;
+  b->eager = o.eager ? 1 : 0;
   int widest = 0;
   for (int p = 0; p < nprob; ++p) {
     widest = grids[p].nx > widest ? grids[p].nx : widest;

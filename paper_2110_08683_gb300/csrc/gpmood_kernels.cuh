@@ -329,15 +329,11 @@ struct FaceTile {
   Real t[4][TS][TF];
 };
 
-// one block of the first-pass face sweep (DIR 0: x faces, 1: y faces) over
-// segment `seg` along the sweep and band `band` of FW rows/columns across it
-template <int R, class Real, int DIR, int FW>
-__device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid& g,
-                                            const ParityW<Real>& W, int seg, int band,
-                                            FaceTile<R, Real, FW>& T_) {
-  constexpr int N = stencil_n(R);
-  constexpr int Q = rule_q(R);
-  constexpr int NS = (Q + 1) / 2;
+// stage the ghosted state X (any element type) around segment `seg` along
+// the sweep and band `band` across it into the shared tile, as Real
+template <int R, class Real, int DIR, int FW, class TX>
+__device__ __forceinline__ void tile_load(FaceTile<R, Real, FW>& T_, const TX* X, const Grid& g,
+                                          int seg, int band) {
   constexpr int TF = FaceTile<R, Real, FW>::TF;
   constexpr int TS = FaceTile<R, Real, FW>::TS;
   auto& tile = T_.t;
@@ -352,30 +348,23 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
     const int i = DIR == 0 ? fast0 + fa : slow0 + sl;
     const int j = DIR == 0 ? slow0 + sl : fast0 + fa;
     Real val = Real(0);
-    if (i >= -g.H && i < g.nx + g.H && j >= -g.H && j < g.ny + g.H) val = (Real)__ldg(A.X + gidx(g, v, i, j));
+    if (i >= -g.H && i < g.nx + g.H && j >= -g.H && j < g.ny + g.H) val = (Real)__ldg(X + gidx(g, v, i, j));
     tile[v][sl][fa] = val;
   }
-  __syncthreads();
-  // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
-  int i, j, nlen, across;
-  if (DIR == 0) {
-    j = band * FW + warp;
-    i = seg * kSegFaces - 1 + lane;
-    nlen = g.nx;
-    across = g.ny;
-  } else {
-    i = band * FW + warp;
-    j = seg * kSegFaces - 1 + lane;
-    nlen = g.ny;
-    across = g.nx;
-  }
-  if ((DIR == 0 ? j : i) >= across) return;  // whole warp
-  const int pos = DIR == 0 ? i : j;  // position along the sweep, -1 .. nlen
-  const bool live = pos <= nlen;
-  const int fl = lane + R, sw = warp + R;  // this cell in the tile
-  // states on the two faces of this cell across the sweep direction:
-  // P = +1/2 side (east / north), M = -1/2 side (west / south)
-  Real SP[Q][4], SM[Q][4];
+}
+
+// states at all Gauss points of the two faces of one tile cell across the
+// sweep (top radius R): SP on the +1/2 side (east / north), SM on the -1/2
+// side (west / south).  (fl, sw): the cell's tile position along / across.
+template <int R, class Real, int DIR, int FW>
+__device__ __forceinline__ void tile_face_states(const FaceTile<R, Real, FW>& T_,
+                                                 const ParityW<Real>& W, int fl, int sw,
+                                                 bool live, Real (&SP)[rule_q(R)][4],
+                                                 Real (&SM)[rule_q(R)][4]) {
+  constexpr int N = stencil_n(R);
+  constexpr int Q = rule_q(R);
+  constexpr int NS = (Q + 1) / 2;
+  auto& tile = T_.t;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     Real s[N];
@@ -423,6 +412,36 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
       }
     }
   }
+}
+
+// one block of the first-pass face sweep (DIR 0: x faces, 1: y faces) over
+// segment `seg` along the sweep and band `band` of FW rows/columns across it
+template <int R, class Real, int DIR, int FW>
+__device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid& g,
+                                            const ParityW<Real>& W, int seg, int band,
+                                            FaceTile<R, Real, FW>& T_) {
+  constexpr int Q = rule_q(R);
+  tile_load<R, Real, DIR, FW>(T_, A.X, g, seg, band);
+  __syncthreads();
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
+  int i, j, nlen, across;
+  if (DIR == 0) {
+    j = band * FW + warp;
+    i = seg * kSegFaces - 1 + lane;
+    nlen = g.nx;
+    across = g.ny;
+  } else {
+    i = band * FW + warp;
+    j = seg * kSegFaces - 1 + lane;
+    nlen = g.ny;
+    across = g.nx;
+  }
+  if ((DIR == 0 ? j : i) >= across) return;  // whole warp
+  const int pos = DIR == 0 ? i : j;  // position along the sweep, -1 .. nlen
+  const bool live = pos <= nlen;
+  Real SP[Q][4], SM[Q][4];
+  tile_face_states<R, Real, DIR, FW>(T_, W, lane + R, warp + R, live, SP, SM);
   // left/lower state of the face between this cell and the previous one
   Real SL[Q][4];
 #pragma unroll

@@ -26,8 +26,8 @@ struct LaunchA {
                                   const DirectW<Real>& Wd, cudaStream_t st);
   // X: the ghosted stage input in Real (converted into Xr when Real is float)
   static cudaError_t adj_faces(const double* X, void* Xr, const double* v, const uint8_t* ord,
-                               const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
-                               const AdjFaces& Ay, cudaStream_t st);
+                               const Grid& g, const ParityW<Real>& W, const DirectW<Real>& Wd,
+                               const AdjFaces& Ax, const AdjFaces& Ay, cudaStream_t st);
   static cudaError_t adj_gather(const Grid& g, const DirectW<Real>& Wd, const AdjFaces& Ax,
                                 const AdjFaces& Ay, double* G, cudaStream_t st);
 };

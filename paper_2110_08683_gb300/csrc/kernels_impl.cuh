@@ -146,10 +146,25 @@ cudaError_t LaunchA<Real>::frozen_stage(const StageArgs<Real>& A, const Grid& g,
   return cudaGetLastError();
 }
 
+template <int R, class Real>
+static cudaError_t adj_faces_r(const Real* X, const double* v, const uint8_t* ord,
+                               const Grid& g, const ParityW<Real>& W, const DirectW<Real>& Wd,
+                               const AdjFaces& Ax, const AdjFaces& Ay, cudaStream_t st) {
+  // 4 warps a block: the reverse sweep holds ~150-250 registers a thread
+  constexpr int FW = 4;
+  dim3 blk(32, FW);
+  dim3 gx((g.nx + 1 + kSegFaces - 1) / kSegFaces, (g.ny + FW - 1) / FW);
+  k_adj_faces_sweep<R, Real, 0, FW><<<gx, blk, 0, st>>>(X, v, ord, g, W, Wd, Ax);
+  dim3 gy((g.nx + FW - 1) / FW, (g.ny + 1 + kSegFaces - 1) / kSegFaces);
+  k_adj_faces_sweep<R, Real, 1, FW><<<gy, blk, 0, st>>>(X, v, ord, g, W, Wd, Ay);
+  return cudaGetLastError();
+}
+
 template <class Real>
 cudaError_t LaunchA<Real>::adj_faces(const double* X, void* Xr, const double* v,
-                                     const uint8_t* ord, const Grid& g, const DirectW<Real>& Wd,
-                                     const AdjFaces& Ax, const AdjFaces& Ay, cudaStream_t st) {
+                                     const uint8_t* ord, const Grid& g, const ParityW<Real>& W,
+                                     const DirectW<Real>& Wd, const AdjFaces& Ax,
+                                     const AdjFaces& Ay, cudaStream_t st) {
   const Real* XR;
   if (sizeof(Real) == sizeof(double)) {
     XR = (const Real*)X;
@@ -157,9 +172,12 @@ cudaError_t LaunchA<Real>::adj_faces(const double* X, void* Xr, const double* v,
     k_to_real<Real><<<152 * 8, 256, 0, st>>>(X, (Real*)Xr, 4 * g.vstride);
     XR = (const Real*)Xr;
   }
-  k_adj_faces<Real, 0><<<(int)((Ax.nf + 127) / 128), 128, 0, st>>>(XR, v, ord, g, Wd, Ax);
-  k_adj_faces<Real, 1><<<(int)((Ay.nf + 127) / 128), 128, 0, st>>>(XR, v, ord, g, Wd, Ay);
-  return cudaGetLastError();
+  switch (Wd.top) {
+    case 0: return adj_faces_r<0, Real>(XR, v, ord, g, W, Wd, Ax, Ay, st);
+    case 1: return adj_faces_r<1, Real>(XR, v, ord, g, W, Wd, Ax, Ay, st);
+    case 2: return adj_faces_r<2, Real>(XR, v, ord, g, W, Wd, Ax, Ay, st);
+    default: return adj_faces_r<3, Real>(XR, v, ord, g, W, Wd, Ax, Ay, st);
+  }
 }
 
 template <class Real>

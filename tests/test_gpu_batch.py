@@ -78,3 +78,20 @@ def test_batch_run_reaches_t_end_per_problem():
         n = s.run(t_end)
         assert n == ns[k]
         assert relerr(Ub[k], s.get_state()) <= 1e-13
+
+
+def test_batch_eager_launches_equal_the_step_graph():
+    probs = mixed_problems()
+    out = []
+    for eager in (False, True):
+        b = gp.GPMoodBatch(probs, "fp64", eager=eager)
+        b.set_state([q["U0"] for q in probs])
+        for _ in range(3):
+            b.step()
+        out.append((b.get_state(), b.info()))
+        b.close()
+    (U0, i0), (U1, i1) = out
+    for k in range(len(probs)):
+        assert np.array_equal(U0[k], U1[k]), k
+    assert list(i0[0]) == list(i1[0])
+    assert i0[3]["iters"] == i1[3]["iters"]

@@ -211,3 +211,24 @@ def test_fp32_dmr_positivity():
     U = g.get_state()
     pr = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
     assert U[0].min() > 0 and pr.min() > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_eager_launches_equal_the_step_graph(precision):
+    """The eager mode (stream launches, host-driven MOOD loop) runs the same
+    kernels in the same order as the captured step graph: equal bit for bit,
+    flags and MOOD counters included, on a problem where MOOD is active."""
+    p = I.quadrants(n=48, ny=40, R=3, seed=1)
+    res = []
+    for eager in (False, True):
+        g = gp.GPMood(p, precision, eager=eager)
+        g.set_state(p["U0"])
+        for _ in range(4):
+            g.step()
+        ordg, badg, st = g.flags()
+        res.append((g.get_state(), ordg, badg, st))
+    (U0, o0, b0, s0), (U1, o1, b1, s1) = res
+    assert np.array_equal(U0, U1)
+    assert np.array_equal(o0, o1) and np.array_equal(b0, b1)
+    assert s0["iters"] == s1["iters"] and s0["nbad_total"] == s1["nbad_total"]
+    assert s0["t"] == s1["t"] and sum(s0["nbad_first"]) > 0
