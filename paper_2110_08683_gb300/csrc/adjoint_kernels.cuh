@@ -389,12 +389,4 @@ __global__ void __launch_bounds__(256) k_adj_gather(Grid g, const __grid_constan
   for (int v = 0; v < 4; ++v) G[gidx(g, v, ci, cj)] = (double)acc[v];
 }
 
-// Real copy of a ghosted state (the FP32 adjoint reads float stencils)
-template <class Real>
-__global__ void k_to_real(const double* X, Real* Y, long long n) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x)
-    Y[t] = (Real)X[t];
-}
-
 }  // namespace gpm

@@ -6,41 +6,35 @@
 
 namespace gpm {
 
-__global__ void k_fill_ghosts(double* X, Grid g, const Scalars* sc, double tfrac) {
+__global__ void k_fill_ghosts(double* X, float* Xf, Grid g, const Scalars* sc, double tfrac) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  fill_ghost(X, g, sc->t + tfrac * sc->dt, tid);
+  fill_ghost(X, Xf, g, sc->t + tfrac * sc->dt, tid);
 }
 
 // time step: min over cells of min(dx/(|u|+c), dy/(|v|+c)), per-direction
 // CFL form; positive doubles order like their bit patterns
 __global__ void k_dt_reduce(const double* X, Grid g, Scalars* sc) {
   if (sc->ctl.fixed_dt > 0.0) return;
-  double best = INFINITY;
+  double best = 0.0;
   bool bad = false;
   const long long n = (long long)g.nx * g.ny;
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % g.nx), j = (int)(c / g.nx);
-    double S[4];
+    double S[4], a;
     load_cell(X, g, i, j, S);
-    double r = S[0], u = S[1] / r, v = S[2] / r;
-    double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * S[1] + S[2] * S[2]) / r);
-    double cs = sqrt(g.gamma * p / r);
-    double ax = g.dx / (fabs(u) + cs);
-    double ay = g.dy / (fabs(v) + cs);
-    double a = ax < ay ? ax : ay;
-    if (!(a > 0.0) || !isfinite(a)) bad = true;
-    else best = a < best ? a : best;
+    if (!cell_rate(S, g, a)) bad = true;
+    else best = a > best ? a : best;
   }
   for (int o = 16; o > 0; o >>= 1) {
     double ob = __shfl_xor_sync(0xffffffffu, best, o);
-    best = ob < best ? ob : best;
+    best = ob > best ? ob : best;
   }
   bad = __any_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
     if (bad) atomicOr(&sc->err, kErrDt);
-    if (best < INFINITY)
-      atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(best));
+    // positive doubles order as their bit patterns
+    if (best > 0.0) atomicMax(&sc->rate_bits, (unsigned long long)__double_as_longlong(best));
   }
 }
 
@@ -53,12 +47,12 @@ __global__ void k_dt_finalize(Scalars* sc) {
   if (c.fixed_dt > 0.0) {
     dt = c.fixed_dt;
   } else {
-    dt = c.cfl * __longlong_as_double((long long)sc->dtmin_bits);
+    dt = c.cfl / __longlong_as_double((long long)sc->rate_bits);
     if (c.clip && sc->t + dt > c.t_end) dt = c.t_end - sc->t;
   }
   if (!(dt > 0.0) || !isfinite(dt)) sc->err |= kErrDt;
   sc->dt = dt;
-  sc->dtmin_bits = 0x7ff0000000000000ull;  // +inf for the next step
+  sc->rate_bits = 0ull;  // +0 for the next step
   for (int s = 0; s < 3; ++s) {
     sc->iters[s] = 0;
     sc->nbad_first[s] = 0;
@@ -130,7 +124,7 @@ __global__ void k_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc
 // ---------------------------------------------------------------------------
 __global__ void k_fill_ghosts_at(double* X, Grid g, double t) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  fill_ghost(X, g, t, tid);
+  fill_ghost(X, nullptr, g, t, tid);
 }
 
 // transpose of the ghost fill: every ghost cell's adjoint goes to the

@@ -25,6 +25,7 @@ struct gpmood_s {
   int max_iters;
   cudaStream_t stream;
   double* U[3];
+  float* Uf[3];    // float shadows of U (FP32 path only, else null)
   void* Fx;
   void* Fy;
   uint8_t* cad;
@@ -96,7 +97,10 @@ void free_all(gpmood_t h) {
   void* adj[] = {h->aX, h->aXr, h->aG, h->av, h->aw, h->amu, h->ax.L, h->ax.R, h->ax.K,
                  h->ay.L, h->ay.R, h->ay.K, h->aord};
   for (void* p : adj) cudaFree(p);
-  for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(h->U[k]);
+    cudaFree(h->Uf[k]);
+  }
   cudaFree(h->Fx);
   cudaFree(h->Fy);
   cudaFree(h->cad);
@@ -116,6 +120,13 @@ StageArgs<Real> stage_args(gpmood_t h, int s, int ia, int ix, int io) {
   A.X = h->U[ix];
   A.U0 = h->U[ia];
   A.out = h->U[io];
+  if constexpr (sizeof(Real) == sizeof(float)) {
+    A.Xr = h->Uf[ix];
+    A.outr = h->Uf[io];
+  } else {
+    A.Xr = h->U[ix];
+    A.outr = nullptr;
+  }
   A.Fx = (Real*)h->Fx;
   A.Fy = (Real*)h->Fy;
   A.cad = h->cad;
@@ -182,7 +193,7 @@ template <class Real>
 int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const ParityW<Real>& P,
                const DirectW<Real>& D, cudaStream_t st) {
   static const double tfrac[3] = {0.0, 1.0, 0.5};
-  CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], st));
+  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, tfrac[s], st));
   CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
   CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
@@ -278,7 +289,7 @@ int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>
     CK(cudaGetLastError());
   }
   rec_event(h, prof, GPMOOD_K_GHOST, 1, st);
-  CK(launch_fill(h->U[ix], h->g, h->sc, tfrac[s], st));
+  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, tfrac[s], st));
   rec_event(h, prof, GPMOOD_K_GHOST, 0, st);
   rec_event(h, prof, GPMOOD_K_FACES_X, 1, st);
   CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
@@ -400,11 +411,11 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
 // ---------------------------------------------------------------------------
 namespace gpm {
 
-cudaError_t launch_fill(double* X, const Grid& g, const Scalars* sc, double tfrac,
+cudaError_t launch_fill(double* X, float* Xf, const Grid& g, const Scalars* sc, double tfrac,
                         cudaStream_t st) {
   long long n = (long long)g.ny * 2 * g.H + (long long)2 * g.H * (g.nx + 2 * g.H);
   int blocks = (int)((n + 255) / 256);
-  k_fill_ghosts<<<blocks, 256, 0, st>>>(X, g, sc, tfrac);
+  k_fill_ghosts<<<blocks, 256, 0, st>>>(X, Xf, g, sc, tfrac);
   return cudaGetLastError();
 }
 
@@ -568,6 +579,9 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   bool ok = true;
   for (int k = 0; k < 3; ++k)
     ok = ok && cudaMalloc(&h->U[k], sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess;
+  if (h->precision == GPMOOD_FP32)
+    for (int k = 0; k < 3; ++k)
+      ok = ok && cudaMalloc(&h->Uf[k], sizeof(float) * 4 * (size_t)g.vstride) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Fx, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Fy, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess;
   ok = ok && cudaMalloc(&h->cad, ncell) == cudaSuccess;
@@ -588,7 +602,9 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
        cudaMemset(h->ord, 0, 3 * ncell) == cudaSuccess &&
        cudaMemset(h->first, 0, 3 * ncell) == cudaSuccess;
   for (int k = 0; k < 3 && ok; ++k)
-    ok = cudaMemset(h->U[k], 0, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess;
+    ok = cudaMemset(h->U[k], 0, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess &&
+         (!h->Uf[k] || cudaMemset(h->Uf[k], 0, sizeof(float) * 4 * (size_t)g.vstride) ==
+                           cudaSuccess);
   if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
     free_all(h);
     delete h;
@@ -626,11 +642,15 @@ int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                          h->stream));
   }
+  if (h->Uf[0]) {
+    k_to_real<float><<<152 * 8, 256, 0, h->stream>>>(h->U[0], h->Uf[0], 4 * g.vstride);
+    CK(cudaGetLastError());
+  }
   // MOOD stamps restart with the scalars
   CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * (size_t)g.nx * g.ny, h->stream));
   Scalars z;
   memset(&z, 0, sizeof(z));
-  z.dtmin_bits = 0x7ff0000000000000ull;
+  z.rate_bits = 0ull;
   *h->hsc = z;
   CK(cudaMemcpyAsync(h->sc, h->hsc, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -774,7 +794,7 @@ int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>
   const size_t nc = (size_t)h->g.nx * h->g.ny;
   static const double tfrac[3] = {0.0, 1.0, 0.5};
   for (int s = 0; s < 3; ++s) {
-    CK(launch_fill(h->U[in[s]], h->g, h->sc, tfrac[s], h->stream));
+    CK(launch_fill(h->U[in[s]], h->Uf[in[s]], h->g, h->sc, tfrac[s], h->stream));
     StageArgs<Real> A = stage_args<Real>(h, s, a, in[s], out[s]);
     CK(cudaMemcpyAsync(A.ord, otape + s * nc, nc, cudaMemcpyDeviceToDevice, h->stream));
     CK(LaunchA<Real>::frozen_stage(A, h->g, D, h->stream));
@@ -974,8 +994,10 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   const size_t sz_c = align256(ncell), sz_c3 = align256(3 * ncell);
   const size_t sz_stamp = align256(sizeof(uint32_t) * ncell), sz_q = align256(sizeof(int) * ncell);
   const size_t sz_sc = align256(sizeof(Scalars));
-  const size_t need =
-      3 * sz_state + sz_fx + sz_fy + sz_c + 2 * sz_c3 + sz_stamp + 2 * sz_q + sz_sc;
+  const size_t sz_shadow =
+      o.precision == GPMOOD_FP32 ? align256(sizeof(float) * 4 * (size_t)g.vstride) : 0;
+  const size_t need = 3 * sz_state + 3 * sz_shadow + sz_fx + sz_fy + sz_c + 2 * sz_c3 +
+                      sz_stamp + 2 * sz_q + sz_sc;
   if (need > (size_t)GPMOOD_NOALLOC_SCRATCH_BYTES) return GPMOOD_E_TOO_BIG;
 
   g.dx = (grid->x1 - grid->x0) / g.nx;
@@ -1034,6 +1056,10 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   for (int k = 0; k < 3; ++k) {
     h->U[k] = (double*)p;
     p += sz_state;
+  }
+  for (int k = 0; k < 3 && sz_shadow; ++k) {
+    h->Uf[k] = (float*)p;
+    p += sz_shadow;
   }
   h->Fx = p; p += sz_fx;
   h->Fy = p; p += sz_fy;

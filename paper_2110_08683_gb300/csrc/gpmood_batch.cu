@@ -30,32 +30,26 @@ __global__ void k_dt_reduce_batch(const double* X, const Prob* probs, Scalars* p
     const Prob& P = probs[w.p];
     const Grid& g = P.g;
     const double* Xp = X + P.state_off;
-    double best = INFINITY;
+    double best = 0.0;
     bool bad = false;
     const long long c0 = (long long)w.a * 4096;
     const long long c1 = c0 + 4096 < (long long)P.ncell ? c0 + 4096 : (long long)P.ncell;
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
       int i = (int)(c % g.nx), j = (int)(c / g.nx);
-      double S[4];
+      double S[4], a;
       load_cell(Xp, g, i, j, S);
-      double r = S[0], u = S[1] / r, v = S[2] / r;
-      double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * S[1] + S[2] * S[2]) / r);
-      double cs = sqrt(g.gamma * p / r);
-      double ax = g.dx / (fabs(u) + cs);
-      double ay = g.dy / (fabs(v) + cs);
-      double a = ax < ay ? ax : ay;
-      if (!(a > 0.0) || !isfinite(a)) bad = true;
-      else best = a < best ? a : best;
+      if (!cell_rate(S, g, a)) bad = true;
+      else best = a > best ? a : best;
     }
     for (int o = 16; o > 0; o >>= 1) {
       double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      best = ob < best ? ob : best;
+      best = ob > best ? ob : best;
     }
     bad = __any_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0) {
       if (bad) atomicOr(&gsc->err, kErrDt);
-      if (best < INFINITY)
-        atomicMin(&psc[w.p].dtmin_bits, (unsigned long long)__double_as_longlong(best));
+      if (best > 0.0)
+        atomicMax(&psc[w.p].rate_bits, (unsigned long long)__double_as_longlong(best));
     }
   }
 }
@@ -74,12 +68,12 @@ __global__ void k_dt_finalize_batch(Scalars* psc, Scalars* gsc, int nprob) {
     } else if (c.fixed_dt > 0.0) {
       dt = c.fixed_dt;
     } else {
-      dt = c.cfl * __longlong_as_double((long long)s.dtmin_bits);
+      dt = c.cfl / __longlong_as_double((long long)s.rate_bits);
       if (c.clip && s.t + dt > c.t_end) dt = c.t_end - s.t;
     }
     if (active && (!(dt > 0.0) || !isfinite(dt))) atomicOr(&gsc->err, kErrDt);
     s.dt = dt;
-    s.dtmin_bits = 0x7ff0000000000000ull;
+    s.rate_bits = 0ull;
     if (active) atomicAdd(&gsc->nactive, 1);
   }
 }
@@ -96,8 +90,8 @@ __global__ void k_batch_reset(Scalars* gsc) {
   gsc->nactive = 0;
 }
 
-__global__ void k_fill_batch(double* X, const Prob* probs, const Scalars* psc, double tfrac,
-                             int nprob) {
+__global__ void k_fill_batch(double* X, float* Xf, const Prob* probs, const Scalars* psc,
+                             double tfrac, int nprob) {
   const int p = blockIdx.y;
   if (p >= nprob) return;
   const Prob& P = probs[p];
@@ -105,7 +99,7 @@ __global__ void k_fill_batch(double* X, const Prob* probs, const Scalars* psc, d
   const long long n = ghost_count(P.g);
   for (long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x; tid < n;
        tid += (long long)gridDim.x * blockDim.x)
-    fill_ghost(X + P.state_off, P.g, t, tid);
+    fill_ghost(X + P.state_off, Xf ? Xf + P.state_off : nullptr, P.g, t, tid);
 }
 
 __global__ void k_finish_batch(Scalars* psc, int nprob) {
@@ -125,6 +119,7 @@ struct gpmood_batch_s {
   int total_cells;
   cudaStream_t stream, cs, cs2;
   double* U[3];
+  float* Uf[3];  // float shadows of U (FP32 path only, else null)
   void *Fx, *Fy;
   uint8_t *cad, *ord, *first;
   uint32_t* stamp;
@@ -176,7 +171,10 @@ void batch_free(gpmood_batch_t b) {
       if (b->gexec[r][p]) cudaGraphExecDestroy(b->gexec[r][p]);
   if (b->cs) cudaStreamDestroy(b->cs);
   if (b->cs2) cudaStreamDestroy(b->cs2);
-  for (int k = 0; k < 3; ++k) cudaFree(b->U[k]);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(b->U[k]);
+    cudaFree(b->Uf[k]);
+  }
   void* ptrs[] = {b->Fx, b->Fy, b->cad, b->ord, b->first, b->stamp, b->queue[0], b->queue[1],
                   b->probs, b->psc, b->gsc, b->items_fx[0], b->items_fx[1], b->items_fy[0],
                   b->items_fy[1], b->items_up, b->items_dt};
@@ -198,6 +196,13 @@ StageArgs<Real> batch_args(gpmood_batch_t b, int s, int ia, int ix, int io) {
   A.X = b->U[ix];
   A.U0 = b->U[ia];
   A.out = b->U[io];
+  if constexpr (sizeof(Real) == sizeof(float)) {
+    A.Xr = b->Uf[ix];
+    A.outr = b->Uf[io];
+  } else {
+    A.Xr = b->U[ix];
+    A.outr = nullptr;
+  }
   A.Fx = (Real*)b->Fx;
   A.Fy = (Real*)b->Fy;
   A.cad = b->cad;
@@ -227,8 +232,8 @@ int launch_dt_batch(gpmood_batch_t b, int ia, cudaStream_t st) {
 
 int launch_fill_batch(gpmood_batch_t b, int ix, int s, cudaStream_t st) {
   static const double tfrac[3] = {0.0, 1.0, 0.5};
-  k_fill_batch<<<dim3(b->fill_blocks_x, b->nprob), 256, 0, st>>>(b->U[ix], b->probs, b->psc,
-                                                                  tfrac[s], b->nprob);
+  k_fill_batch<<<dim3(b->fill_blocks_x, b->nprob), 256, 0, st>>>(b->U[ix], b->Uf[ix], b->probs,
+                                                                  b->psc, tfrac[s], b->nprob);
   return cudaGetLastError() == cudaSuccess ? 0 : GPMOOD_E_CUDA;
 }
 
@@ -645,6 +650,9 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   bool ok = true;
   for (int k = 0; k < 3; ++k)
     ok = ok && cudaMalloc(&b->U[k], sizeof(double) * (size_t)b->state_elems) == cudaSuccess;
+  if (b->precision == GPMOOD_FP32)
+    for (int k = 0; k < 3; ++k)
+      ok = ok && cudaMalloc(&b->Uf[k], sizeof(float) * (size_t)b->state_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&b->Fx, fsz * (size_t)b->fx_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&b->Fy, fsz * (size_t)b->fy_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&b->cad, nc_all) == cudaSuccess;
@@ -675,7 +683,9 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
          cudaMemset(b->stamp, 0, 4 * nc_all) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   for (int k = 0; k < 3 && ok; ++k)
-    ok = cudaMemset(b->U[k], 0, sizeof(double) * (size_t)b->state_elems) == cudaSuccess;
+    ok = cudaMemset(b->U[k], 0, sizeof(double) * (size_t)b->state_elems) == cudaSuccess &&
+         (!b->Uf[k] ||
+          cudaMemset(b->Uf[k], 0, sizeof(float) * (size_t)b->state_elems) == cudaSuccess);
   if (!ok) {
     batch_free(b);
     delete b;
@@ -713,10 +723,14 @@ int gpmood_batch_set_state(gpmood_batch_t b, const double* U, int on_device) {
       off += (size_t)g.nx * g.ny;
     }
   }
+  if (b->Uf[0]) {
+    k_to_real<float><<<152 * 8, 256, 0, b->stream>>>(b->U[0], b->Uf[0], b->state_elems);
+    CKB(cudaGetLastError());
+  }
   std::vector<Scalars> z(b->nprob);
   for (auto& s : z) {
     memset(&s, 0, sizeof(s));
-    s.dtmin_bits = 0x7ff0000000000000ull;
+    s.rate_bits = 0ull;
   }
   CKB(cudaMemcpyAsync(b->psc, z.data(), sizeof(Scalars) * b->nprob, cudaMemcpyHostToDevice,
                       b->stream));

@@ -44,7 +44,7 @@ struct Scalars {
   Control ctl;
   double t;                     // time at the start of the current step
   double dt;                    // current step
-  unsigned long long dtmin_bits;  // running min of dx/(|u|+c) as ordered bits
+  unsigned long long rate_bits;  // running max of the CFL rate (|u|+c)/dx as ordered bits
   int err;                      // error bits (kErr*)
   int count[2];                 // queue lengths (double buffered)
   int slot;                     // queue holding the cells to work on
@@ -94,8 +94,10 @@ struct Detect {
 template <class Real>
 struct StageArgs {
   const double* X;   // ghosted stage input
+  const Real* Xr;    // the same in Real: X itself (FP64), its float shadow (FP32)
   const double* U0;  // ghosted U^n (combination)
   double* out;       // ghosted stage output
+  Real* outr;        // float shadow of out (FP32), null (FP64)
   Real* Fx;
   Real* Fy;
   uint8_t* cad;

@@ -211,6 +211,21 @@ __device__ __forceinline__ void load_cell(const double* X, const Grid& g, int i,
   for (int v = 0; v < 4; ++v) S[v] = X[gidx(g, v, i, j)];
 }
 
+// the per-direction CFL rate of one cell, max((|u|+c)/dx, (|v|+c)/dy): the
+// admissible step is CFL over its maximum over the cells (the minimum of
+// dx/(|u|+c) and dy/(|v|+c), reduced as a maximum of rates so that each cell
+// needs one reciprocal and no division).  False: no admissible step (the
+// rate NaN, infinite or zero; p / rho < 0 gives NaN).
+__device__ __forceinline__ bool cell_rate(const double* S, const Grid& g, double& rate) {
+  const double ir = recip(S[0]);
+  const double u = S[1] * ir, v = S[2] * ir;
+  const double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * u + S[2] * v));
+  const double cs = sqrt(g.gamma * p * ir);
+  const double ax = (fabs(u) + cs) * g.inv_dx, ay = (fabs(v) + cs) * g.inv_dy;
+  rate = ax > ay ? ax : ay;  // a NaN state makes both rates NaN
+  return rate > 0.0 && isfinite(rate);
+}
+
 // value of the x-ghost (i outside [0,nx)) of interior row j
 __device__ __forceinline__ void xghost(const double* X, const Grid& g, int i, int j, double* S) {
   int side = i < 0 ? 0 : 1;
@@ -242,7 +257,9 @@ __device__ __forceinline__ long long ghost_count(const Grid& g) {
   return (long long)g.ny * 2 * g.H + (long long)2 * g.H * (g.nx + 2 * g.H);
 }
 
-__device__ __forceinline__ void fill_ghost(double* X, const Grid& g, double t, long long tid) {
+// Xf: the float shadow of X (FP32 path), filled alongside, or null
+__device__ __forceinline__ void fill_ghost(double* X, float* Xf, const Grid& g, double t,
+                                           long long tid) {
   const int H = g.H;
   const int nxg = g.nx + 2 * H;
   const long long nxs = (long long)g.ny * 2 * H;  // x-ghosts of interior rows
@@ -296,6 +313,19 @@ __device__ __forceinline__ void fill_ghost(double* X, const Grid& g, double t, l
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) X[gidx(g, v, i, j)] = S[v];
+  if (Xf) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Xf[gidx(g, v, i, j)] = (float)S[v];
+  }
+}
+
+// Real copy of a ghosted state: the float shadow of the FP32 path (and of
+// the FP32 adjoint), Y = (Real)X elementwise
+template <class Real>
+__global__ void k_to_real(const double* X, Real* Y, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    Y[t] = (Real)X[t];
 }
 
 // ---------------------------------------------------------------------------
@@ -421,7 +451,7 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
                                             const ParityW<Real>& W, int seg, int band,
                                             FaceTile<R, Real, FW>& T_) {
   constexpr int Q = rule_q(R);
-  tile_load<R, Real, DIR, FW>(T_, A.X, g, seg, band);
+  tile_load<R, Real, DIR, FW>(T_, A.Xr, g, seg, band);
   __syncthreads();
   const int lane = threadIdx.x, warp = threadIdx.y;
   // DIR 0: lanes along x, warp per row; DIR 1: lanes along y, warp per column
@@ -497,12 +527,13 @@ __global__ void __launch_bounds__(32 * FW) k_faces(StageArgs<Real> A, Grid g,
 // stage input X.  Returns true for a troubled cell.
 // ---------------------------------------------------------------------------
 template <class Real>
-__device__ __forceinline__ Real xload(const double* X, const Grid& g, int v, int i, int j) {
-  return (Real)__ldg(X + gidx(g, v, i, j));
+__device__ __forceinline__ Real xload(const Real* X, const Grid& g, int v, int i, int j) {
+  return __ldg(X + gidx(g, v, i, j));
 }
 
+// X: the ghosted stage input in Real
 template <class Real>
-__device__ bool troubled(const double* X, const Grid& g, const Detect& D, const Real* d2x,
+__device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Real* d2x,
                          const Real* d2y, int i, int j, const double* Yd) {
   const Real gm1 = (Real)(g.gamma - 1.0);
   Real Y[4] = {(Real)Yd[0], (Real)Yd[1], (Real)Yd[2], (Real)Yd[3]};
@@ -596,8 +627,9 @@ __device__ __forceinline__ void combine_store(const StageArgs<Real>& A, const Gr
     double o;
     if (A.stage == 0) o = Y[v];
     else if (A.stage == 1) o = 0.25 * (3.0 * A.U0[k] + Y[v]);
-    else o = (A.U0[k] + 2.0 * Y[v]) / 3.0;
+    else o = (A.U0[k] + 2.0 * Y[v]) * (1.0 / 3.0);
     A.out[k] = o;
+    if constexpr (sizeof(Real) == sizeof(float)) A.outr[k] = (float)o;
   }
 }
 
@@ -632,7 +664,7 @@ __device__ __forceinline__ void update_cell_w(const StageArgs<Real>& A, const Gr
     candidate<Real>(A, g, i, j, dt, Y);
     const int top = Wd.top;
     if (top != 0) {
-      bad = A.cad[c] != 0 || troubled<Real>(A.X, g, D, d2x, d2y, i, j, Y);
+      bad = A.cad[c] != 0 || troubled<Real>(A.Xr, g, D, d2x, d2y, i, j, Y);
     } else {
       Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
       Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
@@ -691,8 +723,8 @@ __device__ __forceinline__ void radius_pair(const Grid& g, const uint8_t* ord, c
 }
 
 // direct reconstruction of one face state at radius K (eq. gp_reconstructor)
-// T: storage type of the ghosted state (double, or a float copy)
-template <int K, class Real, class T = double>
+// T: storage type of the ghosted state (Real, or double read into Real)
+template <int K, class Real, class T = Real>
 __device__ __forceinline__ void recon_direct(const T* X, const Grid& g, const Real* z, int i,
                                              int j, Real* S) {
 #pragma unroll
@@ -714,7 +746,7 @@ __device__ __forceinline__ void recon_direct(const T* X, const Grid& g, const Re
 
 // face between cell (iL,jL) and its neighbour (iR,jR) in direction DIR at radius K
 template <int K, class Real, int DIR>
-__device__ void face_at(const double* X, const Grid& g, const DirectW<Real>& Wd, int iL, int jL,
+__device__ void face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, int iL, int jL,
                         Real* F, bool& badL, bool& badR) {
   constexpr int Q = rule_q(K);
   const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
@@ -727,8 +759,8 @@ __device__ void face_at(const double* X, const Grid& g, const DirectW<Real>& Wd,
     if (K == 0) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        UL[v] = (Real)__ldg(X + gidx(g, v, iL, jL));
-        UR[v] = (Real)__ldg(X + gidx(g, v, iR, jR));
+        UL[v] = __ldg(X + gidx(g, v, iL, jL));
+        UR[v] = __ldg(X + gidx(g, v, iR, jR));
       }
     } else {
       // faces: 0 E, 1 W, 2 N, 3 S
@@ -758,10 +790,10 @@ __device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const Di
   Real F[4];
   bool bl, br;
   switch (K) {
-    case 0: face_at<0, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
-    case 1: face_at<1, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
-    case 2: face_at<2, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
-    default: face_at<3, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    case 0: face_at<0, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    case 1: face_at<1, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    case 2: face_at<2, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    default: face_at<3, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
   }
   const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
   if (DIR == 0) {
@@ -845,7 +877,7 @@ __device__ __forceinline__ bool mood_update_item(const StageArgs<Real>& A, const
   candidate<Real>(A, g, di, dj, A.sc->dt, Y);
   bool flag = false;
   if (A.ord[d] != 0) {
-    flag = A.cad[d] != 0 || troubled<Real>(A.X, g, D, d2x, d2y, di, dj, Y);
+    flag = A.cad[d] != 0 || troubled<Real>(A.Xr, g, D, d2x, d2y, di, dj, Y);
   } else {
     Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
     Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
@@ -931,10 +963,10 @@ __global__ void __launch_bounds__(128) k_faces_frozen(StageArgs<Real> A, Grid g,
   Real F[4];
   bool bl, br;
   switch (K) {
-    case 0: face_at<0, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
-    case 1: face_at<1, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
-    case 2: face_at<2, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
-    default: face_at<3, Real, DIR>(A.X, g, Wd, iL, jL, F, bl, br); break;
+    case 0: face_at<0, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    case 1: face_at<1, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    case 2: face_at<2, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    default: face_at<3, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -965,8 +997,10 @@ __device__ __forceinline__ StageArgs<Real> problem_args(const StageArgs<Real>& B
                                                         const Scalars* psc, int p) {
   StageArgs<Real> A = B;
   A.X = B.X + P.state_off;
+  A.Xr = B.Xr + P.state_off;
   A.U0 = B.U0 + P.state_off;
   A.out = B.out + P.state_off;
+  A.outr = B.outr ? B.outr + P.state_off : nullptr;
   A.Fx = B.Fx + P.fx_off;
   A.Fy = B.Fy + P.fy_off;
   A.cad = B.cad + P.cell_off;
