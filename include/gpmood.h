@@ -62,12 +62,16 @@ enum {
 
 /* grid and boundary description (Sec. 2.1); caller-owned, copied at create */
 typedef struct {
-  int nx, ny;                 /* interior cells, each >= R_max + 1 (and >= 2) */
+  int nx, ny;                 /* interior cells, each >= max(R_max + 1, 3) (ny = 1 in 1D) */
   double x0, x1, y0, y1;      /* domain; dx = (x1-x0)/nx, dy = (y1-y0)/ny */
   int bc[4];                  /* GPMOOD_BC_* for W, E, S, N */
   double bc_prim[4][4];       /* (rho, u, v, p) for DIRICHLET sides */
   double dmr_post[4], dmr_pre[4];            /* primitive states for the DMR kinds */
   double dmr_wall_x0, dmr_xs0, dmr_xs_speed; /* DMR wall start and shock line x_s(t) */
+  int dim;                    /* 0 or 2: two-dimensional.  1: one-dimensional (ny = 1; y0, y1
+                                 and the S/N boundaries are ignored): the stencil a = -R..R,
+                                 one point per face, x faces only, detection and the time
+                                 step on the x terms alone.  Single-problem handles only */
 } gpmood_grid;
 
 /* options; a zero-initialised struct (or NULL) gives the paper's defaults */

@@ -39,6 +39,7 @@ class Grid(C.Structure):
         ("bc", C.c_int * 4), ("bc_prim", (C.c_double * 4) * 4),
         ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4),
         ("dmr_wall_x0", C.c_double), ("dmr_xs0", C.c_double), ("dmr_xs_speed", C.c_double),
+        ("dim", C.c_int),
     ]
 
 
@@ -134,6 +135,7 @@ def make_grid(prob):
     g.dmr_wall_x0 = prob["dmr_wall_x0"]
     g.dmr_xs0 = prob["dmr_xs0"]
     g.dmr_xs_speed = prob["dmr_xs_speed"]
+    g.dim = int(prob.get("dim", 2))
     return g
 
 

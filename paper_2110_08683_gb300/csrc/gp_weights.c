@@ -186,3 +186,61 @@ int gpw_second_derivative(double dx, double dy, double ell, int* da, int* db, do
   }
   return n;
 }
+
+/* One-dimensional GP (dim = 1): the stencil a = -R..R, one face point at
+   x = +1/2 (eq. SE-pred and eq. SE-cov with the x factor only), z divided by
+   its sum.  The result is laid out as a 2D radius-R table so that the same
+   kernels apply it: the weight of offset (a, 0) on the row b = 0, zero off
+   that row, the same vector at each of the R+1 Gauss-point slots, and Gauss
+   weights (1, 0, ...): every slot yields the same face state and the first
+   alone enters the face average. */
+int gpw_solve_1d(int R, double dx, double ell, gpw_radius* out) {
+  if (R < 1 || R > 3) return -1;
+  memset(out, 0, sizeof(*out));
+  int n = gpw_stencil(R, out->da, out->db);
+  int q = R + 1;
+  out->n = n;
+  out->q = q;
+  const int n1 = 2 * R + 1;
+  f128 lx = (f128)ell / (f128)dx;
+  f128 A[MAXN * MAXN];
+  for (int m = 0; m < n1; ++m)
+    for (int k = 0; k < n1; ++k) A[m * n1 + k] = axis_cov((f128)(k - m), lx);
+  if (ldlt(n1, A) != 0) return -2;
+  f128 z[MAXN];
+  for (int m = 0; m < n1; ++m) z[m] = axis_pred(0.5F128 - (f128)(m - R), lx);
+  ldlt_solve(n1, A, z);
+  f128 sum = 0;
+  for (int m = 0; m < n1; ++m) sum += z[m];
+  for (int m = 0; m < n; ++m) {
+    double zm = out->db[m] == 0 ? (double)(z[out->da[m] + R] / sum) : 0.0;
+    for (int k = 0; k < q; ++k) out->z[0][k][m] = zm;
+  }
+  f128 gq[4], wq[4];
+  gauss_q(q, gq, wq);
+  for (int k = 0; k < q; ++k) {
+    out->g[k] = (double)gq[k];
+    out->w[k] = k == 0 ? 1.0 : 0.0;
+  }
+  return 0;
+}
+
+/* App. B second-derivative weights of the one-dimensional GP on the
+   3-point stencil, laid out on the 5-point R = 1 table (zero at (0, +-1));
+   wyy is all zero */
+int gpw_second_derivative_1d(double dx, double ell, int* da, int* db, double* wxx,
+                             double* wyy) {
+  int n = gpw_stencil(1, da, db);
+  f128 lx = (f128)ell / (f128)dx, L = ell;
+  f128 A[9], t[3];
+  for (int m = 0; m < 3; ++m)
+    for (int k = 0; k < 3; ++k) A[m * 3 + k] = axis_cov((f128)(k - m), lx);
+  if (ldlt(3, A) != 0) return -2;
+  for (int m = 0; m < 3; ++m) t[m] = axis_pred_d2(-(f128)(m - 1), lx, L);
+  ldlt_solve(3, A, t);
+  for (int m = 0; m < n; ++m) {
+    wxx[m] = db[m] == 0 ? (double)t[da[m] + 1] : 0.0;
+    wyy[m] = 0.0;
+  }
+  return n;
+}

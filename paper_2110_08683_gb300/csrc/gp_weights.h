@@ -23,6 +23,13 @@ int gpw_solve(int R, double dx, double dy, double ell, gpw_radius* out);
    returns the stencil size (5) or -2 */
 int gpw_second_derivative(double dx, double dy, double ell, int* da, int* db, double* wxx,
                           double* wyy);
+/* the one-dimensional GP (stencil a = -R..R, one face point) laid out as a
+   2D radius-R table: weights on the row b = 0, the same vector at every
+   Gauss-point slot, Gauss weights (1, 0, ...); north-face weights zero */
+int gpw_solve_1d(int R, double dx, double ell, gpw_radius* out);
+/* the 1D App. B second-derivative weights on the 5-point table (wyy = 0) */
+int gpw_second_derivative_1d(double dx, double ell, int* da, int* db, double* wxx,
+                             double* wyy);
 
 #ifdef __cplusplus
 }

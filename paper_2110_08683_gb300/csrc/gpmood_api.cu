@@ -195,7 +195,7 @@ int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const Parity
   static const double tfrac[3] = {0.0, 1.0, 0.5};
   CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, tfrac[s], st));
   CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
-  CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
+  if (h->g.dim == 2) CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
   return 0;
 }
@@ -295,7 +295,7 @@ int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>
   CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
   rec_event(h, prof, GPMOOD_K_FACES_X, 0, st);
   rec_event(h, prof, GPMOOD_K_FACES_Y, 1, st);
-  CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
+  if (h->g.dim == 2) CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
   rec_event(h, prof, GPMOOD_K_FACES_Y, 0, st);
   rec_event(h, prof, GPMOOD_K_UPDATE, 1, st);
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
@@ -494,16 +494,18 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   }
   const int H = R_max + 1 > 2 ? R_max + 1 : 2;
   const int minn = H > 3 ? H : 3;
-  if (grid->nx < minn || grid->ny < minn) return GPMOOD_E_INVAL;
-  if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0)) return GPMOOD_E_INVAL;
-  for (int s = 0; s < 4; ++s) {
+  if (grid->dim != 0 && grid->dim != 1 && grid->dim != 2) return GPMOOD_E_INVAL;
+  const bool one_d = grid->dim == 1;
+  if (grid->nx < minn || (one_d ? grid->ny != 1 : grid->ny < minn)) return GPMOOD_E_INVAL;
+  if (!(grid->x1 > grid->x0) || (!one_d && !(grid->y1 > grid->y0))) return GPMOOD_E_INVAL;
+  for (int s = 0; s < (one_d ? 2 : 4); ++s) {
     int k = grid->bc[s];
     if (k < 0 || k > 5) return GPMOOD_E_INVAL;
     if (k == GPMOOD_BC_DMR_BOTTOM && s != 2) return GPMOOD_E_INVAL;
     if (k == GPMOOD_BC_DMR_TOP && s != 3) return GPMOOD_E_INVAL;
   }
   if ((grid->bc[0] == 0) != (grid->bc[1] == 0)) return GPMOOD_E_INVAL;
-  if ((grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
+  if (!one_d && (grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
 
   gpmood_t h = new (std::nothrow) gpmood_s;
@@ -512,23 +514,25 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   Grid& g = h->g;
   g.nx = grid->nx;
   g.ny = grid->ny;
+  g.dim = one_d ? 1 : 2;
   g.H = H;
   g.pitch = round_up(g.nx + 2 * H, 32);
   g.gy = g.ny + 2 * H;
   g.vstride = (long long)g.pitch * g.gy;
   g.dx = (grid->x1 - grid->x0) / g.nx;
-  g.dy = (grid->y1 - grid->y0) / g.ny;
+  g.dy = one_d ? g.dx : (grid->y1 - grid->y0) / g.ny;
   g.inv_dx = 1.0 / g.dx;
   g.inv_dy = 1.0 / g.dy;
   g.x0 = grid->x0;
-  g.y0 = grid->y0;
+  g.y0 = one_d ? 0.0 : grid->y0;
   g.gamma = gamma;
   for (int s = 0; s < 4; ++s) {
-    g.bc[s] = grid->bc[s];
+    // 1D: the ghost rows copy the single row (no y faces read them)
+    g.bc[s] = (one_d && s >= 2) ? GPMOOD_BC_OUTFLOW : grid->bc[s];
     prim_to_cons(grid->bc_prim[s], gamma, g.bcU[s]);
   }
   g.periodic_x = grid->bc[0] == GPMOOD_BC_PERIODIC;
-  g.periodic_y = grid->bc[2] == GPMOOD_BC_PERIODIC;
+  g.periodic_y = g.bc[2] == GPMOOD_BC_PERIODIC;
   prim_to_cons(grid->dmr_post, gamma, g.dmr_post);
   prim_to_cons(grid->dmr_pre, gamma, g.dmr_pre);
   g.dmr_wall_x0 = grid->dmr_wall_x0;
@@ -559,14 +563,18 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   for (int k = 0; k < nc; ++k) {
     int R = cascade[k];
     if (R == 0) continue;
-    if (gpw_solve(R, g.dx, g.dy, ell, &wr[R]) != 0) {
+    const int rc = one_d ? gpw_solve_1d(R, g.dx, ell, &wr[R])
+                         : gpw_solve(R, g.dx, g.dy, ell, &wr[R]);
+    if (rc != 0) {
       delete h;
       return GPMOOD_E_WEIGHTS;
     }
   }
   int da[25], db[25];
   double d2x[25], d2y[25];
-  if (gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y) != 5) {
+  const int nd2 = one_d ? gpw_second_derivative_1d(g.dx, ell, da, db, d2x, d2y)
+                        : gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y);
+  if (nd2 != 5) {
     delete h;
     return GPMOOD_E_WEIGHTS;
   }
@@ -598,7 +606,10 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
     cudaGetLastError();
     return GPMOOD_E_OOM;
   }
-  ok = cudaMemset(h->cad, 0, ncell) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
+  // the face fluxes start at zero: in 1D the y fluxes stay zero
+  ok = cudaMemset(h->Fx, 0, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess &&
+       cudaMemset(h->Fy, 0, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess &&
+       cudaMemset(h->cad, 0, ncell) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
        cudaMemset(h->ord, 0, 3 * ncell) == cudaSuccess &&
        cudaMemset(h->first, 0, 3 * ncell) == cudaSuccess;
   for (int k = 0; k < 3 && ok; ++k)
@@ -889,7 +900,7 @@ int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt
 extern "C" {
 
 int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
-  if (!h || !otape || !(dt > 0.0)) return GPMOOD_E_INVAL;
+  if (!h || !otape || !(dt > 0.0) || h->g.dim != 2) return GPMOOD_E_INVAL;
   if (!h->has_state) return GPMOOD_E_NOSTATE;
   return h->precision == GPMOOD_FP32 ? frozen_step<float>(h, otape, dt, h->dw32)
                                      : frozen_step<double>(h, otape, dt, h->dw64);
@@ -897,7 +908,8 @@ int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
 
 int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
                         const double* lam_in, double* lam_out) {
-  if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0)) return GPMOOD_E_INVAL;
+  if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0) || h->g.dim != 2)
+    return GPMOOD_E_INVAL;
   int rc = adj_buffers(h);
   if (rc) return rc;
   return h->precision == GPMOOD_FP32
@@ -944,6 +956,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
                                    const gpmood_options* opts, const double* U_in, double* U_out,
                                    double t, double cfl, double* dt_out, void* stream) {
   if (!grid || !U_in || !U_out || !(cfl > 0.0) || !isfinite(t)) return GPMOOD_E_INVAL;
+  if (grid->dim == 1) return GPMOOD_E_INVAL;  // two-dimensional grids only
   if (R_max < 0 || R_max > 3 || !(gamma > 1.0) || !(ell > 0.0)) return GPMOOD_E_INVAL;
   gpmood_options o;
   memset(&o, 0, sizeof(o));
@@ -979,6 +992,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   memset(h, 0, sizeof(*h));
   Grid& g = h->g;
   g.nx = grid->nx;
+  g.dim = 2;
   g.ny = grid->ny;
   g.H = H;
   g.pitch = round_up(g.nx + 2 * H, 32);

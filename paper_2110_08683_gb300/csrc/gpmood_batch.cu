@@ -505,7 +505,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   for (int p = 0; p < nprob; ++p) {
     const gpmood_grid* gr = &grids[p];
     if (gr->nx < minn || gr->ny < minn || !(gr->x1 > gr->x0) || !(gr->y1 > gr->y0) ||
-        !(ell[p] > 0.0))
+        !(ell[p] > 0.0) || (gr->dim != 0 && gr->dim != 2))
       return GPMOOD_E_INVAL;
     for (int s = 0; s < 4; ++s) {
       int k = gr->bc[s];
@@ -554,6 +554,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
     memset(&P, 0, sizeof(P));
     Grid& g = P.g;
     g.nx = gr->nx;
+    g.dim = 2;
     g.ny = gr->ny;
     g.H = H;
     g.pitch = round_up(g.nx + 2 * H, 32);

@@ -16,6 +16,7 @@ constexpr int kFaceWarps = 8; // warps per face-kernel block
 // geometry and boundary data, passed by value to every kernel
 struct Grid {
   int nx, ny, H;          // interior cells and ghost layers
+  int dim;                // 2, or 1 (ny = 1, x faces only)
   int pitch, gy;          // ghosted row length (elements) and ghosted rows
   long long vstride;      // elements per variable plane of a ghosted state
   double dx, dy, inv_dx, inv_dy;

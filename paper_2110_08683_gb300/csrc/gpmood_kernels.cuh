@@ -222,7 +222,7 @@ __device__ __forceinline__ bool cell_rate(const double* S, const Grid& g, double
   const double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * u + S[2] * v));
   const double cs = sqrt(g.gamma * p * ir);
   const double ax = (fabs(u) + cs) * g.inv_dx, ay = (fabs(v) + cs) * g.inv_dy;
-  rate = ax > ay ? ax : ay;  // a NaN state makes both rates NaN
+  rate = (g.dim == 1 || ax > ay) ? ax : ay;  // a NaN state makes both rates NaN
   return rate > 0.0 && isfinite(rate);
 }
 
@@ -541,6 +541,7 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
   Real p = gm1 * (Y[3] - Real(0.5) * (Y[1] * Y[1] + Y[2] * Y[2]) * recip(Y[0]));
   if (!finite_r(rho) || !finite_r(p)) return true;   // Step 4, CAD
   if (!(rho > Real(0)) || !(p > Real(0))) return true; // Step 5, PAD
+  const bool two = g.dim == 2;  // 1D: the x terms and the W/E neighbours only
   if (D.csd_on) {                                      // Step 6, CSD
     Real rE = xload<Real>(X, g, 0, i + 1, j), rW = xload<Real>(X, g, 0, i - 1, j);
     Real rN = xload<Real>(X, g, 0, i, j + 1), rS = xload<Real>(X, g, 0, i, j - 1);
@@ -557,16 +558,21 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
     Real pN = gm1 * (eN - Real(0.5) * (mxN * mxN + myN * myN) * iN);
     Real pS = gm1 * (eS - Real(0.5) * (mxS * mxS + myS * myS) * iS);
     const Real hx = Real(0.5) * (Real)g.inv_dx, hy = Real(0.5) * (Real)g.inv_dy;
-    Real divV = (uE - uW) * hx + (vN - vS) * hy;
     Real mx_ = pE < pW ? pE : pW, my_ = pN < pS ? pN : pS;
-    Real gradP = fabs(pE - pW) * hx * recip(mx_) + fabs(pN - pS) * hy * recip(my_);
+    Real divV = (uE - uW) * hx, gradP = fabs(pE - pW) * hx * recip(mx_);
+    if (two) {
+      divV += (vN - vS) * hy;
+      gradP += fabs(pN - pS) * hy * recip(my_);
+    }
     if (divV >= -(Real)D.sigma_v && gradP <= (Real)D.sigma_p) return false;
   }
   Real r0 = xload<Real>(X, g, 0, i, j);
   Real rmin = r0, rmax = r0;
   const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, 1, -1};
+  const int nnb = two ? 4 : 2;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
+    if (m >= nnb) break;
     Real r = xload<Real>(X, g, 0, i + di[m], j + dj[m]);
     rmin = r < rmin ? r : rmin;
     rmax = r > rmax ? r : rmax;
@@ -579,10 +585,12 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
   const Real delta = (Real)D.delta;
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
+    if (d == 1 && !two) break;
     const Real* w = d == 0 ? d2x : d2y;
     Real cmin = Real(0), cmax = Real(0);
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
+      if (m >= 1 + nnb) break;
       int ii = i + ci[m], jj = j + cj[m];
       Real k = w[0] * xload<Real>(X, g, 0, ii, jj - 1) + w[1] * xload<Real>(X, g, 0, ii - 1, jj) +
                w[2] * xload<Real>(X, g, 0, ii, jj) + w[3] * xload<Real>(X, g, 0, ii + 1, jj) +
@@ -827,6 +835,7 @@ __device__ __forceinline__ void mood_face_item(const StageArgs<Real>& A, const G
                                                const DirectW<Real>& Wd, const Cascade& C,
                                                const uint32_t* stamp, uint32_t cur, int c, int f) {
   const int i = c % g.nx, j = c / g.nx;
+  if (f >= 2 && g.dim == 1) return;  // no y faces in 1D
   if (f == 0 || f == 2) {
     int nb = neighbour(g, i, j, f);
     if (nb >= 0 && stamp[nb] == cur) return;

@@ -232,3 +232,62 @@ def test_eager_launches_equal_the_step_graph(precision):
     assert np.array_equal(o0, o1) and np.array_equal(b0, b1)
     assert s0["iters"] == s1["iters"] and s0["nbad_total"] == s1["nbad_total"]
     assert s0["t"] == s1["t"] and sum(s0["nbad_first"]) > 0
+
+
+def test_sod_1d_first_steps_flags_and_states():
+    """One-dimensional mode (the Sod tube, 128 cells, GP-R2 cascade 5->3->1):
+    identical first-pass flags and final radii, states to round-off."""
+    p = I.sod_1d(n=128, R=2)
+    res = _first_step_flags(p, nsteps=3)
+    for Ug, Uo, og, oo, bg, bo, sg, so in res:
+        assert (bg == bo).all(), np.argwhere(bg != bo)[:10]
+        assert (og == oo).all(), np.argwhere(og != oo)[:10]
+        assert sg["iters"] == so["iters"]
+        assert relerr(Ug, Uo) <= 1e-11
+    assert sum(sum(r[7]["nbad_first"]) for r in res) > 0  # MOOD acted
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sod_1d_run_to_t_end(precision):
+    """The Sod tube to t = 0.2: FP64 within 1e-8 L1 density of the oracle,
+    FP32 within 1e-5; both close to the exact Riemann solution, positive,
+    and mass conserved to round-off (no wave reaches the ends by t = 0.2)."""
+    import exact_riemann as ER
+
+    p = I.sod_1d(n=128, R=2)
+    g = gp.GPMood(p, precision)
+    g.set_state(p["U0"])
+    ng = g.run(0.2)
+    Ug = g.get_state()
+    o = O.Oracle(p)
+    Uo, no, to = o.run(p["U0"], 0.2)
+    n = 128
+    L1 = np.abs(Ug[0, 0] - Uo[0, 0]).sum() / n
+    if precision == "fp64":
+        assert ng == no
+        assert L1 <= 1e-8, L1
+    else:
+        assert L1 <= 1e-5, L1
+    xc = (np.arange(n) + 0.5) / n
+    err = np.abs(Ug[0, 0] - ER.sod_density(xc, 0.2)).sum() / n
+    assert err < 7e-3, err  # the oracle's own error at 128 cells is 5.5e-3
+    assert (Ug[0] > 0).all()
+    m0 = p["U0"][0].sum() / n
+    # round-off only (no wave reaches the ends): 1e-13 relative per step
+    assert abs(Ug[0].sum() / n - m0) <= ng * 1e-13 * m0
+
+
+def test_sod_1d_rejected_where_unsupported():
+    """The 1D mode is for single-problem handles: batches, the adjoint and
+    the allocation-free step reject it."""
+    p = I.sod_1d(n=64, R=2)
+    with pytest.raises(gp.GpmoodError):
+        gp.GPMoodBatch([p, p])
+    g = gp.GPMood(p)
+    g.set_state(p["U0"])
+    torch = pytest.importorskip("torch")
+    tape = torch.empty((3, 4, 1, 64), dtype=torch.float64, device="cuda")
+    otape = torch.empty((3, 1, 64), dtype=torch.uint8, device="cuda")
+    dt = g.step_record(tape.data_ptr(), otape.data_ptr())
+    with pytest.raises(gp.GpmoodError):
+        g.step_frozen(otape.data_ptr(), dt)
