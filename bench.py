@@ -424,6 +424,10 @@ def run_adjoint(args, world, rank, local):
     fwd = modes["checkpoints_every_20"]["forward_s"]
     for m in modes.values():
         m["backward_over_plain_forward"] = m["backward_s"] / fwd
+    # finite differences resolve the FP64 map only (FP32: eps_32 / h ~ 6%)
+    fd = None
+    if args.adjoint_fd and args.precision == "fp64":
+        fd = adjoint_fd_check(g, p, U0, W, steps, args.adjoint_fd, torch)
     return {
         "metric": METRIC, "value": n * n * steps / fwd, "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": fwd * 1e3 / steps,
@@ -434,7 +438,48 @@ def run_adjoint(args, world, rank, local):
                                "J = integral of rho over [0.4,0.6]^2",
                    "cells": n * n, "precision": args.precision},
         "adjoint": modes,
+        "fd_check": fd,
     }
+
+
+def adjoint_fd_check(g, p, U0, W, steps, ndir, torch):
+    """Central finite differences (h = 1e-6) of the frozen-mask map along
+    seeded random directions against the adjoint's directional derivative,
+    at the full size: the forward records every step's radii and dt once;
+    J(U) replays the steps with them held fixed (gpmood_step_frozen)."""
+    from paper_2110_08683_gb300.autograd import rollout
+
+    ny, nx = g.ny, g.nx
+    U0r = U0.clone().requires_grad_()
+    (rollout(U0r, g, steps) * W).sum().backward()
+    grad = U0r.grad.detach()
+    otape = torch.empty((steps, 3, ny, nx), dtype=torch.uint8, device="cuda")
+    tape = torch.empty((3, 4, ny, nx), dtype=torch.float64, device="cuda")
+    dts = []
+    g.set_state(U0)
+    for k in range(steps):
+        dts.append(g.step_record(tape.data_ptr(), otape[k].data_ptr()))
+    out = torch.empty_like(U0)
+
+    def J(U):
+        g.set_state(U.contiguous())
+        for k in range(steps):
+            g.step_frozen(otape[k].data_ptr(), dts[k])
+        g.get_state(out)
+        return float(((out * W).sum(dtype=torch.float64)).item())
+
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    h = 1e-6
+    errs = []
+    t0 = time.perf_counter()
+    for _ in range(ndir):
+        d = torch.randn(U0.shape, dtype=torch.float64, device="cuda", generator=gen)
+        fdv = (J(U0 + h * d) - J(U0 - h * d)) / (2 * h)
+        ad = float((grad * d).sum())
+        errs.append(abs(ad - fdv) / max(abs(fdv), 1e-300))
+    return {"directions": ndir, "h": h, "max_rel_err": max(errs),
+            "median_rel_err": sorted(errs)[len(errs) // 2], "seconds": time.perf_counter() - t0,
+            "map": "frozen-mask rollout (radii and dt of the forward held fixed)"}
 
 
 def run_reference(args, world, rank):
@@ -493,6 +538,8 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="time a rollout and its adjoint instead (shear layer, GP-R2)")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-fd", type=int, default=8,
+                    help="random directions of the finite-difference check (0: skip)")
     ap.add_argument("--batch", type=int, default=0,
                     help="time a batch of this many uneven four-quadrant problems instead")
     args = ap.parse_args()

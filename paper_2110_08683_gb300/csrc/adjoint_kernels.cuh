@@ -35,7 +35,7 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
   const Real pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
   const Real pR = gm1 * (UR[3] - Real(0.5) * (UR[1] * uR + UR[2] * vR));
   const Real zL = gam * pL * irL, zR = gam * pR * irR;
-  const Real cL = sqrt(zL), cR = sqrt(zR);
+  const Real cL = sqrt_r(zL), cR = sqrt_r(zR);
   const Real aL = uL - cL, bL = uR - cR;
   const bool selA = aL < bL;
   const Real SL = selA ? aL : bL;

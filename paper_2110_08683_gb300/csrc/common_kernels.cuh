@@ -13,7 +13,8 @@ __global__ void k_fill_ghosts(double* X, float* Xf, Grid g, const Scalars* sc, d
 
 // time step: min over cells of min(dx/(|u|+c), dy/(|v|+c)), per-direction
 // CFL form; positive doubles order like their bit patterns
-__global__ void k_dt_reduce(const double* X, Grid g, Scalars* sc) {
+// Xf: the float shadow of X on the FP32 path (the rate in float), else null
+__global__ void k_dt_reduce(const double* X, const float* Xf, Grid g, Scalars* sc) {
   if (sc->ctl.fixed_dt > 0.0) return;
   double best = 0.0;
   bool bad = false;
@@ -21,9 +22,8 @@ __global__ void k_dt_reduce(const double* X, Grid g, Scalars* sc) {
   for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     int i = (int)(c % g.nx), j = (int)(c / g.nx);
-    double S[4], a;
-    load_cell(X, g, i, j, S);
-    if (!cell_rate(S, g, a)) bad = true;
+    double a;
+    if (!cell_rate_at(X, Xf, g, i, j, a)) bad = true;
     else best = a > best ? a : best;
   }
   for (int o = 16; o > 0; o >>= 1) {

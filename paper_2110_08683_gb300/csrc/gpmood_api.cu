@@ -127,8 +127,8 @@ StageArgs<Real> stage_args(gpmood_t h, int s, int ia, int ix, int io) {
     A.Xr = h->U[ix];
     A.outr = nullptr;
   }
-  A.Fx = (Real*)h->Fx;
-  A.Fy = (Real*)h->Fy;
+  A.Fx = (double*)h->Fx;
+  A.Fy = (double*)h->Fy;
   A.cad = h->cad;
   A.ord = h->ord + s * nc;
   A.first = h->first + s * nc;
@@ -242,7 +242,7 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
   write_control(h, cfl, fixed_dt, clip, t_end);
   int rc = push_control(h);
   if (rc) return rc;
-  CK(launch_dt(h->U[a], h->g, h->sc, h->stream));
+  CK(launch_dt(h->U[a], h->Uf[a], h->g, h->sc, h->stream));
   const int in[3] = {a, b, c}, out[3] = {b, c, b};
   const size_t nc = (size_t)h->g.nx * h->g.ny;
   for (int s = 0; s < 3; ++s) {
@@ -347,7 +347,7 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = 0;
   rec_event(h, prof, GPMOOD_K_DT, 1, st);
-  if (launch_dt(h->U[a], h->g, h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
+  if (launch_dt(h->U[a], h->Uf[a], h->g, h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
   rec_event(h, prof, GPMOOD_K_DT, 0, st);
   for (int s = 0; s < 3 && !rc; ++s)
     rc = h->precision == GPMOOD_FP32
@@ -419,11 +419,12 @@ cudaError_t launch_fill(double* X, float* Xf, const Grid& g, const Scalars* sc, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_dt(const double* X, const Grid& g, Scalars* sc, cudaStream_t st) {
+cudaError_t launch_dt(const double* X, const float* Xf, const Grid& g, Scalars* sc,
+                      cudaStream_t st) {
   long long n = (long long)g.nx * g.ny;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_dt_reduce<<<blocks, 256, 0, st>>>(X, g, sc);
+  k_dt_reduce<<<blocks, 256, 0, st>>>(X, Xf, g, sc);
   k_dt_finalize<<<1, 32, 0, st>>>(sc);
   return cudaGetLastError();
 }
@@ -583,7 +584,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
 
   // device buffers
   const size_t ncell = (size_t)g.nx * g.ny;
-  const size_t fsz = h->precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  const size_t fsz = sizeof(double);  // face fluxes are FP64 on both paths
   bool ok = true;
   for (int k = 0; k < 3; ++k)
     ok = ok && cudaMalloc(&h->U[k], sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess;
@@ -800,7 +801,7 @@ int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>
   write_control(h, 1.0, dt, 0, 0.0);
   int rc = push_control(h);
   if (rc) return rc;
-  CK(launch_dt(h->U[a], h->g, h->sc, h->stream));
+  CK(launch_dt(h->U[a], h->Uf[a], h->g, h->sc, h->stream));
   const int in[3] = {a, b, c}, out[3] = {b, c, b};
   const size_t nc = (size_t)h->g.nx * h->g.ny;
   static const double tfrac[3] = {0.0, 1.0, 0.5};
@@ -1001,7 +1002,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
 
   // carve the buffers out of the scratch, 256-byte aligned each
   const size_t ncell = (size_t)g.nx * g.ny;
-  const size_t fsz = o.precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  const size_t fsz = sizeof(double);  // face fluxes are FP64 on both paths
   const size_t sz_state = align256(sizeof(double) * 4 * (size_t)g.vstride);
   const size_t sz_fx = align256(fsz * 4 * (size_t)g.ny * (g.nx + 1));
   const size_t sz_fy = align256(fsz * 4 * (size_t)(g.ny + 1) * g.nx);

@@ -22,23 +22,23 @@ using namespace gpm;
 namespace gpm {
 
 // per-problem time-step reduction over (problem, chunk) items
-__global__ void k_dt_reduce_batch(const double* X, const Prob* probs, Scalars* psc, Scalars* gsc,
-                                  const Item* items, int nitems) {
+__global__ void k_dt_reduce_batch(const double* X, const float* Xf, const Prob* probs,
+                                  Scalars* psc, Scalars* gsc, const Item* items, int nitems) {
   if (gsc->ctl.fixed_dt > 0.0) return;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const Item w = items[it];
     const Prob& P = probs[w.p];
     const Grid& g = P.g;
     const double* Xp = X + P.state_off;
+    const float* Xfp = Xf ? Xf + P.state_off : nullptr;
     double best = 0.0;
     bool bad = false;
     const long long c0 = (long long)w.a * 4096;
     const long long c1 = c0 + 4096 < (long long)P.ncell ? c0 + 4096 : (long long)P.ncell;
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
       int i = (int)(c % g.nx), j = (int)(c / g.nx);
-      double S[4], a;
-      load_cell(Xp, g, i, j, S);
-      if (!cell_rate(S, g, a)) bad = true;
+      double a;
+      if (!cell_rate_at(Xp, Xfp, g, i, j, a)) bad = true;
       else best = a > best ? a : best;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -203,8 +203,8 @@ StageArgs<Real> batch_args(gpmood_batch_t b, int s, int ia, int ix, int io) {
     A.Xr = b->U[ix];
     A.outr = nullptr;
   }
-  A.Fx = (Real*)b->Fx;
-  A.Fy = (Real*)b->Fy;
+  A.Fx = (double*)b->Fx;
+  A.Fy = (double*)b->Fy;
   A.cad = b->cad;
   A.ord = b->ord + (size_t)s * b->total_cells;
   A.first = b->first + (size_t)s * b->total_cells;
@@ -224,8 +224,8 @@ int pull(gpmood_batch_t b) {
 
 int launch_dt_batch(gpmood_batch_t b, int ia, cudaStream_t st) {
   k_batch_reset<<<1, 32, 0, st>>>(b->gsc);
-  k_dt_reduce_batch<<<b->dt_blocks, 256, 0, st>>>(b->U[ia], b->probs, b->psc, b->gsc, b->items_dt,
-                                                  b->n_dt);
+  k_dt_reduce_batch<<<b->dt_blocks, 256, 0, st>>>(b->U[ia], b->Uf[ia], b->probs, b->psc, b->gsc,
+                                                  b->items_dt, b->n_dt);
   k_dt_finalize_batch<<<1, 256, 0, st>>>(b->psc, b->gsc, b->nprob);
   return cudaGetLastError() == cudaSuccess ? 0 : GPMOOD_E_CUDA;
 }
@@ -545,7 +545,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   b->hprobs.resize(nprob);
   long long soff = 0, fxo = 0, fyo = 0;
   int coff = 0;
-  const size_t fsz = b->precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  const size_t fsz = sizeof(double);  // face fluxes are FP64 on both paths
   std::vector<Item> fx4, fx8, fy4, fy8, up, dtl;
   long long max_ghost = 0;
   for (int p = 0; p < nprob; ++p) {

@@ -99,8 +99,8 @@ struct StageArgs {
   const double* U0;  // ghosted U^n (combination)
   double* out;       // ghosted stage output
   Real* outr;        // float shadow of out (FP32), null (FP64)
-  Real* Fx;
-  Real* Fy;
+  double* Fx;        // face-averaged fluxes, FP64 on both paths: each float flux is
+  double* Fy;        // widened once, by the face kernel, not once per neighbour
   uint8_t* cad;
   uint8_t* ord;      // radius per cell, this stage
   uint8_t* first;    // first-pass troubled map, this stage

@@ -140,10 +140,10 @@ __device__ __forceinline__ bool finite_r(Real x) {
   return isfinite(x);
 }
 
-// reciprocal.  FP64: the hardware approximation (rcp.approx.ftz.f64) refined
-// by two Newton-Raphson steps r <- r + r (1 - x r), each of which squares the
-// relative error; non-finite or zero x give a non-finite result.  FP32: the
-// IEEE division.
+// reciprocal by Newton-Raphson from the hardware approximation: each step
+// r <- r + r (1 - x r) squares the relative error.  FP64: rcp.approx.ftz.f64
+// and two steps; FP32: rcp.approx.ftz.f32 (within 1 ulp) and one step.  Zero
+// or non-finite x give a non-finite result.
 __device__ __forceinline__ double recip(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
@@ -152,7 +152,21 @@ __device__ __forceinline__ double recip(double x) {
   e = fma(-x, r, 1.0);
   return fma(r, e, r);
 }
-__device__ __forceinline__ float recip(float x) { return 1.0f / x; }
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
+// square root of a sound-speed argument: FP64 the IEEE square root; FP32 the
+// hardware approximation sqrt.approx.ftz.f32 (the FP32 path's reconstruction
+// and Riemann solver are FP32 arithmetic throughout)
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_r(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // x-direction HLLC flux; pL/pR return the pressures of the two states so the
 // caller can run face-state CAD without another EoS evaluation.
@@ -168,7 +182,7 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   Real uR = UR[1] * irR, vR = UR[2] * irR;
   pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
   pR = gm1 * (UR[3] - Real(0.5) * (UR[1] * uR + UR[2] * vR));
-  Real cL = sqrt(gam * pL * irL), cR = sqrt(gam * pR * irR);
+  Real cL = sqrt_r(gam * pL * irL), cR = sqrt_r(gam * pR * irR);
   Real aL = uL - cL, bL = uR - cR;
   Real SL = aL < bL ? aL : bL;
   Real aR = uL + cL, bR = uR + cR;
@@ -224,6 +238,33 @@ __device__ __forceinline__ bool cell_rate(const double* S, const Grid& g, double
   const double ax = (fabs(u) + cs) * g.inv_dx, ay = (fabs(v) + cs) * g.inv_dy;
   rate = (g.dim == 1 || ax > ay) ? ax : ay;  // a NaN state makes both rates NaN
   return rate > 0.0 && isfinite(rate);
+}
+
+// the same rate on the FP32 path: from the float shadow, in float
+__device__ __forceinline__ bool cell_rate(const float* S, const Grid& g, double& rate) {
+  const float gam = (float)g.gamma;
+  const float ir = recip(S[0]);
+  const float u = S[1] * ir, v = S[2] * ir;
+  const float p = (gam - 1.0f) * (S[3] - 0.5f * (S[1] * u + S[2] * v));
+  const float cs = sqrt_r(gam * p * ir);
+  const float ax = (fabsf(u) + cs) * (float)g.inv_dx, ay = (fabsf(v) + cs) * (float)g.inv_dy;
+  const float r = (g.dim == 1 || ax > ay) ? ax : ay;
+  rate = (double)r;
+  return r > 0.0f && isfinite(r);
+}
+
+// the rate of cell (i, j): the double state, or its float shadow when Xf is set
+__device__ __forceinline__ bool cell_rate_at(const double* X, const float* Xf, const Grid& g,
+                                             int i, int j, double& rate) {
+  if (Xf) {
+    float S[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) S[v] = Xf[gidx(g, v, i, j)];
+    return cell_rate(S, g, rate);
+  }
+  double S[4];
+  load_cell(X, g, i, j, S);
+  return cell_rate(S, g, rate);
 }
 
 // value of the x-ghost (i outside [0,nx)) of interior row j
@@ -620,8 +661,8 @@ __device__ __forceinline__ void candidate(const StageArgs<Real>& A, const Grid& 
                                           double dt, double* Y) {
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double fe = (double)A.Fx[fxidx(g, v, i + 1, j)], fw = (double)A.Fx[fxidx(g, v, i, j)];
-    double gn = (double)A.Fy[fyidx(g, v, i, j + 1)], gs = (double)A.Fy[fyidx(g, v, i, j)];
+    double fe = A.Fx[fxidx(g, v, i + 1, j)], fw = A.Fx[fxidx(g, v, i, j)];
+    double gn = A.Fy[fyidx(g, v, i, j + 1)], gs = A.Fy[fyidx(g, v, i, j)];
     Y[v] = A.X[gidx(g, v, i, j)] - dt * ((fe - fw) * g.inv_dx + (gn - gs) * g.inv_dy);
   }
 }
