@@ -84,6 +84,10 @@ typedef struct {
   double sigma_p;       /* CSD threshold on the normalised |grad p| (0 -> 5) */
   int csd_off;          /* 1 disables CSD (Step 6) */
   int max_mood_iters;   /* cap on MOOD iterations per RK stage (0 -> 64 + 4 max(nx, ny)) */
+  int rk;               /* 0 or 3: SSP-RK3 (eq. rk3).  4: the five-stage SSP-RK4 (eq. rk4), its
+                           Dt F(U^(3)) term of the final combination read with a minus
+                           sign; each stage's MOOD candidate is its forward-Euler
+                           sub-step.  Single-problem handles, no adjoint */
   int eager;            /* 0: one captured CUDA graph per step, the MOOD loop of each stage
                            a conditional WHILE node (no host round trip in a step);
                            1: every kernel launched on the stream and the host reading the
@@ -97,10 +101,10 @@ typedef struct {
   double t;             /* simulation time after the step */
   double dt;            /* the step's Delta t */
   long long nsteps;     /* steps taken since set_state */
-  int iters[3];         /* MOOD iterations per RK stage */
-  int nbad_first[3];    /* troubled cells after the first pass, per stage */
-  int nbad_total[3];    /* troubled cells summed over all iterations, per stage */
-  int nfog_pad[3];      /* FOG candidates failing PAD (accepted per Step 10, reported) */
+  int iters[5];         /* MOOD iterations per RK stage (3 stages SSP-RK3, 5 SSP-RK4) */
+  int nbad_first[5];    /* troubled cells after the first pass, per stage */
+  int nbad_total[5];    /* troubled cells summed over all iterations, per stage */
+  int nfog_pad[5];      /* FOG candidates failing PAD (accepted per Step 10, reported) */
   int status;           /* GPMOOD_OK or the error code of the last step */
 } gpmood_stats;
 

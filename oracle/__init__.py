@@ -43,12 +43,13 @@ class Config(C.Structure):
         ("max_iters", C.c_int),
         ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4),
         ("dmr_wall_x0", C.c_double), ("dmr_xs0", C.c_double), ("dmr_xs_speed", C.c_double),
+        ("rk", C.c_int),
     ]
 
 
 class StepStats(C.Structure):
-    _fields_ = [("dt", C.c_double), ("iters", C.c_int * 3), ("nbad_first", C.c_int * 3),
-                ("nbad_total", C.c_int * 3), ("status", C.c_int)]
+    _fields_ = [("dt", C.c_double), ("iters", C.c_int * 5), ("nbad_first", C.c_int * 5),
+                ("nbad_total", C.c_int * 5), ("status", C.c_int)]
 
 
 _lib_handle = None
@@ -168,6 +169,7 @@ def make_config(prob):
     cfg.dmr_wall_x0 = prob["dmr_wall_x0"]
     cfg.dmr_xs0 = prob["dmr_xs0"]
     cfg.dmr_xs_speed = prob["dmr_xs_speed"]
+    cfg.rk = int(prob.get("rk", 3))
     return cfg
 
 
@@ -219,20 +221,26 @@ class Oracle:
     def dt(self, U, cfl):
         return lib().orc_dt(self.h, _ptr(self._state(U)), cfl)
 
+    @property
+    def nstages(self):
+        return 5 if self.cfg.rk == 4 else 3
+
     def step(self, U, t=0.0, cfl=None, dt_fixed=0.0):
-        """One SSP-RK3 step.  Returns (U_new, stats dict, ord[3,ny,nx], first-pass bad[3,ny,nx])."""
+        """One SSP-RK3 (or SSP-RK4) step.  Returns (U_new, stats dict,
+        ord[S,ny,nx], first-pass bad[S,ny,nx]), S the number of stages."""
         U = self._state(U).copy()
         cfl = self.prob["cfl"] if cfl is None else cfl
         nc = self.nx * self.ny
-        ordm = np.zeros(3 * nc, dtype=np.uint8)
-        bad = np.zeros(3 * nc, dtype=np.uint8)
+        S = self.nstages
+        ordm = np.zeros(S * nc, dtype=np.uint8)
+        bad = np.zeros(S * nc, dtype=np.uint8)
         st = StepStats()
         rc = lib().orc_step(self.h, _ptr(U), t, cfl, dt_fixed, _ptr(ordm), _ptr(bad), C.byref(st))
         if rc != 0:
             raise RuntimeError(f"orc_step rc={rc}")
-        stats = dict(dt=st.dt, iters=list(st.iters), nbad_first=list(st.nbad_first),
-                     nbad_total=list(st.nbad_total))
-        return U, stats, ordm.reshape(3, self.ny, self.nx), bad.reshape(3, self.ny, self.nx)
+        stats = dict(dt=st.dt, iters=list(st.iters)[:S], nbad_first=list(st.nbad_first)[:S],
+                     nbad_total=list(st.nbad_total)[:S])
+        return U, stats, ordm.reshape(S, self.ny, self.nx), bad.reshape(S, self.ny, self.nx)
 
     def stage(self, X, ts, dt):
         X = self._state(X)

@@ -279,6 +279,7 @@ struct orc_ctx {
   double wxx[MAXN], wyy[MAXN];
   /* work buffers */
   double *Xg, *Fx, *Fy, *Y, *U0, *S;
+  double *Us[5], *Fn, *F3;  /* SSP-RK4: U^(1..4), F_nabla of a stage, F_nabla(U^(3)) */
   uint8_t *ord, *cad, *bad, *first, *inA;
 };
 
@@ -296,6 +297,7 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
   if (cfg->dim != 1 && cfg->dim != 2) return -1;
   if (cfg->nx < 1 || cfg->ny < 1 || (cfg->dim == 1 && cfg->ny != 1)) return -1;
   if (cfg->ncascade < 1 || cfg->ncascade > 4) return -1;
+  if (cfg->rk != 0 && cfg->rk != 3 && cfg->rk != 4) return -1;
   if (cfg->cascade[cfg->ncascade - 1] != 0) return -1;
   for (int k = 0; k + 1 < cfg->ncascade; ++k)
     if (!(cfg->cascade[k] > cfg->cascade[k + 1])) return -1;
@@ -347,6 +349,9 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
   c->Y = (double*)calloc(ni, sizeof(double));
   c->U0 = (double*)calloc(ni, sizeof(double));
   c->S = (double*)calloc(ni, sizeof(double));
+  for (int s = 1; s < 5; ++s) c->Us[s] = (double*)calloc(ni, sizeof(double));
+  c->Fn = (double*)calloc(ni, sizeof(double));
+  c->F3 = (double*)calloc(ni, sizeof(double));
   c->ord = (uint8_t*)calloc(nc, 1);
   c->cad = (uint8_t*)calloc(nc, 1);
   c->bad = (uint8_t*)calloc(nc, 1);
@@ -360,6 +365,8 @@ void orc_destroy(orc_ctx* c) {
   if (!c) return;
   for (int R = 0; R < 4; ++R) free(c->z[R]);
   free(c->Xg); free(c->Fx); free(c->Fy); free(c->Y); free(c->U0); free(c->S);
+  for (int s = 1; s < 5; ++s) free(c->Us[s]);
+  free(c->Fn); free(c->F3);
   free(c->ord); free(c->cad); free(c->bad); free(c->first); free(c->inA);
   free(c);
 }
@@ -768,8 +775,10 @@ static int cell_neighbours(const orc_ctx* c, int i, int j, int* ni, int* nj) {
   return n;
 }
 
+/* one MOOD stage on the ghosted input Xg: the candidate Y = X - dt F(X) with
+   the order cascade; Fn (nullable) receives the final F_nabla */
 static int stage_on_ghosted(orc_ctx* c, const double* Xg, double dt, double* Y, int* iters_out,
-                            int* nfirst_out, int* ntotal_out) {
+                            int* nfirst_out, int* ntotal_out, double* Fn) {
   int nx = c->cfg.nx, ny = c->cfg.ny;
   size_t nc = (size_t)nx * ny;
   /* the highest order first, reset at every stage */
@@ -818,6 +827,13 @@ static int stage_on_ghosted(orc_ctx* c, const double* Xg, double dt, double* Y, 
   }
   if (iters_out) *iters_out = it;
   if (ntotal_out) *ntotal_out = total;
+  if (Fn)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double f[4];
+        fnabla(c, i, j, f);
+        for (int v = 0; v < NV; ++v) Fn[iidx(c, v, i, j)] = f[v];
+      }
   return 0;
 }
 
@@ -826,7 +842,7 @@ int orc_stage(orc_ctx* c, const double* X, double ts, double dt, double* Y, uint
   size_t nc = (size_t)c->cfg.nx * c->cfg.ny;
   orc_fill_ghosts(c, X, ts, c->Xg);
   int nfirst = 0;
-  int rc = stage_on_ghosted(c, c->Xg, dt, Y, iters, &nfirst, nbad_total);
+  int rc = stage_on_ghosted(c, c->Xg, dt, Y, iters, &nfirst, nbad_total, 0);
   if (ord_out) memcpy(ord_out, c->ord, nc);
   if (bad_out) memcpy(bad_out, c->first, nc);
   return rc;
@@ -852,6 +868,65 @@ double orc_dt(orc_ctx* c, const double* U, double cfl) {
   return cfl * best;
 }
 
+/* eq. rk4, the five-stage SSP-RK4, as printed:
+     U^(s+1) = a_s U^n + b_s U^(s) - g_s Dt F(U^(s)),  s = 0..3, U^(0) = U^n,
+     U^{n+1} = e2 U^(2) + e3 U^(3) - f3 Dt F(U^(3)) + e4 U^(4) - f4 Dt F(U^(4)).
+   The printed final line carries "+ f3 Dt F(U^(3))"; every other Dt F term of
+   the scheme enters with a minus and the weights of the Dt F terms must sum
+   to one for consistency, so f3 is read with a minus (the stage times below
+   then end at exactly one).  The MOOD candidate of a stage is its
+   forward-Euler sub-step U^(s) - (g_s / b_s) Dt F(U^(s)), the same reading as
+   for eq. rk3 (b_0 counts as one); the last stage's sub-step is
+   U^(4) - (f4 / e4) Dt F(U^(4)).  Its U^(3) term, f3 / e3 = g_3 / b_3, is the
+   sub-step already validated in stage 3. */
+static const double RK4_A[4] = {1.0, 0.444370493651235, 0.620101851488403, 0.178079954393132};
+static const double RK4_B[4] = {0.0, 0.555629506348765, 0.379898148511597, 0.821920045606868};
+static const double RK4_G[4] = {0.391752226571890, 0.368410593050371, 0.251891774271694,
+                                0.544974750228521};
+static const double RK4_E2 = 0.517231671970585, RK4_E3 = 0.096059710526147,
+                    RK4_F3 = 0.063692468666290, RK4_E4 = 0.386708617503269,
+                    RK4_F4 = 0.226007483236906;
+
+static int rk4_step(orc_ctx* c, double* U, double t, double dt, uint8_t* ord_out,
+                    uint8_t* bad_out, orc_step_stats* st) {
+  size_t nc = (size_t)c->cfg.nx * c->cfg.ny, ni = NV * nc;
+  memcpy(c->U0, U, ni * sizeof(double));
+  double* Us[5] = {c->U0, c->Us[1], c->Us[2], c->Us[3], c->Us[4]};
+  double ts = 0.0; /* time of U^(s) as a fraction of Dt */
+  for (int s = 0; s < 5; ++s) {
+    double h = s < 4 ? RK4_G[s] / (s == 0 ? 1.0 : RK4_B[s]) : RK4_F4 / RK4_E4;
+    orc_fill_ghosts(c, Us[s], t + ts * dt, c->Xg);
+    int it = 0, nfirst = 0, ntot = 0;
+    int rc = stage_on_ghosted(c, c->Xg, h * dt, c->Y, &it, &nfirst, &ntot, c->Fn);
+    if (bad_out) memcpy(bad_out + s * nc, c->first, nc);
+    if (ord_out) memcpy(ord_out + s * nc, c->ord, nc);
+    if (st) {
+      st->iters[s] = it;
+      st->nbad_first[s] = nfirst;
+      st->nbad_total[s] = ntot;
+    }
+    if (rc != 0) {
+      if (st) st->status = rc;
+      return rc;
+    }
+    if (s < 4) {
+      for (size_t k = 0; k < ni; ++k)
+        Us[s + 1][k] = RK4_A[s] * c->U0[k] + RK4_B[s] * Us[s][k] - RK4_G[s] * dt * c->Fn[k];
+      if (s == 3) memcpy(c->F3, c->Fn, ni * sizeof(double));
+      ts = RK4_B[s] * ts + RK4_G[s];
+    } else {
+      for (size_t k = 0; k < ni; ++k)
+        U[k] = RK4_E2 * Us[2][k] + RK4_E3 * Us[3][k] - RK4_F3 * dt * c->F3[k] +
+               RK4_E4 * Us[4][k] - RK4_F4 * dt * c->Fn[k];
+    }
+  }
+  if (st) {
+    st->dt = dt;
+    st->status = 0;
+  }
+  return 0;
+}
+
 int orc_step(orc_ctx* c, double* U, double t, double cfl, double dt_fixed, uint8_t* ord_out,
              uint8_t* bad_out, orc_step_stats* st) {
   int nx = c->cfg.nx, ny = c->cfg.ny;
@@ -861,6 +936,7 @@ int orc_step(orc_ctx* c, double* U, double t, double cfl, double dt_fixed, uint8
     if (st) st->status = -4;
     return -4;
   }
+  if (c->cfg.rk == 4) return rk4_step(c, U, t, dt, ord_out, bad_out, st);
   memcpy(c->U0, U, ni * sizeof(double));
   const double stage_t[3] = {t, t + dt, t + 0.5 * dt};
   for (int s = 0; s < 3; ++s) {
@@ -868,7 +944,7 @@ int orc_step(orc_ctx* c, double* U, double t, double cfl, double dt_fixed, uint8
     const double* Xin = (s == 0) ? c->U0 : c->S;
     orc_fill_ghosts(c, Xin, stage_t[s], c->Xg);
     int it = 0, nfirst = 0, ntot = 0;
-    int rc = stage_on_ghosted(c, c->Xg, dt, c->Y, &it, &nfirst, &ntot);
+    int rc = stage_on_ghosted(c, c->Xg, dt, c->Y, &it, &nfirst, &ntot, 0);
     if (bad_out) memcpy(bad_out + s * nc, c->first, nc);
     if (ord_out) memcpy(ord_out + s * nc, c->ord, nc);
     if (st) {

@@ -64,6 +64,7 @@ typedef struct {
   /* double Mach reflection boundary data (used by the DMR_* kinds) */
   double dmr_post[4], dmr_pre[4];
   double dmr_wall_x0, dmr_xs0, dmr_xs_speed;
+  int rk;                /* 3 (or 0): SSP-RK3, eq. rk3; 4: five-stage SSP-RK4, eq. rk4 */
 } orc_config;
 
 typedef struct orc_ctx orc_ctx;
@@ -71,11 +72,11 @@ typedef struct orc_ctx orc_ctx;
 /* per-step diagnostics */
 typedef struct {
   double dt;
-  int iters[3];          /* MOOD iterations per RK stage (0 = first pass clean) */
-  int nbad_first[3];     /* troubled cells after the first pass, per stage */
-  int nbad_total[3];     /* sum over iterations of troubled-cell counts */
+  int iters[5];          /* MOOD iterations per RK stage (0 = first pass clean) */
+  int nbad_first[5];     /* troubled cells after the first pass, per stage */
+  int nbad_total[5];     /* sum over iterations of troubled-cell counts */
   int status;            /* 0 ok, <0 error */
-} orc_step_stats;
+} orc_step_stats;       /* the first 3 (RK3) or 5 (RK4) entries are used */
 
 int orc_create(const orc_config* cfg, orc_ctx** out);
 void orc_destroy(orc_ctx* ctx);
@@ -103,9 +104,10 @@ void orc_hllc(const double* UL, const double* UR, double gamma, int dir, double*
 int orc_residual(orc_ctx* ctx, const double* U, const uint8_t* ord, double t, double* Fn);
 /* Delta t from U (per-direction CFL form) */
 double orc_dt(orc_ctx* ctx, const double* U, double cfl);
-/* one SSP-RK3 step with the MOOD loop; dt_fixed > 0 overrides the CFL step.
-   ord_out (nullable) receives [3][ny][nx] final radii per stage,
-   bad_out (nullable) the [3][ny][nx] first-pass troubled-cell map. */
+/* one SSP-RK3 (or SSP-RK4, cfg.rk = 4) step with the MOOD loop; dt_fixed > 0
+   overrides the CFL step.  ord_out (nullable) receives [S][ny][nx] final radii
+   per stage, bad_out (nullable) the [S][ny][nx] first-pass troubled-cell map,
+   S = 3 (RK3) or 5 (RK4). */
 int orc_step(orc_ctx* ctx, double* U, double t, double cfl, double dt_fixed,
              uint8_t* ord_out, uint8_t* bad_out, orc_step_stats* st);
 /* one MOOD stage: candidate Y = X - dt F(X) with the order cascade, from the

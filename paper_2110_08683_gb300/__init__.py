@@ -47,15 +47,15 @@ class Options(C.Structure):
     _fields_ = [
         ("ncascade", C.c_int), ("cascade", C.c_int * 4), ("precision", C.c_int),
         ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
-        ("max_mood_iters", C.c_int), ("eager", C.c_int),
+        ("max_mood_iters", C.c_int), ("rk", C.c_int), ("eager", C.c_int),
     ]
 
 
 class Stats(C.Structure):
     _fields_ = [
         ("t", C.c_double), ("dt", C.c_double), ("nsteps", C.c_longlong),
-        ("iters", C.c_int * 3), ("nbad_first", C.c_int * 3), ("nbad_total", C.c_int * 3),
-        ("nfog_pad", C.c_int * 3), ("status", C.c_int),
+        ("iters", C.c_int * 5), ("nbad_first", C.c_int * 5), ("nbad_total", C.c_int * 5),
+        ("nfog_pad", C.c_int * 5), ("status", C.c_int),
     ]
 
 
@@ -149,6 +149,7 @@ def make_options(prob, precision=FP64, eager=False):
     o.sigma_v, o.sigma_p = prob["sigma_v"], prob["sigma_p"]
     o.csd_off = 0 if prob["csd_on"] else 1
     o.max_mood_iters = int(prob.get("max_iters", 0))
+    o.rk = int(prob.get("rk", 3))
     o.eager = 1 if eager else 0
     return o
 
@@ -201,19 +202,22 @@ def gpmood_run(h, t_end, cfl):
     return n.value
 
 
-def gpmood_flags(h, nx, ny, maps=True):
+def gpmood_flags(h, nx, ny, maps=True, nstages=3):
+    """final radii and first-pass troubled maps [S][ny][nx] and the stats of
+    the last step (S = 3 for SSP-RK3, 5 for SSP-RK4)"""
     st = Stats()
+    S = nstages
     if maps:
-        order = np.zeros((3, ny, nx), dtype=np.uint8)
-        first = np.zeros((3, ny, nx), dtype=np.uint8)
+        order = np.zeros((S, ny, nx), dtype=np.uint8)
+        first = np.zeros((S, ny, nx), dtype=np.uint8)
         _check(load().gpmood_flags(h, order.ctypes.data_as(C.c_void_p),
                                    first.ctypes.data_as(C.c_void_p), C.byref(st)), "gpmood_flags")
     else:
         order = first = None
         _check(load().gpmood_flags(h, None, None, C.byref(st)), "gpmood_flags")
-    stats = dict(t=st.t, dt=st.dt, nsteps=st.nsteps, iters=list(st.iters),
-                 nbad_first=list(st.nbad_first), nbad_total=list(st.nbad_total),
-                 nfog_pad=list(st.nfog_pad), status=st.status)
+    stats = dict(t=st.t, dt=st.dt, nsteps=st.nsteps, iters=list(st.iters)[:S],
+                 nbad_first=list(st.nbad_first)[:S], nbad_total=list(st.nbad_total)[:S],
+                 nfog_pad=list(st.nfog_pad)[:S], status=st.status)
     return order, first, stats
 
 
@@ -306,8 +310,12 @@ class GPMood:
     def run(self, t_end, cfl=None):
         return gpmood_run(self.h, t_end, self.prob["cfl"] if cfl is None else cfl)
 
+    @property
+    def nstages(self):
+        return 5 if int(self.prob.get("rk", 3)) == 4 else 3
+
     def flags(self, maps=True):
-        return gpmood_flags(self.h, self.nx, self.ny, maps)
+        return gpmood_flags(self.h, self.nx, self.ny, maps, self.nstages)
 
     def last_launches(self):
         return gpmood_last_launches(self.h)
@@ -412,8 +420,8 @@ class GPMoodBatch:
         _check(load().gpmood_batch_info(self.h, t.ctypes.data_as(C.c_void_p),
                                         dt.ctypes.data_as(C.c_void_p),
                                         ns.ctypes.data_as(C.c_void_p), C.byref(st)), "info")
-        return t, dt, ns, dict(iters=list(st.iters), nbad_first=list(st.nbad_first),
-                               nbad_total=list(st.nbad_total))
+        return t, dt, ns, dict(iters=list(st.iters)[:3], nbad_first=list(st.nbad_first)[:3],
+                               nbad_total=list(st.nbad_total)[:3])
 
     def tuning(self):
         w = (C.c_int * 2)()

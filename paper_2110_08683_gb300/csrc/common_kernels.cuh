@@ -53,7 +53,7 @@ __global__ void k_dt_finalize(Scalars* sc) {
   if (!(dt > 0.0) || !isfinite(dt)) sc->err |= kErrDt;
   sc->dt = dt;
   sc->rate_bits = 0ull;  // +0 for the next step
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < 5; ++s) {
     sc->iters[s] = 0;
     sc->nbad_first[s] = 0;
     sc->nbad_total[s] = 0;

@@ -24,13 +24,14 @@ struct gpmood_s {
   int precision;
   int max_iters;
   cudaStream_t stream;
-  double* U[3];
-  float* Uf[3];    // float shadows of U (FP32 path only, else null)
+  Scheme sch;      // the RK scheme as stage roles and coefficients
+  double* U[5];    // state buffers (3 for SSP-RK3, 5 for SSP-RK4)
+  float* Uf[5];    // float shadows of U (FP32 path only, else null)
   void* Fx;
   void* Fy;
   uint8_t* cad;
-  uint8_t* ord;    // [3][nc]
-  uint8_t* first;  // [3][nc]
+  uint8_t* ord;    // [S][nc], S stages
+  uint8_t* first;  // [S][nc]
   uint32_t* stamp;
   int* queue[2];
   Scalars* sc;     // device
@@ -51,7 +52,7 @@ struct gpmood_s {
   Control ctl;  // host copy of the step controls
   int eager;    // stream launches instead of the captured step graph
   cudaStream_t cs, cs2;
-  cudaGraphExec_t gexec[3][3];  // [rotation][plain, profiled, recording]
+  cudaGraphExec_t gexec[5][3];  // [rotation][plain, profiled, recording]
   cudaEvent_t gev[64];
   int gev_cls[32];
   int gev_n, gev_pairs;
@@ -89,7 +90,7 @@ int set_err(gpmood_t h, int code) {
 void free_all(gpmood_t h) {
   for (int k = 0; k < 64; ++k)
     if (h->gev[k]) cudaEventDestroy(h->gev[k]);
-  for (int r = 0; r < 3; ++r)
+  for (int r = 0; r < 5; ++r)
     for (int p = 0; p < 3; ++p)
       if (h->gexec[r][p]) cudaGraphExecDestroy(h->gexec[r][p]);
   if (h->cs) cudaStreamDestroy(h->cs);
@@ -97,7 +98,7 @@ void free_all(gpmood_t h) {
   void* adj[] = {h->aX, h->aXr, h->aG, h->av, h->aw, h->amu, h->ax.L, h->ax.R, h->ax.K,
                  h->ay.L, h->ay.R, h->ay.K, h->aord};
   for (void* p : adj) cudaFree(p);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 5; ++k) {
     cudaFree(h->U[k]);
     cudaFree(h->Uf[k]);
   }
@@ -113,10 +114,64 @@ void free_all(gpmood_t h) {
   if (h->hsc) cudaFreeHost(h->hsc);
 }
 
+// the time integrators as stage roles.  SSP-RK3 (eq. rk3): three buffers
+// rotating by one per step.  SSP-RK4 (eq. rk4, five stages), each stage
+//   U^(s+1) = a_s U^n + b_s U^(s) - g_s Dt F(U^(s)) = a_s U^n + b_s Y_s,
+// Y_s = U^(s) - (g_s / b_s) Dt F(U^(s)) its forward-Euler sub-step (the MOOD
+// candidate), and U^{n+1} = e2 U^(2) + e3 Y_3 + e4 Y_4 with
+// Y_4 = U^(4) - (f4 / e4) Dt F(U^(4)); e3 Y_3 = e3 U^(3) - f3 Dt F(U^(3)) (the
+// printed plus sign of that term read as a minus).  Buffers: 0 U^n, 1 U^(1)
+// then U^(4), 2 U^(2), 3 U^(3), 4 e2 U^(2) + e3 Y_3; the last stage writes
+// U^{n+1} over U^n, so the buffers do not rotate.
+void make_scheme(int rk, Scheme* S) {
+  memset(S, 0, sizeof(*S));
+  if (rk != 4) {
+    S->nstages = 3;
+    S->nbuf = 3;
+    S->advance = 1;
+    S->st[0] = {0, 1, 0, -1, -1, 1.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+    S->st[1] = {1, 2, 0, -1, -1, 1.0, 0.75, 0.25, 0.0, 0.0, 1.0};
+    S->st[2] = {2, 1, 0, -1, -1, 1.0, 1.0 / 3.0, 2.0 / 3.0, 0.0, 0.0, 0.5};
+    return;
+  }
+  const double a[4] = {0.0, 0.444370493651235, 0.620101851488403, 0.178079954393132};
+  const double b[4] = {1.0, 0.555629506348765, 0.379898148511597, 0.821920045606868};
+  const double g[4] = {0.391752226571890, 0.368410593050371, 0.251891774271694,
+                       0.544974750228521};
+  const double e2 = 0.517231671970585, e3 = 0.096059710526147, e4 = 0.386708617503269;
+  const double f4 = 0.226007483236906;
+  S->nstages = 5;
+  S->nbuf = 5;
+  S->advance = 0;
+  double c = 0.0;  // time of U^(s) over Dt
+  const int in[4] = {0, 1, 2, 3}, out[4] = {1, 2, 3, 1};
+  for (int s = 0; s < 4; ++s) {
+    S->st[s] = {in[s], out[s], 0, -1, -1, g[s] / b[s], a[s], b[s], 0.0, 0.0, c};
+    c = b[s] * c + g[s];
+  }
+  S->st[3].w = 2;
+  S->st[3].out2 = 4;
+  S->st[3].wa = e2;
+  S->st[3].wb = e3;
+  S->st[4] = {1, 0, 4, -1, -1, f4 / e4, 1.0, e4, 0.0, 0.0, c};
+}
+
+// buffer holding slot `slot` of the scheme in rotation `rot`
+int buf_of(gpmood_t h, int rot, int slot) { return (rot + slot) % h->sch.nbuf; }
+
 template <class Real>
-StageArgs<Real> stage_args(gpmood_t h, int s, int ia, int ix, int io) {
+StageArgs<Real> stage_args(gpmood_t h, int s, int rot) {
   StageArgs<Real> A;
+  const StageSpec& p = h->sch.st[s];
+  const int ix = buf_of(h, rot, p.in), io = buf_of(h, rot, p.out), ia = buf_of(h, rot, p.u0);
   const size_t nc = (size_t)h->g.nx * h->g.ny;
+  A.h = p.h;
+  A.ca = p.ca;
+  A.cb = p.cb;
+  A.W = p.w >= 0 ? h->U[buf_of(h, rot, p.w)] : nullptr;
+  A.out2 = p.out2 >= 0 ? h->U[buf_of(h, rot, p.out2)] : nullptr;
+  A.wa = p.wa;
+  A.wb = p.wb;
   A.X = h->U[ix];
   A.U0 = h->U[ia];
   A.out = h->U[io];
@@ -167,9 +222,9 @@ int push_control(gpmood_t h) {
 
 // kernels launched by one step: dt (2), per stage fill, faces x/y, update,
 // begin (5), 4 per MOOD iteration, finish (1)
-int step_launches(const Scalars& s) {
-  int n = 2 + 3 * 5 + 1;
-  for (int k = 0; k < 3; ++k) n += 4 * s.iters[k];
+int step_launches(const Scalars& s, int nstages) {
+  int n = 2 + nstages * 5 + 1;
+  for (int k = 0; k < nstages; ++k) n += 4 * s.iters[k];
   return n;
 }
 
@@ -192,8 +247,7 @@ MoodArgs mood_args(gpmood_t h) {
 template <class Real>
 int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const ParityW<Real>& P,
                const DirectW<Real>& D, cudaStream_t st) {
-  static const double tfrac[3] = {0.0, 1.0, 0.5};
-  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, tfrac[s], st));
+  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
   CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
   if (h->g.dim == 2) CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
@@ -203,9 +257,9 @@ int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const Parity
 // ---- eager step: the host reads the loop decision after every iteration.
 // Used by gpmood_step_noalloc, which must not build graphs. ----
 template <class Real>
-int eager_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
-                const DirectW<Real>& D) {
-  StageArgs<Real> A = stage_args<Real>(h, s, ia, ix, io);
+int eager_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const DirectW<Real>& D) {
+  StageArgs<Real> A = stage_args<Real>(h, s, rot);
+  const int ix = buf_of(h, rot, h->sch.st[s].in);
   int rc = first_pass<Real>(h, A, ix, s, P, D, h->stream);
   if (rc) return rc;
   CK(launch_mood_begin(h->sc, s, 0, 0, h->stream));
@@ -238,20 +292,19 @@ int copy_interior(gpmood_t h, const double* Xg, double* out) {
 int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
             double* tape = nullptr, uint8_t* otape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
-  const int a = h->cur, b = (a + 1) % 3, c = (a + 2) % 3;
+  const int a = h->cur;
   write_control(h, cfl, fixed_dt, clip, t_end);
   int rc = push_control(h);
   if (rc) return rc;
   CK(launch_dt(h->U[a], h->Uf[a], h->g, h->sc, h->stream));
-  const int in[3] = {a, b, c}, out[3] = {b, c, b};
   const size_t nc = (size_t)h->g.nx * h->g.ny;
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < h->sch.nstages; ++s) {
     if (tape) {
-      rc = copy_interior(h, h->U[in[s]], tape + (size_t)s * 4 * nc);
+      rc = copy_interior(h, h->U[buf_of(h, a, h->sch.st[s].in)], tape + (size_t)s * 4 * nc);
       if (rc) return rc;
     }
-    rc = h->precision == GPMOOD_FP32 ? eager_stage<float>(h, s, a, in[s], out[s], h->pw32, h->dw32)
-                                     : eager_stage<double>(h, s, a, in[s], out[s], h->pw64, h->dw64);
+    rc = h->precision == GPMOOD_FP32 ? eager_stage<float>(h, s, a, h->pw32, h->dw32)
+                                     : eager_stage<double>(h, s, a, h->pw64, h->dw64);
     if (rc) return rc;
     rc = step_error(h);
     if (rc) return rc;
@@ -261,8 +314,8 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
   CK(launch_finish(h->sc, h->stream));
   rc = pull_scalars(h);
   if (rc) return rc;
-  h->launches = step_launches(*h->hsc);
-  h->cur = b;
+  h->launches = step_launches(*h->hsc, h->sch.nstages);
+  h->cur = buf_of(h, a, h->sch.advance);
   h->last_status = GPMOOD_OK;
   return GPMOOD_OK;
 }
@@ -279,17 +332,17 @@ void rec_event(gpmood_t h, int prof, int cls, int open, cudaStream_t st) {
 }
 
 template <class Real>
-int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>& P,
-                  const DirectW<Real>& D, int prof, int record) {
-  static const double tfrac[3] = {0.0, 1.0, 0.5};
+int capture_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const DirectW<Real>& D,
+                  int prof, int record) {
   cudaStream_t st = h->cs;
-  StageArgs<Real> A = stage_args<Real>(h, s, ia, ix, io);
+  StageArgs<Real> A = stage_args<Real>(h, s, rot);
+  const int ix = buf_of(h, rot, h->sch.st[s].in);
   if (record) {
     k_tape_state<<<152 * 4, 256, 0, st>>>(h->U[ix], h->g, h->sc, s);
     CK(cudaGetLastError());
   }
   rec_event(h, prof, GPMOOD_K_GHOST, 1, st);
-  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, tfrac[s], st));
+  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
   rec_event(h, prof, GPMOOD_K_GHOST, 0, st);
   rec_event(h, prof, GPMOOD_K_FACES_X, 1, st);
   CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
@@ -340,8 +393,7 @@ int capture_stage(gpmood_t h, int s, int ia, int ix, int io, const ParityW<Real>
 }
 
 int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out) {
-  const int a = cur, b = (a + 1) % 3, c = (a + 2) % 3;
-  const int in[3] = {a, b, c}, outb[3] = {b, c, b};
+  const int a = cur;
   cudaStream_t st = h->cs;
   h->gev_n = 0;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -349,10 +401,10 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
   rec_event(h, prof, GPMOOD_K_DT, 1, st);
   if (launch_dt(h->U[a], h->Uf[a], h->g, h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
   rec_event(h, prof, GPMOOD_K_DT, 0, st);
-  for (int s = 0; s < 3 && !rc; ++s)
+  for (int s = 0; s < h->sch.nstages && !rc; ++s)
     rc = h->precision == GPMOOD_FP32
-             ? capture_stage<float>(h, s, a, in[s], outb[s], h->pw32, h->dw32, prof, record)
-             : capture_stage<double>(h, s, a, in[s], outb[s], h->pw64, h->dw64, prof, record);
+             ? capture_stage<float>(h, s, a, h->pw32, h->dw32, prof, record)
+             : capture_stage<double>(h, s, a, h->pw64, h->dw64, prof, record);
   if (!rc && launch_finish(h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -389,17 +441,18 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
         h->prof_ms[h->gev_cls[k]] += ms;
     }
     const Scalars& s = *h->hsc;
+    const int S = h->sch.nstages;
     h->prof_n[GPMOOD_K_DT] += 3;
-    h->prof_n[GPMOOD_K_GHOST] += 3;
-    h->prof_n[GPMOOD_K_FACES_X] += 3;
-    h->prof_n[GPMOOD_K_FACES_Y] += 3;
-    h->prof_n[GPMOOD_K_UPDATE] += 6;
-    h->prof_n[GPMOOD_K_MOOD] += 4 * (s.iters[0] + s.iters[1] + s.iters[2]);
+    h->prof_n[GPMOOD_K_GHOST] += S;
+    h->prof_n[GPMOOD_K_FACES_X] += S;
+    h->prof_n[GPMOOD_K_FACES_Y] += h->g.dim == 2 ? S : 0;
+    h->prof_n[GPMOOD_K_UPDATE] += 2 * S;
+    for (int k = 0; k < S; ++k) h->prof_n[GPMOOD_K_MOOD] += 4 * s.iters[k];
   }
   rc = step_error(h);
   if (rc) return rc;
-  h->launches = step_launches(*h->hsc);
-  h->cur = (h->cur + 1) % 3;
+  h->launches = step_launches(*h->hsc, h->sch.nstages);
+  h->cur = buf_of(h, h->cur, h->sch.advance);
   h->last_status = GPMOOD_OK;
   return GPMOOD_OK;
 }
@@ -508,10 +561,13 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   if ((grid->bc[0] == 0) != (grid->bc[1] == 0)) return GPMOOD_E_INVAL;
   if (!one_d && (grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
+  if (o.rk != 0 && o.rk != 3 && o.rk != 4) return GPMOOD_E_INVAL;
 
   gpmood_t h = new (std::nothrow) gpmood_s;
   if (!h) return GPMOOD_E_OOM;
   memset(h, 0, sizeof(*h));
+  make_scheme(o.rk, &h->sch);
+  const int S = h->sch.nstages;
   Grid& g = h->g;
   g.nx = grid->nx;
   g.ny = grid->ny;
@@ -586,16 +642,16 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   const size_t ncell = (size_t)g.nx * g.ny;
   const size_t fsz = sizeof(double);  // face fluxes are FP64 on both paths
   bool ok = true;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < h->sch.nbuf; ++k)
     ok = ok && cudaMalloc(&h->U[k], sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess;
   if (h->precision == GPMOOD_FP32)
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < h->sch.nbuf; ++k)
       ok = ok && cudaMalloc(&h->Uf[k], sizeof(float) * 4 * (size_t)g.vstride) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Fx, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Fy, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess;
   ok = ok && cudaMalloc(&h->cad, ncell) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->ord, 3 * ncell) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->first, 3 * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ord, S * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->first, S * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stamp, sizeof(uint32_t) * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->queue[0], sizeof(int) * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->queue[1], sizeof(int) * ncell) == cudaSuccess;
@@ -611,9 +667,9 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   ok = cudaMemset(h->Fx, 0, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess &&
        cudaMemset(h->Fy, 0, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess &&
        cudaMemset(h->cad, 0, ncell) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
-       cudaMemset(h->ord, 0, 3 * ncell) == cudaSuccess &&
-       cudaMemset(h->first, 0, 3 * ncell) == cudaSuccess;
-  for (int k = 0; k < 3 && ok; ++k)
+       cudaMemset(h->ord, 0, S * ncell) == cudaSuccess &&
+       cudaMemset(h->first, 0, S * ncell) == cudaSuccess;
+  for (int k = 0; k < h->sch.nbuf && ok; ++k)
     ok = cudaMemset(h->U[k], 0, sizeof(double) * 4 * (size_t)g.vstride) == cudaSuccess &&
          (!h->Uf[k] || cudaMemset(h->Uf[k], 0, sizeof(float) * 4 * (size_t)g.vstride) ==
                            cudaSuccess);
@@ -725,8 +781,9 @@ int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out) {
 int gpmood_flags(gpmood_t h, uint8_t* order_out, uint8_t* first_out, gpmood_stats* stats_out) {
   if (!h) return GPMOOD_E_INVAL;
   const size_t nc = (size_t)h->g.nx * h->g.ny;
-  if (order_out) CK(cudaMemcpyAsync(order_out, h->ord, 3 * nc, cudaMemcpyDeviceToHost, h->stream));
-  if (first_out) CK(cudaMemcpyAsync(first_out, h->first, 3 * nc, cudaMemcpyDeviceToHost, h->stream));
+  const size_t S = (size_t)h->sch.nstages;
+  if (order_out) CK(cudaMemcpyAsync(order_out, h->ord, S * nc, cudaMemcpyDeviceToHost, h->stream));
+  if (first_out) CK(cudaMemcpyAsync(first_out, h->first, S * nc, cudaMemcpyDeviceToHost, h->stream));
   int rc = pull_scalars(h);
   if (rc) return rc;
   if (stats_out) {
@@ -734,7 +791,7 @@ int gpmood_flags(gpmood_t h, uint8_t* order_out, uint8_t* first_out, gpmood_stat
     stats_out->t = s.t;
     stats_out->dt = s.dt;
     stats_out->nsteps = s.nsteps;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 5; ++k) {
       stats_out->iters[k] = s.iters[k];
       stats_out->nbad_first[k] = s.nbad_first[k];
       stats_out->nbad_total[k] = s.nbad_total[k];
@@ -784,6 +841,7 @@ int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
 int gpmood_step_record(gpmood_t h, double cfl, double dt_fixed, double* tape, uint8_t* otape,
                        double* dt_out) {
   if (!h || !tape || !otape || (!(cfl > 0.0) && !(dt_fixed > 0.0))) return GPMOOD_E_INVAL;
+  if (h->sch.nstages != 3) return GPMOOD_E_INVAL;  // the adjoint follows SSP-RK3
   int rc = graph_step(h, cfl > 0.0 ? cfl : 1.0, dt_fixed > 0.0 ? dt_fixed : 0.0, 0, 0.0, tape,
                       otape);
   if (rc) return rc;
@@ -797,17 +855,16 @@ namespace {
 
 template <class Real>
 int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>& D) {
-  const int a = h->cur, b = (a + 1) % 3, c = (a + 2) % 3;
+  const int a = h->cur;
   write_control(h, 1.0, dt, 0, 0.0);
   int rc = push_control(h);
   if (rc) return rc;
   CK(launch_dt(h->U[a], h->Uf[a], h->g, h->sc, h->stream));
-  const int in[3] = {a, b, c}, out[3] = {b, c, b};
   const size_t nc = (size_t)h->g.nx * h->g.ny;
-  static const double tfrac[3] = {0.0, 1.0, 0.5};
-  for (int s = 0; s < 3; ++s) {
-    CK(launch_fill(h->U[in[s]], h->Uf[in[s]], h->g, h->sc, tfrac[s], h->stream));
-    StageArgs<Real> A = stage_args<Real>(h, s, a, in[s], out[s]);
+  for (int s = 0; s < h->sch.nstages; ++s) {
+    const int ix = buf_of(h, a, h->sch.st[s].in);
+    CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, h->stream));
+    StageArgs<Real> A = stage_args<Real>(h, s, a);
     CK(cudaMemcpyAsync(A.ord, otape + s * nc, nc, cudaMemcpyDeviceToDevice, h->stream));
     CK(LaunchA<Real>::frozen_stage(A, h->g, D, h->stream));
   }
@@ -815,7 +872,7 @@ int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>
   rc = pull_scalars(h);
   if (rc) return rc;
   if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
-  h->cur = b;
+  h->cur = buf_of(h, a, h->sch.advance);
   return GPMOOD_OK;
 }
 
@@ -901,7 +958,7 @@ int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt
 extern "C" {
 
 int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
-  if (!h || !otape || !(dt > 0.0) || h->g.dim != 2) return GPMOOD_E_INVAL;
+  if (!h || !otape || !(dt > 0.0) || h->g.dim != 2 || h->sch.nstages != 3) return GPMOOD_E_INVAL;
   if (!h->has_state) return GPMOOD_E_NOSTATE;
   return h->precision == GPMOOD_FP32 ? frozen_step<float>(h, otape, dt, h->dw32)
                                      : frozen_step<double>(h, otape, dt, h->dw64);
@@ -909,7 +966,8 @@ int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
 
 int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
                         const double* lam_in, double* lam_out) {
-  if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0) || h->g.dim != 2)
+  if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0) || h->g.dim != 2 ||
+      h->sch.nstages != 3)
     return GPMOOD_E_INVAL;
   int rc = adj_buffers(h);
   if (rc) return rc;
@@ -986,11 +1044,13 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   if ((grid->bc[0] == 0) != (grid->bc[1] == 0)) return GPMOOD_E_INVAL;
   if ((grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
+  if (o.rk == 4) return GPMOOD_E_INVAL;  // SSP-RK3 only: the scratch holds three states
 
   // the temporary handle lives on the host stack
   gpmood_s hs;
   gpmood_s* h = &hs;
   memset(h, 0, sizeof(*h));
+  make_scheme(3, &h->sch);
   Grid& g = h->g;
   g.nx = grid->nx;
   g.dim = 2;

@@ -193,6 +193,14 @@ int upload_items(const std::vector<Item>& v, Item** out, int* n) {
 template <class Real>
 StageArgs<Real> batch_args(gpmood_batch_t b, int s, int ia, int ix, int io) {
   StageArgs<Real> A;
+  // SSP-RK3 (eq. rk3): the stage combinations as out = ca U0 + cb Y
+  static const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  A.h = 1.0;
+  A.ca = ca[s];
+  A.cb = cb[s];
+  A.W = nullptr;
+  A.out2 = nullptr;
+  A.wa = A.wb = 0.0;
   A.X = b->U[ix];
   A.U0 = b->U[ia];
   A.out = b->U[io];
@@ -498,6 +506,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
       if (!(cascade[k] > cascade[k + 1])) return GPMOOD_E_INVAL;
   }
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
+  if (o.rk != 0 && o.rk != 3) return GPMOOD_E_INVAL;  // batches step with SSP-RK3
   const int H = R_max + 1 > 2 ? R_max + 1 : 2;
   const int minn = H > 3 ? H : 3;
   // every problem shares the weights: the same ell/dx and ell/dy

@@ -51,7 +51,7 @@ struct Scalars {
   int slot;                     // queue holding the cells to work on
   int go;                       // MOOD loop continues (mirrors the graph condition)
   unsigned int stamp_cur;       // stamp of the cells in the current queue
-  int iters[3], nbad_first[3], nbad_total[3], nfog_pad[3];
+  int iters[5], nbad_first[5], nbad_total[5], nfog_pad[5];  // per RK stage
   long long nsteps;
   int nactive;                  // batches: problems still advancing in this step
 };
@@ -92,6 +92,19 @@ struct Detect {
   double delta;         // min(dx, dy)
 };
 
+// one RK stage as buffer roles (slots relative to the step's rotation of
+// the state buffers) and the coefficients of StageArgs; w, out2 = -1: none
+struct StageSpec {
+  int in, out, u0, w, out2;
+  double h, ca, cb, wa, wb;
+  double tfrac;  // time of the stage input as a fraction of dt
+};
+
+struct Scheme {
+  int nstages, nbuf, advance;  // stages, state buffers, rotation per step
+  StageSpec st[5];
+};
+
 template <class Real>
 struct StageArgs {
   const double* X;   // ghosted stage input
@@ -109,6 +122,13 @@ struct StageArgs {
   const Scalars* sc;
   Scalars* scw;
   int stage;
+  // the RK stage as a forward-Euler sub-step and a combination (eqs. rk3,
+  // rk4): candidate Y = X - h dt F(X); out = ca U0 + cb Y (ca = 0: U0 unread);
+  // with out2 set, also out2 = wa W + wb Y
+  double h, ca, cb;
+  const double* W;
+  double* out2;
+  double wa, wb;
 };
 
 // the two queues alternate: sc->slot names the one holding the cells of the

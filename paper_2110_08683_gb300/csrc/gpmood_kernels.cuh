@@ -663,7 +663,7 @@ __device__ __forceinline__ void candidate(const StageArgs<Real>& A, const Grid& 
   for (int v = 0; v < 4; ++v) {
     double fe = A.Fx[fxidx(g, v, i + 1, j)], fw = A.Fx[fxidx(g, v, i, j)];
     double gn = A.Fy[fyidx(g, v, i, j + 1)], gs = A.Fy[fyidx(g, v, i, j)];
-    Y[v] = A.X[gidx(g, v, i, j)] - dt * ((fe - fw) * g.inv_dx + (gn - gs) * g.inv_dy);
+    Y[v] = A.X[gidx(g, v, i, j)] - (A.h * dt) * ((fe - fw) * g.inv_dx + (gn - gs) * g.inv_dy);
   }
 }
 
@@ -673,12 +673,10 @@ __device__ __forceinline__ void combine_store(const StageArgs<Real>& A, const Gr
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     long long k = gidx(g, v, i, j);
-    double o;
-    if (A.stage == 0) o = Y[v];
-    else if (A.stage == 1) o = 0.25 * (3.0 * A.U0[k] + Y[v]);
-    else o = (A.U0[k] + 2.0 * Y[v]) * (1.0 / 3.0);
+    const double o = A.ca != 0.0 ? fma(A.ca, A.U0[k], A.cb * Y[v]) : A.cb * Y[v];
     A.out[k] = o;
     if constexpr (sizeof(Real) == sizeof(float)) A.outr[k] = (float)o;
+    if (A.out2) A.out2[k] = fma(A.wa, A.W[k], A.wb * Y[v]);
   }
 }
 
@@ -1051,6 +1049,8 @@ __device__ __forceinline__ StageArgs<Real> problem_args(const StageArgs<Real>& B
   A.U0 = B.U0 + P.state_off;
   A.out = B.out + P.state_off;
   A.outr = B.outr ? B.outr + P.state_off : nullptr;
+  A.W = B.W ? B.W + P.state_off : nullptr;
+  A.out2 = B.out2 ? B.out2 + P.state_off : nullptr;
   A.Fx = B.Fx + P.fx_off;
   A.Fy = B.Fy + P.fy_off;
   A.cad = B.cad + P.cell_off;

@@ -291,3 +291,58 @@ def test_sod_1d_rejected_where_unsupported():
     dt = g.step_record(tape.data_ptr(), otape.data_ptr())
     with pytest.raises(gp.GpmoodError):
         g.step_frozen(otape.data_ptr(), dt)
+
+
+@pytest.mark.parametrize("case", ["vortex", "quadrants", "dmr"])
+def test_rk4_steps_against_oracle(case):
+    """SSP-RK4 (eq. rk4): five MOOD stages per step against the oracle:
+    <= 1e-12 relative on the smooth vortex, identical first-pass flags, final
+    radii and iteration counts of every stage on the shock problems."""
+    if case == "vortex":
+        p = I.vortex(n=40, lo=0.0, hi=20.0, R=3, ell=1.0, cascade=[3, 1, 0])
+    elif case == "quadrants":
+        p = I.quadrants(n=48, ny=40, R=3, seed=7)
+    else:
+        p = I.dmr(nx=96, ny=24, R=3)
+    p["rk"] = 4
+    res = _first_step_flags(p, nsteps=3)
+    for Ug, Uo, og, oo, bg, bo, sg, so in res:
+        assert og.shape == (5, p["ny"], p["nx"])
+        assert (bg == bo).all() and (og == oo).all()
+        assert sg["iters"] == so["iters"] and len(sg["iters"]) == 5
+        assert relerr(Ug, Uo) <= (1e-12 if case == "vortex" else 1e-11)
+    if case != "vortex":
+        assert sum(sum(r[7]["nbad_first"]) for r in res) > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rk4_eager_equals_graph_and_conserves(precision):
+    p = I.quadrants(n=48, ny=40, R=3, seed=1)
+    p["bc"] = ["periodic"] * 4
+    p["rk"] = 4
+    out = []
+    for eager in (False, True):
+        g = gp.GPMood(p, precision, eager=eager)
+        g.set_state(p["U0"])
+        for _ in range(4):
+            g.step()
+        out.append((g.get_state(), g.flags()[2]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["iters"] == out[1][1]["iters"]
+    U0 = p["U0"]
+    for v in range(4):
+        assert abs(out[0][0][v].sum() - U0[v].sum()) <= 1e-13 * np.abs(U0[v]).sum()
+
+
+def test_rk4_rejected_by_the_adjoint_batch_and_noalloc():
+    p = I.quadrants(n=40, R=3, seed=1)
+    p["rk"] = 4
+    with pytest.raises(gp.GpmoodError):
+        gp.GPMoodBatch([p, p])
+    g = gp.GPMood(p)
+    g.set_state(p["U0"])
+    torch = pytest.importorskip("torch")
+    tape = torch.empty((3, 4, 40, 40), dtype=torch.float64, device="cuda")
+    otape = torch.empty((3, 40, 40), dtype=torch.uint8, device="cuda")
+    with pytest.raises(gp.GpmoodError):
+        g.step_record(tape.data_ptr(), otape.data_ptr())
