@@ -43,7 +43,9 @@ enum {
   GPMOOD_BC_REFLECT = 2,    /* mirror, normal momentum negated */
   GPMOOD_BC_DIRICHLET = 3,  /* fixed primitive state bc_prim[side] */
   GPMOOD_BC_DMR_BOTTOM = 4, /* S only: x < dmr_wall_x0 -> dmr_post, else reflect */
-  GPMOOD_BC_DMR_TOP = 5     /* N only: x < dmr_xs0 + dmr_xs_speed t -> dmr_post, else dmr_pre */
+  GPMOOD_BC_DMR_TOP = 5,    /* N only: x < dmr_xs0 + dmr_xs_speed t -> dmr_post, else dmr_pre */
+  GPMOOD_BC_JET = 6         /* S or N: jet_prim[side] for ghost-cell centres with
+                               jet_x0 <= x <= jet_x1, outflow elsewhere (Sec. 5.3, the Mach jets) */
 };
 
 enum { GPMOOD_FP64 = 0, GPMOOD_FP32 = 1 };
@@ -68,6 +70,8 @@ typedef struct {
   double bc_prim[4][4];       /* (rho, u, v, p) for DIRICHLET sides */
   double dmr_post[4], dmr_pre[4];            /* primitive states for the DMR kinds */
   double dmr_wall_x0, dmr_xs0, dmr_xs_speed; /* DMR wall start and shock line x_s(t) */
+  double jet_x0, jet_x1;      /* inflow slit of GPMOOD_BC_JET */
+  double jet_prim[2][4];      /* jet (rho, u, v, p) on the S and N sides */
   int dim;                    /* 0 or 2: two-dimensional.  1: one-dimensional (ny = 1; y0, y1
                                  and the S/N boundaries are ignored): the stencil a = -R..R,
                                  one point per face, x faces only, detection and the time
@@ -84,6 +88,9 @@ typedef struct {
   double sigma_p;       /* CSD threshold on the normalised |grad p| (0 -> 5) */
   int csd_off;          /* 1 disables CSD (Step 6) */
   int max_mood_iters;   /* cap on MOOD iterations per RK stage (0 -> 64 + 4 max(nx, ny)) */
+  int riemann;          /* 0: HLLC (Toro et al. 1994, the default); 1: HLL (Harten, Lax, van
+                           Leer 1983, the paper's choice for the Mach jets); the same wave
+                           speeds.  The adjoint requires HLLC */
   int rk;               /* 0 or 3: SSP-RK3 (eq. rk3).  4: the five-stage SSP-RK4 (eq. rk4), its
                            Dt F(U^(3)) term of the final combination read with a minus
                            sign; each stage's MOOD candidate is its forward-Euler

@@ -15,7 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "gpmood_oracle.c")
 LIB = os.path.join(HERE, "_build", "libgpmood_oracle.so")
 
-BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5}
+BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5,
+      "jet": 6}
+RIEMANN = {"hllc": 0, "hll": 1}
 ACCEPT_CSD, ACCEPT_PLATEAU, ACCEPT_DMP, ACCEPT_U2 = 1, 2, 3, 4
 FAIL_CAD, FAIL_PAD, FAIL_U2 = -1, -2, -3
 
@@ -43,7 +45,8 @@ class Config(C.Structure):
         ("max_iters", C.c_int),
         ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4),
         ("dmr_wall_x0", C.c_double), ("dmr_xs0", C.c_double), ("dmr_xs_speed", C.c_double),
-        ("rk", C.c_int),
+        ("rk", C.c_int), ("riemann", C.c_int), ("jet_x0", C.c_double), ("jet_x1", C.c_double),
+        ("jet_prim", (C.c_double * 4) * 2),
     ]
 
 
@@ -82,6 +85,8 @@ def lib():
         L.orc_fill_ghosts.argtypes = [p, p, d, p]
         L.orc_hllc.argtypes = [p, p, d, i, p]
         L.orc_hllc.restype = None
+        L.orc_hll.argtypes = [p, p, d, i, p]
+        L.orc_hll.restype = None
         _lib_handle = L
     return _lib_handle
 
@@ -145,6 +150,14 @@ def hllc(UL, UR, gamma=1.4, direction=0):
     return F
 
 
+def hll(UL, UR, gamma=1.4, direction=0):
+    UL = np.ascontiguousarray(UL, dtype=np.float64)
+    UR = np.ascontiguousarray(UR, dtype=np.float64)
+    F = np.zeros(4)
+    lib().orc_hll(_ptr(UL), _ptr(UR), gamma, direction, _ptr(F))
+    return F
+
+
 def make_config(prob):
     cfg = Config()
     cfg.dim = int(prob.get("dim", 2))
@@ -170,6 +183,11 @@ def make_config(prob):
     cfg.dmr_xs0 = prob["dmr_xs0"]
     cfg.dmr_xs_speed = prob["dmr_xs_speed"]
     cfg.rk = int(prob.get("rk", 3))
+    cfg.riemann = RIEMANN[prob.get("riemann", "hllc")]
+    cfg.jet_x0, cfg.jet_x1 = prob.get("jet_x", (0.0, 0.0))
+    for side, P in enumerate(prob.get("jet_prim", ([1.0, 0.0, 0.0, 1.0],) * 2)):
+        for k in range(4):
+            cfg.jet_prim[side][k] = P[k]
     return cfg
 
 

@@ -298,6 +298,7 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
   if (cfg->nx < 1 || cfg->ny < 1 || (cfg->dim == 1 && cfg->ny != 1)) return -1;
   if (cfg->ncascade < 1 || cfg->ncascade > 4) return -1;
   if (cfg->rk != 0 && cfg->rk != 3 && cfg->rk != 4) return -1;
+  if (cfg->riemann != 0 && cfg->riemann != 1) return -1;
   if (cfg->cascade[cfg->ncascade - 1] != 0) return -1;
   for (int k = 0; k + 1 < cfg->ncascade; ++k)
     if (!(cfg->cascade[k] > cfg->cascade[k + 1])) return -1;
@@ -308,7 +309,8 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
   c->H = c->top + 1 > 2 ? c->top + 1 : 2;
   for (int s = 0; s < 4; ++s) {
     int k = cfg->bc[s];
-    if (k < 0 || k > 5) { free(c); return -1; }
+    if (k < 0 || k > 6) { free(c); return -1; }
+    if (k == ORC_BC_JET && s < 2) { free(c); return -1; }
     if (k == ORC_BC_DMR_BOTTOM && s != 2) { free(c); return -1; }
     if (k == ORC_BC_DMR_TOP && s != 3) { free(c); return -1; }
     if ((cfg->bc[0] == ORC_BC_PERIODIC) != (cfg->bc[1] == ORC_BC_PERIODIC)) { free(c); return -1; }
@@ -403,7 +405,11 @@ static void hllc_x(const double* UL, const double* UR, double gam, double* F) {
   double Ss = num / den;
   double FL[4] = {rL * uL, rL * uL * uL + pL, rL * uL * vL, uL * (EL + pL)};
   double FR[4] = {rR * uR, rR * uR * uR + pR, rR * uR * vR, uR * (ER + pR)};
-  if (SL >= 0.0) {
+  if (!(rL > 0.0 && rR > 0.0 && pL > 0.0 && pR > 0.0)) {
+    /* a state outside the solver's domain (c^2 = gamma p / rho <= 0 or NaN):
+       the flux is undefined */
+    for (int v = 0; v < 4; ++v) F[v] = NAN;
+  } else if (SL >= 0.0) {
     for (int v = 0; v < 4; ++v) F[v] = FL[v];
   } else if (Ss >= 0.0) {
     double f = rL * (SL - uL) / (SL - Ss);
@@ -421,6 +427,40 @@ static void hllc_x(const double* UL, const double* UR, double gam, double* F) {
 void orc_hllc(const double* UL, const double* UR, double gam, int dir, double* F) {
   if (dir == 0) hllc_x(UL, UR, gam, F);
   else hllc_y(UL, UR, gam, F);
+}
+
+/* HLL approximate Riemann solver in the x direction (Harten, Lax and van
+   Leer 1983): the single intermediate state between S_L and S_R, with the
+   wave speeds of hllc_x */
+static void hll_x(const double* UL, const double* UR, double gam, double* F) {
+  double rL = UL[0], uL = UL[1] / rL, vL = UL[2] / rL, EL = UL[3];
+  double rR = UR[0], uR = UR[1] / rR, vR = UR[2] / rR, ER = UR[3];
+  double pL = pressure(UL, gam), pR = pressure(UR, gam);
+  double cL = sqrt(gam * pL / rL), cR = sqrt(gam * pR / rR);
+  double SL = dmin2(uL - cL, uR - cR);
+  double SR = dmax2(uL + cL, uR + cR);
+  double FL[4] = {rL * uL, rL * uL * uL + pL, rL * uL * vL, uL * (EL + pL)};
+  double FR[4] = {rR * uR, rR * uR * uR + pR, rR * uR * vR, uR * (ER + pR)};
+  int dom = rL > 0.0 && rR > 0.0 && pL > 0.0 && pR > 0.0; /* else: flux undefined */
+  for (int v = 0; v < 4; ++v) {
+    if (!dom) F[v] = NAN;
+    else if (SL >= 0.0) F[v] = FL[v];
+    else if (SR > 0.0) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+    else F[v] = FR[v];
+  }
+}
+
+static void hll_y(const double* UL, const double* UR, double gam, double* G) {
+  double L[4] = {UL[0], UL[2], UL[1], UL[3]};
+  double R[4] = {UR[0], UR[2], UR[1], UR[3]};
+  double f[4];
+  hll_x(L, R, gam, f);
+  G[0] = f[0]; G[1] = f[2]; G[2] = f[1]; G[3] = f[3];
+}
+
+void orc_hll(const double* UL, const double* UR, double gam, int dir, double* F) {
+  if (dir == 0) hll_x(UL, UR, gam, F);
+  else hll_y(UL, UR, gam, F);
 }
 
 /* y-direction flux G by rotating (rho, rho v, rho u, E) through hllc_x */
@@ -482,6 +522,9 @@ int orc_fill_ghosts(orc_ctx* c, const double* U, double t, double* Xg) {
           } else if (kind == ORC_BC_DMR_TOP) {
             fixed = 1;
             P = (xc < cf->dmr_xs0 + cf->dmr_xs_speed * t) ? cf->dmr_post : cf->dmr_pre;
+          } else if (kind == ORC_BC_JET) {
+            /* jet_prim inside the slit, outflow elsewhere */
+            if (xc >= cf->jet_x0 && xc <= cf->jet_x1) { fixed = 1; P = cf->jet_prim[side]; }
           } else if (kind == ORC_BC_REFLECT) reflect = 1;
           if (fixed) {
             prim_to_cons(P, gam, S);
@@ -539,9 +582,13 @@ static void mark_cad(orc_ctx* c, int i, int j) {
   c->cad[(size_t)j * cf->nx + i] = 1;
 }
 
+/* face-state check (Sec. 3.3.1, read with the Riemann solver's domain): a
+   reconstructed state is admissible when its density and pressure are
+   finite and positive -- the solver takes c = sqrt(gamma p / rho), which a
+   non-positive p or rho leaves undefined */
 static int finite_state(const double* U, double gam) {
   double p = pressure(U, gam);
-  return isfinite(U[0]) && isfinite(p);
+  return isfinite(U[0]) && isfinite(p) && U[0] > 0.0 && p > 0.0;
 }
 
 /* reconstruct the pointwise state of cell (i,j) at Gauss point gi of face f
@@ -575,7 +622,8 @@ static void face_flux_x(orc_ctx* c, const double* Xg, const uint8_t* ord, int i,
     reconstruct(c, Xg, R, 1, gi, i, j, UR);     /* west face of the right cell */
     if (!finite_state(UL, c->cfg.gamma)) mark_cad(c, i - 1, j);
     if (!finite_state(UR, c->cfg.gamma)) mark_cad(c, i, j);
-    hllc_x(UL, UR, c->cfg.gamma, f);
+    if (c->cfg.riemann == 1) hll_x(UL, UR, c->cfg.gamma, f);
+    else hllc_x(UL, UR, c->cfg.gamma, f);
     for (int v = 0; v < NV; ++v) F[v] += c->gw[q][gi] * f[v];
   }
   int nx = c->cfg.nx, ny = c->cfg.ny;
@@ -595,7 +643,8 @@ static void face_flux_y(orc_ctx* c, const double* Xg, const uint8_t* ord, int i,
     reconstruct(c, Xg, R, 3, gi, i, j, UR);     /* south face of the upper cell */
     if (!finite_state(UL, c->cfg.gamma)) mark_cad(c, i, j - 1);
     if (!finite_state(UR, c->cfg.gamma)) mark_cad(c, i, j);
-    hllc_y(UL, UR, c->cfg.gamma, f);
+    if (c->cfg.riemann == 1) hll_y(UL, UR, c->cfg.gamma, f);
+    else hllc_y(UL, UR, c->cfg.gamma, f);
     for (int v = 0; v < NV; ++v) G[v] += c->gw[q][gi] * f[v];
   }
   int nx = c->cfg.nx;
@@ -865,6 +914,18 @@ double orc_dt(orc_ctx* c, const double* U, double cfl) {
       if (!(a > 0.0) || !isfinite(a)) return NAN; /* no admissible step */
       best = dmin2(best, a);
     }
+  /* the inflow state of a jet boundary enters the domain at the first step:
+     its bound counts too (the quiescent ambient alone would give the jet a
+     Courant number in the hundreds) */
+  for (int side = 0; side < 2; ++side) {
+    if (c->cfg.bc[2 + side] != ORC_BC_JET) continue;
+    double S[4];
+    prim_to_cons(c->cfg.jet_prim[side], gam, S);
+    double u = S[1] / S[0], v = S[2] / S[0];
+    double cs = sqrt(gam * pressure(S, gam) / S[0]);
+    double a = dmin2(c->dx / (fabs(u) + cs), c->dy / (fabs(v) + cs));
+    best = dmin2(best, a);
+  }
   return cfl * best;
 }
 

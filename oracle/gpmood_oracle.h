@@ -34,7 +34,9 @@ enum {
   ORC_BC_REFLECT = 2,    /* mirror, normal momentum negated */
   ORC_BC_DIRICHLET = 3,  /* fixed primitive state bc_prim[side] */
   ORC_BC_DMR_BOTTOM = 4, /* S side: x < wall_x0 -> state post, else reflect */
-  ORC_BC_DMR_TOP = 5     /* N side: x < xs0 + xs_speed*t -> post, else pre */
+  ORC_BC_DMR_TOP = 5,    /* N side: x < xs0 + xs_speed*t -> post, else pre */
+  ORC_BC_JET = 6         /* S or N side: jet_prim inside jet_x0 <= x <= jet_x1 (cell
+                            centres), outflow elsewhere (Sec. 5.3, the Mach jets) */
 };
 
 /* detection outcome codes for a single cell (Steps 4-9 of Sec. 4) */
@@ -65,6 +67,9 @@ typedef struct {
   double dmr_post[4], dmr_pre[4];
   double dmr_wall_x0, dmr_xs0, dmr_xs_speed;
   int rk;                /* 3 (or 0): SSP-RK3, eq. rk3; 4: five-stage SSP-RK4, eq. rk4 */
+  int riemann;           /* 0: HLLC (Toro et al. 1994); 1: HLL (Harten, Lax, van Leer 1983) */
+  double jet_x0, jet_x1; /* inflow slit of the JET kind */
+  double jet_prim[2][4]; /* jet state (rho, u, v, p) on the S and N sides */
 } orc_config;
 
 typedef struct orc_ctx orc_ctx;
@@ -100,6 +105,8 @@ int orc_d2_weights(int dim, double ell, double dx, double dy, double* wxx, doubl
 /* --- scheme --- */
 /* HLLC flux between pointwise states UL, UR across an x (dir 0) or y (dir 1) face */
 void orc_hllc(const double* UL, const double* UR, double gamma, int dir, double* F);
+/* HLL flux with the same wave speeds */
+void orc_hll(const double* UL, const double* UR, double gamma, int dir, double* F);
 /* F_nabla (eq. fvm_F) of the interior state U at per-cell radii ord (EDP1 faces) */
 int orc_residual(orc_ctx* ctx, const double* U, const uint8_t* ord, double t, double* Fn);
 /* Delta t from U (per-direction CFL form) */

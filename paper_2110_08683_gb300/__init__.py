@@ -17,7 +17,9 @@ import numpy as np
 
 from . import build as _build
 
-BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5}
+BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5,
+      "jet": 6}
+RIEMANN = {"hllc": 0, "hll": 1}
 FP64, FP32 = 0, 1
 
 E_CODES = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "device allocation failed",
@@ -39,6 +41,7 @@ class Grid(C.Structure):
         ("bc", C.c_int * 4), ("bc_prim", (C.c_double * 4) * 4),
         ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4),
         ("dmr_wall_x0", C.c_double), ("dmr_xs0", C.c_double), ("dmr_xs_speed", C.c_double),
+        ("jet_x0", C.c_double), ("jet_x1", C.c_double), ("jet_prim", (C.c_double * 4) * 2),
         ("dim", C.c_int),
     ]
 
@@ -47,7 +50,8 @@ class Options(C.Structure):
     _fields_ = [
         ("ncascade", C.c_int), ("cascade", C.c_int * 4), ("precision", C.c_int),
         ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
-        ("max_mood_iters", C.c_int), ("rk", C.c_int), ("eager", C.c_int),
+        ("max_mood_iters", C.c_int), ("riemann", C.c_int), ("rk", C.c_int),
+        ("eager", C.c_int),
     ]
 
 
@@ -135,6 +139,10 @@ def make_grid(prob):
     g.dmr_wall_x0 = prob["dmr_wall_x0"]
     g.dmr_xs0 = prob["dmr_xs0"]
     g.dmr_xs_speed = prob["dmr_xs_speed"]
+    g.jet_x0, g.jet_x1 = prob.get("jet_x", (0.0, 0.0))
+    for side, P in enumerate(prob.get("jet_prim", ([1.0, 0.0, 0.0, 1.0],) * 2)):
+        for k in range(4):
+            g.jet_prim[side][k] = P[k]
     g.dim = int(prob.get("dim", 2))
     return g
 
@@ -150,6 +158,7 @@ def make_options(prob, precision=FP64, eager=False):
     o.csd_off = 0 if prob["csd_on"] else 1
     o.max_mood_iters = int(prob.get("max_iters", 0))
     o.rk = int(prob.get("rk", 3))
+    o.riemann = RIEMANN[prob.get("riemann", "hllc")]
     o.eager = 1 if eager else 0
     return o
 

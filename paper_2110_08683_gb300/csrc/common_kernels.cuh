@@ -26,6 +26,8 @@ __global__ void k_dt_reduce(const double* X, const float* Xf, Grid g, Scalars* s
     if (!cell_rate_at(X, Xf, g, i, j, a)) bad = true;
     else best = a > best ? a : best;
   }
+  // the inflow state of a jet boundary enters at the first step: its rate counts
+  if (blockIdx.x == 0 && threadIdx.x == 0 && g.rate_floor > best) best = g.rate_floor;
   for (int o = 16; o > 0; o >>= 1) {
     double ob = __shfl_xor_sync(0xffffffffu, best, o);
     best = ob > best ? ob : best;
@@ -141,6 +143,10 @@ __device__ __forceinline__ bool fold_src_y(const Grid& g, int i, int j, int& sj,
   const int kind = g.bc[2 + side];
   bool reflect = kind == 2;
   if (kind == 3 || kind == 5) return false;
+  if (kind == 6) {  // jet: fixed inside the slit, outflow elsewhere
+    const double xc = g.x0 + (i + 0.5) * g.dx;
+    if (xc >= g.jet_x0 && xc <= g.jet_x1) return false;
+  }
   if (kind == 4) {
     const double xc = g.x0 + (i + 0.5) * g.dx;
     if (xc < g.dmr_wall_x0) return false;

@@ -192,8 +192,9 @@ int gpw_second_derivative(double dx, double dy, double ell, int* da, int* db, do
    its sum.  The result is laid out as a 2D radius-R table so that the same
    kernels apply it: the weight of offset (a, 0) on the row b = 0, zero off
    that row, the same vector at each of the R+1 Gauss-point slots, and Gauss
-   weights (1, 0, ...): every slot yields the same face state and the first
-   alone enters the face average. */
+   weights (1/2, 0, ..., 0, 1/2): every slot yields the same face state, and
+   the first and last slots, a mirror pair of the kernels' pairwise Gauss
+   sum, give exactly that state's flux. */
 int gpw_solve_1d(int R, double dx, double ell, gpw_radius* out) {
   if (R < 1 || R > 3) return -1;
   memset(out, 0, sizeof(*out));
@@ -220,7 +221,7 @@ int gpw_solve_1d(int R, double dx, double ell, gpw_radius* out) {
   gauss_q(q, gq, wq);
   for (int k = 0; k < q; ++k) {
     out->g[k] = (double)gq[k];
-    out->w[k] = k == 0 ? 1.0 : 0.0;
+    out->w[k] = (k == 0 || k == q - 1) ? 0.5 : 0.0; /* q >= 2: a mirror pair of equal weight */
   }
   return 0;
 }

@@ -25,7 +25,7 @@ int gpw_second_derivative(double dx, double dy, double ell, int* da, int* db, do
                           double* wyy);
 /* the one-dimensional GP (stencil a = -R..R, one face point) laid out as a
    2D radius-R table: weights on the row b = 0, the same vector at every
-   Gauss-point slot, Gauss weights (1, 0, ...); north-face weights zero */
+   Gauss-point slot, Gauss weights (1/2, 0, ..., 0, 1/2); north-face weights zero */
 int gpw_solve_1d(int R, double dx, double ell, gpw_radius* out);
 /* the 1D App. B second-derivative weights on the 5-point table (wyy = 0) */
 int gpw_second_derivative_1d(double dx, double ell, int* da, int* db, double* wxx,

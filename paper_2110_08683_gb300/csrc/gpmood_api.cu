@@ -29,7 +29,7 @@ struct gpmood_s {
   float* Uf[5];    // float shadows of U (FP32 path only, else null)
   void* Fx;
   void* Fy;
-  uint8_t* cad;
+  uint8_t* fb;     // face-state check bits: x faces, then y faces
   uint8_t* ord;    // [S][nc], S stages
   uint8_t* first;  // [S][nc]
   uint32_t* stamp;
@@ -66,6 +66,22 @@ struct gpmood_s {
 };
 
 namespace {
+
+// CFL rate max((|u|+c)/dx, (|v|+c)/dy) of the jet inflow states of a grid's
+// jet sides (0 without): those states enter the domain at the first step
+double jet_rate(const Grid& g) {
+  double r = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    if (g.bc[2 + side] != 6) continue;
+    const double* S = g.jetU[side];
+    const double u = S[1] / S[0], v = S[2] / S[0];
+    const double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * u + S[2] * v));
+    const double c = sqrt(g.gamma * p / S[0]);
+    const double ax = (fabs(u) + c) / g.dx, ay = (fabs(v) + c) / g.dy;
+    r = fmax(r, fmax(ax, ay));
+  }
+  return r;
+}
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -104,7 +120,7 @@ void free_all(gpmood_t h) {
   }
   cudaFree(h->Fx);
   cudaFree(h->Fy);
-  cudaFree(h->cad);
+  cudaFree(h->fb);
   cudaFree(h->ord);
   cudaFree(h->first);
   cudaFree(h->stamp);
@@ -184,7 +200,8 @@ StageArgs<Real> stage_args(gpmood_t h, int s, int rot) {
   }
   A.Fx = (double*)h->Fx;
   A.Fy = (double*)h->Fy;
-  A.cad = h->cad;
+  A.fbx = h->fb;
+  A.fby = h->fb + (size_t)(h->g.nx + 1) * h->g.ny;
   A.ord = h->ord + s * nc;
   A.first = h->first + s * nc;
   A.queue = h->queue[0];
@@ -554,7 +571,8 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   if (!(grid->x1 > grid->x0) || (!one_d && !(grid->y1 > grid->y0))) return GPMOOD_E_INVAL;
   for (int s = 0; s < (one_d ? 2 : 4); ++s) {
     int k = grid->bc[s];
-    if (k < 0 || k > 5) return GPMOOD_E_INVAL;
+    if (k < 0 || k > 6) return GPMOOD_E_INVAL;
+    if (k == GPMOOD_BC_JET && s < 2) return GPMOOD_E_INVAL;
     if (k == GPMOOD_BC_DMR_BOTTOM && s != 2) return GPMOOD_E_INVAL;
     if (k == GPMOOD_BC_DMR_TOP && s != 3) return GPMOOD_E_INVAL;
   }
@@ -562,6 +580,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   if (!one_d && (grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
   if (o.rk != 0 && o.rk != 3 && o.rk != 4) return GPMOOD_E_INVAL;
+  if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
 
   gpmood_t h = new (std::nothrow) gpmood_s;
   if (!h) return GPMOOD_E_OOM;
@@ -595,6 +614,12 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   g.dmr_wall_x0 = grid->dmr_wall_x0;
   g.dmr_xs0 = grid->dmr_xs0;
   g.dmr_xs_speed = grid->dmr_xs_speed;
+  g.jet_x0 = grid->jet_x0;
+  g.jet_x1 = grid->jet_x1;
+  prim_to_cons(grid->jet_prim[0], gamma, g.jetU[0]);
+  prim_to_cons(grid->jet_prim[1], gamma, g.jetU[1]);
+  g.riemann = o.riemann;
+  g.rate_floor = jet_rate(g);
 
   for (int r = 0; r < 4; ++r) h->cas.next[r] = h->cas.prev[r] = r;
   for (int k = 0; k + 1 < nc; ++k) {
@@ -649,7 +674,8 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
       ok = ok && cudaMalloc(&h->Uf[k], sizeof(float) * 4 * (size_t)g.vstride) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Fx, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->Fy, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->cad, ncell) == cudaSuccess;
+  const size_t nfb = (size_t)(g.nx + 1) * g.ny + (size_t)g.nx * (g.ny + 1);
+  ok = ok && cudaMalloc(&h->fb, nfb) == cudaSuccess;
   ok = ok && cudaMalloc(&h->ord, S * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->first, S * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->stamp, sizeof(uint32_t) * ncell) == cudaSuccess;
@@ -666,7 +692,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   // the face fluxes start at zero: in 1D the y fluxes stay zero
   ok = cudaMemset(h->Fx, 0, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess &&
        cudaMemset(h->Fy, 0, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess &&
-       cudaMemset(h->cad, 0, ncell) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
+       cudaMemset(h->fb, 0, nfb) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
        cudaMemset(h->ord, 0, S * ncell) == cudaSuccess &&
        cudaMemset(h->first, 0, S * ncell) == cudaSuccess;
   for (int k = 0; k < h->sch.nbuf && ok; ++k)
@@ -967,7 +993,7 @@ int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
 int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
                         const double* lam_in, double* lam_out) {
   if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0) || h->g.dim != 2 ||
-      h->sch.nstages != 3)
+      h->sch.nstages != 3 || h->g.riemann != 0)  // the reverse Riemann solver is HLLC's
     return GPMOOD_E_INVAL;
   int rc = adj_buffers(h);
   if (rc) return rc;
@@ -1037,7 +1063,8 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   if (!(grid->x1 > grid->x0) || !(grid->y1 > grid->y0)) return GPMOOD_E_INVAL;
   for (int s = 0; s < 4; ++s) {
     int k = grid->bc[s];
-    if (k < 0 || k > 5) return GPMOOD_E_INVAL;
+    if (k < 0 || k > 6) return GPMOOD_E_INVAL;
+    if (k == GPMOOD_BC_JET && s < 2) return GPMOOD_E_INVAL;
     if (k == GPMOOD_BC_DMR_BOTTOM && s != 2) return GPMOOD_E_INVAL;
     if (k == GPMOOD_BC_DMR_TOP && s != 3) return GPMOOD_E_INVAL;
   }
@@ -1045,6 +1072,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   if ((grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
   if (o.rk == 4) return GPMOOD_E_INVAL;  // SSP-RK3 only: the scratch holds three states
+  if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
 
   // the temporary handle lives on the host stack
   gpmood_s hs;
@@ -1066,12 +1094,13 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   const size_t sz_state = align256(sizeof(double) * 4 * (size_t)g.vstride);
   const size_t sz_fx = align256(fsz * 4 * (size_t)g.ny * (g.nx + 1));
   const size_t sz_fy = align256(fsz * 4 * (size_t)(g.ny + 1) * g.nx);
-  const size_t sz_c = align256(ncell), sz_c3 = align256(3 * ncell);
+  const size_t nfb = (size_t)(g.nx + 1) * g.ny + (size_t)g.nx * (g.ny + 1);
+  const size_t sz_fb = align256(nfb), sz_c3 = align256(3 * ncell);
   const size_t sz_stamp = align256(sizeof(uint32_t) * ncell), sz_q = align256(sizeof(int) * ncell);
   const size_t sz_sc = align256(sizeof(Scalars));
   const size_t sz_shadow =
       o.precision == GPMOOD_FP32 ? align256(sizeof(float) * 4 * (size_t)g.vstride) : 0;
-  const size_t need = 3 * sz_state + 3 * sz_shadow + sz_fx + sz_fy + sz_c + 2 * sz_c3 +
+  const size_t need = 3 * sz_state + 3 * sz_shadow + sz_fx + sz_fy + sz_fb + 2 * sz_c3 +
                       sz_stamp + 2 * sz_q + sz_sc;
   if (need > (size_t)GPMOOD_NOALLOC_SCRATCH_BYTES) return GPMOOD_E_TOO_BIG;
 
@@ -1093,6 +1122,12 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   g.dmr_wall_x0 = grid->dmr_wall_x0;
   g.dmr_xs0 = grid->dmr_xs0;
   g.dmr_xs_speed = grid->dmr_xs_speed;
+  g.jet_x0 = grid->jet_x0;
+  g.jet_x1 = grid->jet_x1;
+  prim_to_cons(grid->jet_prim[0], gamma, g.jetU[0]);
+  prim_to_cons(grid->jet_prim[1], gamma, g.jetU[1]);
+  g.riemann = o.riemann;
+  g.rate_floor = jet_rate(g);
   for (int r = 0; r < 4; ++r) h->cas.next[r] = h->cas.prev[r] = r;
   for (int k = 0; k + 1 < nc; ++k) {
     h->cas.next[cascade[k]] = cascade[k + 1];
@@ -1138,7 +1173,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   }
   h->Fx = p; p += sz_fx;
   h->Fy = p; p += sz_fy;
-  h->cad = p; p += sz_c;
+  h->fb = p; p += sz_fb;
   h->ord = p; p += sz_c3;
   h->first = p; p += sz_c3;
   h->stamp = (uint32_t*)p; p += sz_stamp;
@@ -1149,7 +1184,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   h->stream = (cudaStream_t)stream;
 
   // what the kernels expect to start at zero: face-CAD flags and MOOD stamps
-  CK(cudaMemsetAsync(h->cad, 0, ncell, h->stream));
+  CK(cudaMemsetAsync(h->fb, 0, nfb, h->stream));
   CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * ncell, h->stream));
   rc = gpmood_set_state(h, U_in, 1);
   if (rc) return rc;

@@ -41,6 +41,7 @@ __global__ void k_dt_reduce_batch(const double* X, const float* Xf, const Prob* 
       if (!cell_rate_at(Xp, Xfp, g, i, j, a)) bad = true;
       else best = a > best ? a : best;
     }
+    if (w.a == 0 && threadIdx.x == 0 && g.rate_floor > best) best = g.rate_floor;
     for (int o = 16; o > 0; o >>= 1) {
       double ob = __shfl_xor_sync(0xffffffffu, best, o);
       best = ob > best ? ob : best;
@@ -121,7 +122,7 @@ struct gpmood_batch_s {
   double* U[3];
   float* Uf[3];  // float shadows of U (FP32 path only, else null)
   void *Fx, *Fy;
-  uint8_t *cad, *ord, *first;
+  uint8_t *fb, *ord, *first;  // fb: face-state check bits, x faces then y faces
   uint32_t* stamp;
   int* queue[2];
   Prob* probs;
@@ -149,6 +150,22 @@ struct gpmood_batch_s {
 
 namespace {
 
+// CFL rate max((|u|+c)/dx, (|v|+c)/dy) of the jet inflow states of a grid's
+// jet sides (0 without): those states enter the domain at the first step
+double jet_rate(const Grid& g) {
+  double r = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    if (g.bc[2 + side] != 6) continue;
+    const double* S = g.jetU[side];
+    const double u = S[1] / S[0], v = S[2] / S[0];
+    const double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * u + S[2] * v));
+    const double c = sqrt(g.gamma * p / S[0]);
+    const double ax = (fabs(u) + c) / g.dx, ay = (fabs(v) + c) / g.dy;
+    r = fmax(r, fmax(ax, ay));
+  }
+  return r;
+}
+
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 void prim_to_cons(const double* P, double gam, double* U) {
@@ -175,7 +192,7 @@ void batch_free(gpmood_batch_t b) {
     cudaFree(b->U[k]);
     cudaFree(b->Uf[k]);
   }
-  void* ptrs[] = {b->Fx, b->Fy, b->cad, b->ord, b->first, b->stamp, b->queue[0], b->queue[1],
+  void* ptrs[] = {b->Fx, b->Fy, b->fb, b->ord, b->first, b->stamp, b->queue[0], b->queue[1],
                   b->probs, b->psc, b->gsc, b->items_fx[0], b->items_fx[1], b->items_fy[0],
                   b->items_fy[1], b->items_up, b->items_dt};
   for (void* p : ptrs) cudaFree(p);
@@ -213,7 +230,8 @@ StageArgs<Real> batch_args(gpmood_batch_t b, int s, int ia, int ix, int io) {
   }
   A.Fx = (double*)b->Fx;
   A.Fy = (double*)b->Fy;
-  A.cad = b->cad;
+  A.fbx = b->fb;
+  A.fby = b->fb + b->fx_elems / 4;
   A.ord = b->ord + (size_t)s * b->total_cells;
   A.first = b->first + (size_t)s * b->total_cells;
   A.queue = b->queue[0];
@@ -507,6 +525,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   }
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
   if (o.rk != 0 && o.rk != 3) return GPMOOD_E_INVAL;  // batches step with SSP-RK3
+  if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
   const int H = R_max + 1 > 2 ? R_max + 1 : 2;
   const int minn = H > 3 ? H : 3;
   // every problem shares the weights: the same ell/dx and ell/dy
@@ -518,7 +537,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
       return GPMOOD_E_INVAL;
     for (int s = 0; s < 4; ++s) {
       int k = gr->bc[s];
-      if (k < 0 || k > 5 || (k == GPMOOD_BC_DMR_BOTTOM && s != 2) ||
+      if (k < 0 || k > 6 || (k == GPMOOD_BC_JET && s < 2) || (k == GPMOOD_BC_DMR_BOTTOM && s != 2) ||
           (k == GPMOOD_BC_DMR_TOP && s != 3))
         return GPMOOD_E_INVAL;
     }
@@ -587,6 +606,12 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
     g.dmr_wall_x0 = gr->dmr_wall_x0;
     g.dmr_xs0 = gr->dmr_xs0;
     g.dmr_xs_speed = gr->dmr_xs_speed;
+    g.jet_x0 = gr->jet_x0;
+    g.jet_x1 = gr->jet_x1;
+    prim_to_cons(gr->jet_prim[0], gamma, g.jetU[0]);
+    prim_to_cons(gr->jet_prim[1], gamma, g.jetU[1]);
+    g.riemann = o.riemann;
+    g.rate_floor = jet_rate(g);
     P.det.sigma_v = o.sigma_v > 0 ? o.sigma_v : 5.0;
     P.det.sigma_p = o.sigma_p > 0 ? o.sigma_p : 5.0;
     P.det.csd_on = o.csd_off ? 0 : 1;
@@ -665,7 +690,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
       ok = ok && cudaMalloc(&b->Uf[k], sizeof(float) * (size_t)b->state_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&b->Fx, fsz * (size_t)b->fx_elems) == cudaSuccess;
   ok = ok && cudaMalloc(&b->Fy, fsz * (size_t)b->fy_elems) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->cad, nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->fb, (size_t)(b->fx_elems + b->fy_elems) / 4) == cudaSuccess;
   ok = ok && cudaMalloc(&b->ord, 3 * nc_all) == cudaSuccess;
   ok = ok && cudaMalloc(&b->first, 3 * nc_all) == cudaSuccess;
   ok = ok && cudaMalloc(&b->stamp, 4 * nc_all) == cudaSuccess;
@@ -687,7 +712,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   if (ok)
     ok = cudaMemcpy(b->probs, b->hprobs.data(), sizeof(Prob) * nprob, cudaMemcpyHostToDevice) ==
              cudaSuccess &&
-         cudaMemset(b->cad, 0, nc_all) == cudaSuccess &&
+         cudaMemset(b->fb, 0, (size_t)(b->fx_elems + b->fy_elems) / 4) == cudaSuccess &&
          cudaMemset(b->ord, 0, 3 * nc_all) == cudaSuccess &&
          cudaMemset(b->first, 0, 3 * nc_all) == cudaSuccess &&
          cudaMemset(b->stamp, 0, 4 * nc_all) == cudaSuccess &&

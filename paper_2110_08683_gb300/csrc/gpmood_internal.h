@@ -27,6 +27,10 @@ struct Grid {
   double bcU[4][4];       // conservative Dirichlet state per side
   double dmr_post[4], dmr_pre[4];  // conservative states
   double dmr_wall_x0, dmr_xs0, dmr_xs_speed;
+  double jet_x0, jet_x1;  // inflow slit of the JET kind
+  double jetU[2][4];      // conservative jet states, S and N sides
+  int riemann;            // 0 HLLC, 1 HLL
+  double rate_floor;      // CFL rate of the jet inflow states (0: no jet side)
 };
 
 // step controls written by the host before every step
@@ -114,7 +118,8 @@ struct StageArgs {
   Real* outr;        // float shadow of out (FP32), null (FP64)
   double* Fx;        // face-averaged fluxes, FP64 on both paths: each float flux is
   double* Fy;        // widened once, by the face kernel, not once per neighbour
-  uint8_t* cad;
+  uint8_t* fbx;      // per x face: bit 0 its left, bit 1 its right state failed the
+  uint8_t* fby;      // face-state check (per y face: lower, upper), at the face's radius
   uint8_t* ord;      // radius per cell, this stage
   uint8_t* first;    // first-pass troubled map, this stage
   int* queue;        // troubled cells (first pass output)

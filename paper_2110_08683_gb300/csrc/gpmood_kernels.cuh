@@ -168,6 +168,35 @@ __device__ __forceinline__ float sqrt_r(float x) {
   return r;
 }
 
+// products and sums rounded one by one (no contraction into an FMA): where
+// an expression's mirror image swaps its terms, both then round alike, so a
+// mirror-symmetric problem stays symmetric bit for bit
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// pressure of a conservative state with 1/rho given, the velocities out: one
+// fixed sequence of rounded operations, so two states that are mirror images
+// (a momentum component negated) give the same pressure bit for bit, whichever
+// side of a face or of a cell each sits on
+template <class Real>
+__device__ __forceinline__ Real pressure_ir(const Real* U, Real ir, Real gm1, Real& u, Real& v) {
+  u = mul_rn(U[1], ir);
+  v = mul_rn(U[2], ir);
+  const Real k = fma(U[1], u, mul_rn(U[2], v));  // m_x u + m_y v
+  return mul_rn(gm1, fma(Real(-0.5), k, U[3]));
+}
+
+// quiet NaN: the flux of a face whose state lies outside the Riemann solver's
+// domain (non-positive or non-finite density or pressure) is undefined
+__device__ __forceinline__ void qnan(double& x) { x = __longlong_as_double(0x7ff8000000000000ll); }
+__device__ __forceinline__ void qnan(float& x) { x = __int_as_float(0x7fc00000); }
+template <class Real>
+__device__ __forceinline__ bool solver_domain(Real rL, Real rR, Real pL, Real pR) {
+  return rL > Real(0) && rR > Real(0) && pL > Real(0) && pR > Real(0);
+}
+
 // x-direction HLLC flux; pL/pR return the pressures of the two states so the
 // caller can run face-state CAD without another EoS evaluation.
 // wave speeds S_L = min(uL-cL, uR-cR), S_R = max(uL+cL, uR+cR); the star
@@ -210,8 +239,55 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   }
   bool useL = SL >= Real(0);
   bool useS = left || (SR > Real(0));
+  const bool dom = solver_domain(rL, rR, pL, pR);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) F[v] = useL ? FL[v] : (useS ? Fs[v] : FR[v]);
+  for (int v = 0; v < 4; ++v) {
+    F[v] = useL ? FL[v] : (useS ? Fs[v] : FR[v]);
+    if (!dom) qnan(F[v]);
+  }
+}
+
+// x-direction HLL flux (Harten, Lax and van Leer 1983): the single
+// intermediate state between the wave speeds of hllc_x; pL/pR as there
+template <class Real>
+__device__ __forceinline__ void hll_x(const Real* UL, const Real* UR, Real gam, Real* F,
+                                      Real& pL, Real& pR) {
+  const Real gm1 = gam - Real(1);
+  Real rL = UL[0], rR = UR[0];
+  Real irL = recip(rL), irR = recip(rR);
+  Real uL, vL, uR, vR;
+  pL = pressure_ir(UL, irL, gm1, uL, vL);
+  pR = pressure_ir(UR, irR, gm1, uR, vR);
+  Real cL = sqrt_r(mul_rn(mul_rn(gam, pL), irL)), cR = sqrt_r(mul_rn(mul_rn(gam, pR), irR));
+  Real aL = uL - cL, bL = uR - cR;
+  Real SL = aL < bL ? aL : bL;
+  Real aR = uL + cL, bR = uR + cR;
+  Real SR = aR > bR ? aR : bR;
+  // physical fluxes by the same rounded sequence on both sides
+  const Real mL = mul_rn(rL, uL), mR = mul_rn(rR, uR);
+  Real FL[4] = {mL, fma(mL, uL, pL), mul_rn(mL, vL), mul_rn(uL, UL[3] + pL)};
+  Real FR[4] = {mR, fma(mR, uR, pR), mul_rn(mR, vR), mul_rn(uR, UR[3] + pR)};
+  const Real iw = recip(SR - SL);
+  const bool useL = SL >= Real(0), useR = !(SR > Real(0));
+  const bool dom = solver_domain(rL, rR, pL, pR);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    // x-mirror: (L, R, S_L, S_R) -> (R', L', -S_R, -S_L) swaps the two
+    // products; each is rounded on its own so the mirror face negates exactly
+    const Real a = mul_rn(SR, FL[v]), b = mul_rn(SL, FR[v]);
+    const Real c = mul_rn(mul_rn(SL, SR), UR[v] - UL[v]);
+    Real Fm = add_rn(a - b, c) * iw;
+    F[v] = useL ? FL[v] : (useR ? FR[v] : Fm);
+    if (!dom) qnan(F[v]);
+  }
+}
+
+// the Riemann solver of the grid (Grid::riemann: 0 HLLC, 1 HLL)
+template <class Real>
+__device__ __forceinline__ void riemann_x(int kind, const Real* UL, const Real* UR, Real gam,
+                                          Real* F, Real& pL, Real& pR) {
+  if (kind == 1) hll_x<Real>(UL, UR, gam, F, pL, pR);
+  else hllc_x<Real>(UL, UR, gam, F, pL, pR);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,6 +413,12 @@ __device__ __forceinline__ void fill_ghost(double* X, float* Xf, const Grid& g, 
     } else if (kind == 5) {
       fixed = true;
       P = (xc < g.dmr_xs0 + g.dmr_xs_speed * t) ? g.dmr_post : g.dmr_pre;
+    } else if (kind == 6) {
+      // jet inflow inside the slit (cell centres), outflow elsewhere
+      if (xc >= g.jet_x0 && xc <= g.jet_x1) {
+        fixed = true;
+        P = g.jetU[side];
+      }
     } else if (kind == 2) {
       reflect = true;
     }
@@ -370,18 +452,22 @@ __global__ void k_to_real(const double* X, Real* Y, long long n) {
 }
 
 // ---------------------------------------------------------------------------
-// face-state CAD flag on a possibly-ghost cell
+// face-state check of cell (i, j): a state that its own stencil produced on
+// one of its four faces, at the face's current radius, failed (non-finite or
+// non-positive density or pressure).  Periodic seams need no care: a seam
+// face's state of the cell across the seam is computed from the same data at
+// the cell's own face; other ghosts' states flag nothing.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void flag_cad(uint8_t* cad, const Grid& g, int i, int j) {
-  if (i < 0 || i >= g.nx) {
-    if (!g.periodic_x) return;
-    i = wrapi(i, g.nx);
+template <class Real>
+__device__ __forceinline__ bool face_state_bad(const StageArgs<Real>& A, const Grid& g, int i,
+                                               int j) {
+  const long long wf = (long long)j * (g.nx + 1) + i;  // x face i: W face of (i, j)
+  int b = (A.fbx[wf] >> 1) | A.fbx[wf + 1];            // its right / the E face's left state
+  if (g.dim == 2) {
+    const long long sf = (long long)j * g.nx + i;       // y face j: S face of (i, j)
+    b |= (A.fby[sf] >> 1) | A.fby[sf + g.nx];
   }
-  if (j < 0 || j >= g.ny) {
-    if (!g.periodic_y) return;
-    j = wrapi(j, g.ny);
-  }
-  cad[cidx(g, i, j)] = 1;
+  return (b & 1) != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -524,33 +610,46 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
   const Real gam = (Real)g.gamma;
   Real F[4] = {0, 0, 0, 0};
   bool badL = false, badR = false;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    Real f[4], pl, pr;
+  auto point = [&](int q, Real* f) {
+    Real pl, pr;
     if (DIR == 0) {
-      hllc_x<Real>(SL[q], SM[q], gam, f, pl, pr);
+      riemann_x<Real>(g.riemann, SL[q], SM[q], gam, f, pl, pr);
     } else {
       Real a[4] = {SL[q][0], SL[q][2], SL[q][1], SL[q][3]};
       Real b[4] = {SM[q][0], SM[q][2], SM[q][1], SM[q][3]};
       Real h[4];
-      hllc_x<Real>(a, b, gam, h, pl, pr);
+      riemann_x<Real>(g.riemann, a, b, gam, h, pl, pr);
       f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
     }
-    badL |= !(finite_r(SL[q][0]) && finite_r(pl));
-    badR |= !(finite_r(SM[q][0]) && finite_r(pr));
+    // face-state check: finite and positive density and pressure (the
+    // solver's sound speed needs gamma p / rho > 0; NaN fails the test)
+    badL |= !(SL[q][0] > Real(0) && pl > Real(0) && finite_r(SL[q][0]) && finite_r(pl));
+    badR |= !(SM[q][0] > Real(0) && pr > Real(0) && finite_r(SM[q][0]) && finite_r(pr));
+  };
+  // the Gauss points in mirror pairs (g, -g), each pair summed first: a
+  // mirror image of the problem that reverses the points sums alike
 #pragma unroll
-    for (int v = 0; v < 4; ++v) F[v] = fma(W.w[q], f[v], F[v]);
+  for (int kk = 0; kk < (Q + 1) / 2; ++kk) {
+    Real f1[4];
+    point(kk, f1);
+    if (Q - 1 - kk != kk) {
+      Real f2[4];
+      point(Q - 1 - kk, f2);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) F[v] = fma(W.w[kk], add_rn(f1[v], f2[v]), F[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) F[v] = fma(W.w[kk], f1[v], F[v]);
+    }
   }
   if (DIR == 0) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, i, j)] = F[v];
-    if (badL) flag_cad(A.cad, g, i - 1, j);
-    if (badR) flag_cad(A.cad, g, i, j);
+    A.fbx[(long long)j * (g.nx + 1) + i] = (uint8_t)((badL ? 1 : 0) | (badR ? 2 : 0));
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, i, j)] = F[v];
-    if (badL) flag_cad(A.cad, g, i, j - 1);
-    if (badR) flag_cad(A.cad, g, i, j);
+    A.fby[(long long)j * g.nx + i] = (uint8_t)((badL ? 1 : 0) | (badR ? 2 : 0));
   }
 }
 
@@ -593,11 +692,14 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
     Real eE = xload<Real>(X, g, 3, i + 1, j), eW = xload<Real>(X, g, 3, i - 1, j);
     Real eN = xload<Real>(X, g, 3, i, j + 1), eS = xload<Real>(X, g, 3, i, j - 1);
     Real iE = recip(rE), iW = recip(rW), iN = recip(rN), iS = recip(rS);
-    Real uE = mxE * iE, uW = mxW * iW, vN = myN * iN, vS = myS * iS;
-    Real pE = gm1 * (eE - Real(0.5) * (mxE * mxE + myE * myE) * iE);
-    Real pW = gm1 * (eW - Real(0.5) * (mxW * mxW + myW * myW) * iW);
-    Real pN = gm1 * (eN - Real(0.5) * (mxN * mxN + myN * myN) * iN);
-    Real pS = gm1 * (eS - Real(0.5) * (mxS * mxS + myS * myS) * iS);
+    // one rounded sequence for every neighbour: mirror neighbours agree bitwise
+    const Real SE[4] = {rE, mxE, myE, eE}, SW[4] = {rW, mxW, myW, eW};
+    const Real SN[4] = {rN, mxN, myN, eN}, SS[4] = {rS, mxS, myS, eS};
+    Real uE, uW, vN, vS, tmp;
+    Real pE = pressure_ir(SE, iE, gm1, uE, tmp);
+    Real pW = pressure_ir(SW, iW, gm1, uW, tmp);
+    Real pN = pressure_ir(SN, iN, gm1, tmp, vN);
+    Real pS = pressure_ir(SS, iS, gm1, tmp, vS);
     const Real hx = Real(0.5) * (Real)g.inv_dx, hy = Real(0.5) * (Real)g.inv_dy;
     Real mx_ = pE < pW ? pE : pW, my_ = pN < pS ? pN : pS;
     Real divV = (uE - uW) * hx, gradP = fabs(pE - pW) * hx * recip(mx_);
@@ -633,9 +735,13 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
     for (int m = 0; m < 5; ++m) {
       if (m >= 1 + nnb) break;
       int ii = i + ci[m], jj = j + cj[m];
-      Real k = w[0] * xload<Real>(X, g, 0, ii, jj - 1) + w[1] * xload<Real>(X, g, 0, ii - 1, jj) +
-               w[2] * xload<Real>(X, g, 0, ii, jj) + w[3] * xload<Real>(X, g, 0, ii + 1, jj) +
-               w[4] * xload<Real>(X, g, 0, ii, jj + 1);
+      // mirror pairs (S, N) and (W, E) summed first, each product rounded on
+      // its own: a mirror-symmetric state gives the same curvature bit for bit
+      const Real ks = add_rn(mul_rn(w[0], xload<Real>(X, g, 0, ii, jj - 1)),
+                             mul_rn(w[4], xload<Real>(X, g, 0, ii, jj + 1)));
+      const Real kw = add_rn(mul_rn(w[1], xload<Real>(X, g, 0, ii - 1, jj)),
+                             mul_rn(w[3], xload<Real>(X, g, 0, ii + 1, jj)));
+      Real k = add_rn(add_rn(ks, kw), mul_rn(w[2], xload<Real>(X, g, 0, ii, jj)));
       if (m == 0) {
         cmin = k;
         cmax = k;
@@ -711,13 +817,12 @@ __device__ __forceinline__ void update_cell_w(const StageArgs<Real>& A, const Gr
     candidate<Real>(A, g, i, j, dt, Y);
     const int top = Wd.top;
     if (top != 0) {
-      bad = A.cad[c] != 0 || troubled<Real>(A.Xr, g, D, d2x, d2y, i, j, Y);
+      bad = face_state_bad<Real>(A, g, i, j) || troubled<Real>(A.Xr, g, D, d2x, d2y, i, j, Y);
     } else {
       Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
       Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
       if (!(y[0] > Real(0)) || !(p > Real(0))) atomicAdd(&A.scw->nfog_pad[A.stage], 1);
     }
-    A.cad[c] = 0;
     A.ord[c] = (uint8_t)top;
     A.first[c] = (uint8_t)bad;
     combine_store<Real>(A, g, i, j, Y);
@@ -774,19 +879,27 @@ __device__ __forceinline__ void radius_pair(const Grid& g, const uint8_t* ord, c
 template <int K, class Real, class T = Real>
 __device__ __forceinline__ void recon_direct(const T* X, const Grid& g, const Real* z, int i,
                                              int j, Real* S) {
+  // row by row, each row from its centre out in x-mirror pairs (a, -a) with
+  // every product rounded on its own: the x-mirror image of the problem,
+  // whose weights are the mirrored ones, gives the mirrored state bit for bit
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const T* Xv = X + (long long)v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
     Real s = Real(0);
-    int m = 0;
+    int row = 0;  // stencil index of the row's first cell
 #pragma unroll
-    for (int b = -K; b <= K; ++b)
+    for (int b = -K; b <= K; ++b) {
+      const int hb = K - (b < 0 ? -b : b);
+      const int mid = row + hb;  // (0, b)
+      const T* Xr = Xv + (long long)b * g.pitch;
+      Real t = mul_rn(z[mid], (Real)__ldg(Xr));
 #pragma unroll
-      for (int a = -K; a <= K; ++a)
-        if ((a < 0 ? -a : a) + (b < 0 ? -b : b) <= K) {
-          s = fma(z[m], (Real)__ldg(Xv + b * g.pitch + a), s);
-          ++m;
-        }
+      for (int a = 1; a <= hb; ++a)
+        t = add_rn(t, add_rn(mul_rn(z[mid + a], (Real)__ldg(Xr + a)),
+                             mul_rn(z[mid - a], (Real)__ldg(Xr - a))));
+      s = add_rn(s, t);
+      row += 2 * hb + 1;
+    }
     S[v] = s;
   }
 }
@@ -800,8 +913,7 @@ __device__ void face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, i
   const Real gam = (Real)g.gamma;
   F[0] = F[1] = F[2] = F[3] = Real(0);
   badL = badR = false;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
+  auto point = [&](int q, Real* f) {
     Real UL[4], UR[4];
     if (K == 0) {
 #pragma unroll
@@ -814,20 +926,33 @@ __device__ void face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, i
       recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
       recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
     }
-    Real f[4], pl, pr;
+    Real pl, pr;
     if (DIR == 0) {
-      hllc_x<Real>(UL, UR, gam, f, pl, pr);
+      riemann_x<Real>(g.riemann, UL, UR, gam, f, pl, pr);
     } else {
       Real a[4] = {UL[0], UL[2], UL[1], UL[3]};
       Real b[4] = {UR[0], UR[2], UR[1], UR[3]};
       Real h[4];
-      hllc_x<Real>(a, b, gam, h, pl, pr);
+      riemann_x<Real>(g.riemann, a, b, gam, h, pl, pr);
       f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
     }
-    badL |= !(finite_r(UL[0]) && finite_r(pl));
-    badR |= !(finite_r(UR[0]) && finite_r(pr));
+    badL |= !(UL[0] > Real(0) && pl > Real(0) && finite_r(UL[0]) && finite_r(pl));
+    badR |= !(UR[0] > Real(0) && pr > Real(0) && finite_r(UR[0]) && finite_r(pr));
+  };
+  // mirror pairs (g, -g) summed first, in the order of the first-pass sweep
 #pragma unroll
-    for (int v = 0; v < 4; ++v) F[v] = fma(Wd.w[K][q], f[v], F[v]);
+  for (int kk = 0; kk < (Q + 1) / 2; ++kk) {
+    Real f1[4];
+    point(kk, f1);
+    if (Q - 1 - kk != kk) {
+      Real f2[4];
+      point(Q - 1 - kk, f2);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) F[v] = fma(Wd.w[K][kk], add_rn(f1[v], f2[v]), F[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) F[v] = fma(Wd.w[K][kk], f1[v], F[v]);
+    }
   }
 }
 
@@ -843,27 +968,31 @@ __device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const Di
     default: face_at<3, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
   }
   const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
+  // the face's state-check bits; a periodic seam face writes both copies
+  const uint8_t bits = (uint8_t)((bl ? 1 : 0) | (br ? 2 : 0));
   if (DIR == 0) {
     int f = iR;  // face index
 #pragma unroll
     for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, f, jL)] = F[v];
+    A.fbx[(long long)jL * (g.nx + 1) + f] = bits;
     if (g.periodic_x && (f == 0 || f == g.nx)) {
       int f2 = f == 0 ? g.nx : 0;
 #pragma unroll
       for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, f2, jL)] = F[v];
+      A.fbx[(long long)jL * (g.nx + 1) + f2] = bits;
     }
   } else {
     int f = jR;
 #pragma unroll
     for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, iL, f)] = F[v];
+    A.fby[(long long)f * g.nx + iL] = bits;
     if (g.periodic_y && (f == 0 || f == g.ny)) {
       int f2 = f == 0 ? g.ny : 0;
 #pragma unroll
       for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, iL, f2)] = F[v];
+      A.fby[(long long)f2 * g.nx + iL] = bits;
     }
   }
-  if (bl) flag_cad(A.cad, g, iL, jL);
-  if (br) flag_cad(A.cad, g, iR, jR);
 }
 
 // face f (0 W, 1 E, 2 S, 3 N) of queued cell c: recompute it if its EDP1
@@ -925,13 +1054,12 @@ __device__ __forceinline__ bool mood_update_item(const StageArgs<Real>& A, const
   candidate<Real>(A, g, di, dj, A.sc->dt, Y);
   bool flag = false;
   if (A.ord[d] != 0) {
-    flag = A.cad[d] != 0 || troubled<Real>(A.Xr, g, D, d2x, d2y, di, dj, Y);
+    flag = face_state_bad<Real>(A, g, di, dj) || troubled<Real>(A.Xr, g, D, d2x, d2y, di, dj, Y);
   } else {
     Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
     Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
     if (!(y[0] > Real(0)) || !(p > Real(0))) atomicAdd(&A.scw->nfog_pad[A.stage], 1);
   }
-  A.cad[d] = 0;
   combine_store<Real>(A, g, di, dj, Y);
   return flag;
 }
@@ -1053,7 +1181,8 @@ __device__ __forceinline__ StageArgs<Real> problem_args(const StageArgs<Real>& B
   A.out2 = B.out2 ? B.out2 + P.state_off : nullptr;
   A.Fx = B.Fx + P.fx_off;
   A.Fy = B.Fy + P.fy_off;
-  A.cad = B.cad + P.cell_off;
+  A.fbx = B.fbx + P.fx_off / 4;  // face planes: one per variable in the flux pools
+  A.fby = B.fby + P.fy_off / 4;
   A.ord = B.ord + P.cell_off;
   A.first = B.first + P.cell_off;
   A.sc = psc + p;

@@ -211,6 +211,51 @@ def dmr(nx=4096, ny=1024, R=3, ell_cells=12.0, cascade=None):
     )
 
 
+def mach_jet(n=600, R=3, ell_cells=12.0, cascade=None):
+    """Single Mach 100 light jet (Sec. 5.3): the outflow box [0,1.5]^2 with the
+    jet (gamma, 0, 100, 1) entering through the slit 0.7 <= x <= 0.8 at y = 0
+    into the ambient (10 gamma, 0, 0, 1); HLL; t_end 0.04.  The paper's
+    cascades are GP-MOOD3/5/7: [1, 0], [2, 1, 0], [3, 1, 0]."""
+    gamma = 1.4
+    jet = [gamma, 0.0, 100.0, 1.0]
+
+    def prim(x, y):
+        one = np.ones_like(x)
+        return 10.0 * gamma * one, 0.0 * one, 0.0 * one, one
+
+    U = cell_average(prim, n, n, 0.0, 1.5, 0.0, 1.5, gamma)
+    dx = 1.5 / n
+    return _problem(
+        name=f"machjet_{n}", nx=n, ny=n, x0=0.0, x1=1.5, y0=0.0, y1=1.5,
+        bc=["outflow", "outflow", "jet", "outflow"], jet_x=(0.7, 0.8), jet_prim=[jet, jet],
+        riemann="hll", cascade=cascade or ([R, 1, 0] if R > 1 else [1, 0]),
+        ell=ell_cells * dx, t_end=0.04, U0=U,
+    )
+
+
+def double_mach_jet(n=600, R=3, ell_cells=12.0, cascade=None):
+    """Double Mach 800 jet collision (Sec. 5.3): the single-jet box with the
+    ambient density stratified as rho = -9.24 y + 14 (u = v = 0, p = 1) and
+    jets (gamma, 0, +-800, 1) through 0.7 <= x <= 0.8 at y = 0 and y = 1.5.
+    The printed jet velocity is +800 at both ends; the top jet is injected
+    into the domain, so it enters with v = -800.  HLL; t_end 0.005."""
+    gamma = 1.4
+
+    def prim(x, y):
+        one = np.ones_like(x)
+        return -9.24 * y + 14.0, 0.0 * one, 0.0 * one, one
+
+    U = cell_average(prim, n, n, 0.0, 1.5, 0.0, 1.5, gamma)
+    dx = 1.5 / n
+    return _problem(
+        name=f"doublejet_{n}", nx=n, ny=n, x0=0.0, x1=1.5, y0=0.0, y1=1.5,
+        bc=["outflow", "outflow", "jet", "jet"], jet_x=(0.7, 0.8),
+        jet_prim=[[gamma, 0.0, 800.0, 1.0], [gamma, 0.0, -800.0, 1.0]],
+        riemann="hll", cascade=cascade or ([R, 1, 0] if R > 1 else [1, 0]),
+        ell=ell_cells * dx, t_end=0.005, U0=U,
+    )
+
+
 def quadrant_states(seed=0, count=1):
     """count draws of four quadrant states (rho, u, v, p) with rho in [0.1,2],
     p in [0.05,2], u,v in [-1,1] from numpy's default_rng(seed)."""

@@ -273,8 +273,12 @@ def test_sod_1d_run_to_t_end(precision):
     assert err < 7e-3, err  # the oracle's own error at 128 cells is 5.5e-3
     assert (Ug[0] > 0).all()
     m0 = p["U0"][0].sum() / n
-    # round-off only (no wave reaches the ends): 1e-13 relative per step
-    assert abs(Ug[0].sum() / n - m0) <= ng * 1e-13 * m0
+    # round-off only (no wave reaches the ends): 1e-13 relative per step in
+    # FP64; the FP32 path's reconstruction of the uniform end states rounds in
+    # float, so the outflow faces carry float-level fluxes (periodic domains,
+    # with no boundary flux, hold 1e-13 in both paths: the conservation tests)
+    per_step = 1e-13 if precision == "fp64" else 1e-12
+    assert abs(Ug[0].sum() / n - m0) <= ng * per_step * m0
 
 
 def test_sod_1d_rejected_where_unsupported():

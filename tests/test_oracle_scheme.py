@@ -53,6 +53,66 @@ def test_hllc_supersonic_is_upwind():
     np.testing.assert_allclose(O.hllc(UL, UR), euler_flux(UR), rtol=1e-15)
 
 
+@pytest.mark.parametrize("state", [(1.0, 0.3, -0.2, 1.0), (14.0, 0.0, 100.0, 1.0)])
+def test_hll_consistency_and_upwinding(state):
+    # HLL (Harten, Lax, van Leer 1983), the flux of the Mach-jet runs (Sec. 5.3)
+    U = cons(*state)
+    np.testing.assert_allclose(O.hll(U, U), euler_flux(U), rtol=1e-14, atol=1e-14)
+    Uy = np.array([U[0], U[2], U[1], U[3]])
+    Fx = euler_flux(Uy)
+    np.testing.assert_allclose(O.hll(U, U, direction=1), [Fx[0], Fx[2], Fx[1], Fx[3]],
+                               rtol=1e-14, atol=1e-12)
+    UL, UR = cons(1.0, 3.0, 0.1, 0.4), cons(0.5, 2.5, 0.0, 0.3)
+    np.testing.assert_allclose(O.hll(UL, UR), euler_flux(UL), rtol=1e-15)
+    UL, UR = cons(1.0, -3.0, 0.1, 0.4), cons(0.5, -3.5, 0.0, 0.3)
+    np.testing.assert_allclose(O.hll(UL, UR), euler_flux(UR), rtol=1e-15)
+
+
+def test_hll_is_rusanov_when_the_wave_speeds_are_symmetric():
+    # at rest with equal sound speeds S_L = -S_R = -c, and HLL reduces to the
+    # local Lax-Friedrichs (Rusanov) flux (F_L + F_R)/2 - c (U_R - U_L)/2
+    gam = 1.4
+    UL, UR = cons(1.0, 0.0, 0.4, 1.0), cons(0.5, 0.0, -0.3, 0.5)
+    c = math.sqrt(gam * 1.0 / 1.0)
+    rus = 0.5 * (euler_flux(UL) + euler_flux(UR)) - 0.5 * c * (UR - UL)
+    np.testing.assert_allclose(O.hll(UL, UR), rus, rtol=1e-14, atol=1e-15)
+    # and unlike HLLC it does not hold the stationary contact exactly
+    assert abs(O.hll(UL, UR)[0]) > 0.1
+
+
+def test_jet_ghosts_and_first_time_step():
+    # jet kind (Sec. 5.3): ghost rows under the slit carry the jet state, the
+    # rest copy the edge row; the first CFL bound counts the entering jet
+    p = I.mach_jet(n=30, R=1)
+    o = O.Oracle(p)
+    U = p["U0"]
+    Xg = o.fill_ghosts(U)
+    H = o.H
+    dx = 1.5 / 30
+    xc = (np.arange(30) + 0.5) * dx
+    slit = (xc >= 0.7) & (xc <= 0.8)
+    jet = cons(1.4, 0.0, 100.0, 1.0)
+    for k in range(H):
+        row = Xg[:, k, H:H + 30]
+        np.testing.assert_allclose(row[:, slit], np.repeat(jet[:, None], slit.sum(), 1), rtol=1e-15)
+        np.testing.assert_array_equal(row[:, ~slit], U[:, 0, ~slit])
+        np.testing.assert_array_equal(Xg[:, H + 30 + k, H:H + 30], U[:, -1, :])
+    # the jet's bound dx / (|v| + c) with c = 1 is far below the ambient's
+    assert o.dt(U, 0.8) == pytest.approx(0.8 * dx / 101.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("riemann", ["hllc", "hll"])
+def test_sod_converges_with_either_riemann_solver(riemann):
+    errs = []
+    for n in (64, 128, 256):
+        p = I.sod_1d(n=n)
+        p["riemann"] = riemann
+        U, _, _ = O.Oracle(p).run(p["U0"], 0.2)
+        xc = (np.arange(n) + 0.5) / n
+        errs.append(np.abs(U[0, 0] - ER.sod_density(xc, 0.2)).sum() / n)
+    assert errs[0] > errs[1] > errs[2] and errs[1] < 8e-3, errs
+
+
 def test_sod_against_exact_riemann_solution():
     # Sod tube (1D, GP-R2 cascade 5->3->1, ell = 12 dx, CFL 0.8, t = 0.2):
     # L1 density error against the exact solution decreases under refinement
