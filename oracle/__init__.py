@@ -18,6 +18,7 @@ LIB = os.path.join(HERE, "_build", "libgpmood_oracle.so")
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5,
       "jet": 6}
 RIEMANN = {"hllc": 0, "hll": 1}
+RECON = {"gp": 0, "poly3": 1}
 ACCEPT_CSD, ACCEPT_PLATEAU, ACCEPT_DMP, ACCEPT_U2 = 1, 2, 3, 4
 FAIL_CAD, FAIL_PAD, FAIL_U2 = -1, -2, -3
 
@@ -46,7 +47,7 @@ class Config(C.Structure):
         ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4),
         ("dmr_wall_x0", C.c_double), ("dmr_xs0", C.c_double), ("dmr_xs_speed", C.c_double),
         ("rk", C.c_int), ("riemann", C.c_int), ("jet_x0", C.c_double), ("jet_x1", C.c_double),
-        ("jet_prim", (C.c_double * 4) * 2),
+        ("jet_prim", (C.c_double * 4) * 2), ("poly3", C.c_int),
     ]
 
 
@@ -87,6 +88,10 @@ def lib():
         L.orc_hllc.restype = None
         L.orc_hll.argtypes = [p, p, d, i, p]
         L.orc_hll.restype = None
+        L.orc_curvature.argtypes = [p, p, i, i, i]
+        L.orc_curvature.restype = d
+        L.orc_poly3_eval.argtypes = [i, p, d, d]
+        L.orc_poly3_eval.restype = d
         _lib_handle = L
     return _lib_handle
 
@@ -142,6 +147,13 @@ def d2_weights(dim, ell, dx, dy):
     return wxx[:n], wyy[:n]
 
 
+def poly3_eval(dim, qv, xs, ys):
+    """Poly3 (eq. poly3, App. C) of the R = 1 stencil values qv (orc_stencil
+    order) at (xs, ys) in cell units from the cell centre."""
+    qv = np.ascontiguousarray(qv, dtype=np.float64)
+    return lib().orc_poly3_eval(int(dim), _ptr(qv), float(xs), float(ys))
+
+
 def hllc(UL, UR, gamma=1.4, direction=0):
     UL = np.ascontiguousarray(UL, dtype=np.float64)
     UR = np.ascontiguousarray(UR, dtype=np.float64)
@@ -188,6 +200,7 @@ def make_config(prob):
     for side, P in enumerate(prob.get("jet_prim", ([1.0, 0.0, 0.0, 1.0],) * 2)):
         for k in range(4):
             cfg.jet_prim[side][k] = P[k]
+    cfg.poly3 = RECON[prob.get("recon", "gp")]
     return cfg
 
 
@@ -277,6 +290,10 @@ class Oracle:
         Xg = np.ascontiguousarray(Xg, dtype=np.float64)
         Y4 = np.ascontiguousarray(Y4, dtype=np.float64)
         return lib().orc_detect_cell(self.h, _ptr(Xg), i, j, _ptr(Y4))
+
+    def curvature(self, Xg, d, i, j):
+        Xg = np.ascontiguousarray(Xg, dtype=np.float64)
+        return lib().orc_curvature(self.h, _ptr(Xg), d, i, j)
 
     def run(self, U, t_end, cfl=None, max_steps=10**9):
         """Steps to t_end with the last step clipped.  Returns (U, nsteps, t)."""

@@ -13,6 +13,7 @@
  *             (eq. normalized_z), Cholesky solve
  *   Sec. 2.5  weights in quadruple precision, stored in double
  *   Sec. 2.6  FOG = radius 0
+ *   Sec. 3.1 (iv), App. C  Poly3 of POL-MOOD3 (eq. poly3, eq. p3_coeffs)
  *   Sec. 3.2-3.4  PAD, CAD (cell and face states), plateau, DMP, u2, CSD
  *   Sec. 3.6  EDP1 face orders
  *   Sec. 3.8  SSP-RK3 (eq. rk3)
@@ -264,6 +265,34 @@ int orc_d2_weights(int dim, double ell_d, double dx, double dy, double* wxx, dou
 }
 
 /* ------------------------------------------------------------------------- */
+/* Poly3 of POL-MOOD3 (Sec. 3.1 (iv)): p3 = a0 + a1 x + a2 x^2 + a3 y + a4 y^2  */
+/* (+ a5 xy, eq. poly3) matched to the five cell averages of the R = 1 stencil  */
+/* (eq. p3_coeffs).  The xy monomial averages to zero on each of the five     */
+/* cells, so a5 is left at 0.  The coefficients are App. C's, with its        */
+/* labelling q1 centre, q2 west, q3 north, q4 east, q5 south (the orc_stencil */
+/* order), in cell units with the origin at the cell centre.                 */
+/* ------------------------------------------------------------------------- */
+static void poly3_coeffs(const double* q /* q1..q5 as q[0..4] */, double* a) {
+  a[0] = 7.0 / 6.0 * q[0] - q[1] / 24.0 - q[2] / 24.0 - q[3] / 24.0 - q[4] / 24.0;
+  a[1] = -0.5 * q[1] + 0.5 * q[3];
+  a[2] = -q[0] + 0.5 * q[1] + 0.5 * q[3];
+  a[3] = 0.5 * q[2] - 0.5 * q[4];
+  a[4] = -q[0] + 0.5 * q[2] + 0.5 * q[4];
+}
+
+double orc_poly3_eval(int dim, const double* qv, double xs, double ys) {
+  double q[5], a[5];
+  if (dim == 1) {
+    /* 1D stencil order: centre, west, east; the y neighbours equal the centre */
+    q[0] = qv[0]; q[1] = qv[1]; q[2] = qv[0]; q[3] = qv[2]; q[4] = qv[0];
+  } else {
+    for (int m = 0; m < 5; ++m) q[m] = qv[m];
+  }
+  poly3_coeffs(q, a);
+  return a[0] + a[1] * xs + a[2] * xs * xs + a[3] * ys + a[4] * ys * ys;
+}
+
+/* ------------------------------------------------------------------------- */
 /* context                                                                   */
 /* ------------------------------------------------------------------------- */
 struct orc_ctx {
@@ -303,6 +332,7 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
   for (int k = 0; k + 1 < cfg->ncascade; ++k)
     if (!(cfg->cascade[k] > cfg->cascade[k + 1])) return -1;
   if (cfg->cascade[0] > 3) return -1;
+  if (cfg->poly3 && !(cfg->ncascade == 2 && cfg->cascade[0] == 1)) return -1;
   orc_ctx* c = (orc_ctx*)calloc(1, sizeof(orc_ctx));
   c->cfg = *cfg;
   c->top = cfg->cascade[0];
@@ -332,6 +362,7 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
     c->n[R] = orc_stencil(cfg->dim, R, c->off[R]);
     c->q[R] = face_q(cfg->dim, R);
     c->z[R] = (double*)malloc(sizeof(double) * 4 * MAXQ * MAXN);
+    if (cfg->poly3) continue; /* Poly3 is evaluated from App. C, no weights */
     if (orc_gp_weights(cfg->dim, R, lamx, lamy, c->z[R], 0, 0) != 0) {
       orc_destroy(c);
       return -2;
@@ -339,7 +370,17 @@ int orc_create(const orc_config* cfg, orc_ctx** out) {
   }
   for (int q = 1; q <= 4; ++q) orc_gauss_rule(q, c->gq[q], c->gw[q]);
   orc_stencil(cfg->dim, 1, c->off1);
-  if (orc_d2_weights(cfg->dim, cfg->ell, c->dx, c->dy, c->wxx, c->wyy) < 0) {
+  if (cfg->poly3) {
+    /* POL-MOOD3: the u2 curvatures (eq. u2_curvature) are p3's own second
+       derivatives, 2 a2 / dx^2 and 2 a4 / dy^2 (App. C), i.e. the centred
+       differences q2 - 2 q1 + q4 and q3 - 2 q1 + q5 over the cell size squared */
+    int n1 = orc_stencil(cfg->dim, 1, c->off1);
+    for (int m = 0; m < n1; ++m) {
+      int a = c->off1[2 * m], b = c->off1[2 * m + 1];
+      c->wxx[m] = (b == 0 ? (a == 0 ? -2.0 : 1.0) : 0.0) / (c->dx * c->dx);
+      c->wyy[m] = (cfg->dim == 2 && a == 0) ? (b == 0 ? -2.0 : 1.0) / (c->dy * c->dy) : 0.0;
+    }
+  } else if (orc_d2_weights(cfg->dim, cfg->ell, c->dx, c->dy, c->wxx, c->wyy) < 0) {
     orc_destroy(c);
     return -2;
   }
@@ -600,6 +641,21 @@ static void reconstruct(const orc_ctx* c, const double* Xg, int R, int f, int gi
     return;
   }
   int n = c->n[R], q = c->q[R];
+  if (c->cfg.poly3) {
+    /* POL-MOOD3: p3 at the Gauss point of face f (Sec. 3.1 (iv)) */
+    double xs, ys;
+    qreal xq, yq;
+    face_point(f, c->cfg.dim == 2 ? (qreal)c->gq[q][gi] : 0, &xq, &yq);
+    xs = (double)xq;
+    ys = (double)yq;
+    for (int v = 0; v < NV; ++v) {
+      double qv[MAXN];
+      for (int m = 0; m < n; ++m)
+        qv[m] = Xg[gidx(c, v, i + c->off[R][2 * m], j + c->off[R][2 * m + 1])];
+      Us[v] = orc_poly3_eval(c->cfg.dim, qv, xs, ys);
+    }
+    return;
+  }
   const double* z = c->z[R] + (size_t)(f * q + gi) * n;
   for (int v = 0; v < NV; ++v) {
     double s = 0.0;
@@ -690,6 +746,10 @@ static double curvature(const orc_ctx* c, const double* Xg, int d, int i, int j)
   double s = 0.0;
   for (int m = 0; m < n; ++m) s += w[m] * Xv(c, Xg, 0, i + c->off1[2 * m], j + c->off1[2 * m + 1]);
   return s;
+}
+
+double orc_curvature(orc_ctx* c, const double* Xg, int d, int i, int j) {
+  return curvature(c, Xg, d, i, j);
 }
 
 int orc_detect_cell(orc_ctx* c, const double* Xg, int i, int j, const double* Y4) {

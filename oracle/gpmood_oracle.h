@@ -70,6 +70,9 @@ typedef struct {
   int riemann;           /* 0: HLLC (Toro et al. 1994); 1: HLL (Harten, Lax, van Leer 1983) */
   double jet_x0, jet_x1; /* inflow slit of the JET kind */
   double jet_prim[2][4]; /* jet state (rho, u, v, p) on the S and N sides */
+  int poly3;             /* 1: POL-MOOD3 (Sec. 3.1 (iv)): the R = 1 rung is Poly3
+                            (eq. poly3, App. C) instead of GP-R1, and the u2 curvatures
+                            are the second derivatives of p3; cascade must be {1, 0} */
 } orc_config;
 
 typedef struct orc_ctx orc_ctx;
@@ -101,6 +104,10 @@ int orc_gp_weights(int dim, int R, double lamx, double lamy, double* z, int* nq,
 int orc_gp_weights_raw(int dim, int R, double lamx, double lamy, double* z);
 /* App. B second-derivative weights at the cell centre on the R=1 stencil */
 int orc_d2_weights(int dim, double ell, double dx, double dy, double* wxx, double* wyy);
+/* Poly3 (eq. poly3 with the App. C coefficients) of the cell whose R = 1
+   stencil values, in orc_stencil order, are qv, evaluated at (xs, ys) in cell
+   units from the cell centre; dim 1 reads the data as constant in y */
+double orc_poly3_eval(int dim, const double* qv, double xs, double ys);
 
 /* --- scheme --- */
 /* HLLC flux between pointwise states UL, UR across an x (dir 0) or y (dir 1) face */
@@ -124,6 +131,9 @@ int orc_stage(orc_ctx* ctx, const double* X, double ts, double dt, double* Y,
 /* detection of one cell (Steps 4-9) given the ghosted stage input X and the
    candidate Y4 of that cell; returns an ORC_ACCEPT_* or ORC_FAIL_* code */
 int orc_detect_cell(orc_ctx* ctx, const double* Xg, int i, int j, const double* Y4);
+/* the u2 curvature (eq. u2_curvature) of the density of ghosted state Xg at
+   interior cell (i, j) along direction d (0: x, 1: y), physical units */
+double orc_curvature(orc_ctx* ctx, const double* Xg, int d, int i, int j);
 /* ghost fill of an interior array into a ghosted array at time t */
 int orc_fill_ghosts(orc_ctx* ctx, const double* U, double t, double* Xg);
 

@@ -16,6 +16,8 @@ Problems (sizes are arguments; the defaults are the paper-shaped workloads):
   vortex          isentropic vortex (Sec. 5.1, eqs. vortex_IC_*) on a square
   density_wave    smooth density wave, an exact translation
   dmr             Mach-10 double Mach reflection (Sec. 5.2.3)
+  shu_osher       Shu-Osher shock tube, 1D (Sec. 5.2.1)
+  mach_jet, double_mach_jet   the Mach 100 and Mach 800 jets (Sec. 5.3)
   quadrants       four-quadrant Riemann problem with seeded random states
   shear_layer     smooth periodic double shear layer with a seeded random field
 """
@@ -253,6 +255,59 @@ def double_mach_jet(n=600, R=3, ell_cells=12.0, cascade=None):
         jet_prim=[[gamma, 0.0, 800.0, 1.0], [gamma, 0.0, -800.0, 1.0]],
         riemann="hll", cascade=cascade or ([R, 1, 0] if R > 1 else [1, 0]),
         ell=ell_cells * dx, t_end=0.005, U0=U,
+    )
+
+
+# The paper's four schemes (Sec. 3.1): cascade, reconstruction and time
+# integrator.  GP-MOOD5/7 step with SSP-RK4 and a time step reduced by
+# Delta^((2R+1)/4 - 1) (Sec. 5.1 b); GP-MOOD3 and POL-MOOD3 with SSP-RK3.
+SCHEMES = {
+    "GP-MOOD3": dict(cascade=[1, 0], recon="gp", rk=3),
+    "GP-MOOD5": dict(cascade=[2, 1, 0], recon="gp", rk=4),
+    "GP-MOOD7": dict(cascade=[3, 1, 0], recon="gp", rk=4),
+    "POL-MOOD3": dict(cascade=[1, 0], recon="poly3", rk=3),
+}
+
+
+def scheme_cfl(name, delta, cfl=0.8, reduce=True):
+    """CFL number of a scheme: cfl, times Delta^((2R+1)/4 - 1) for the
+    SSP-RK4 schemes when reduce is set."""
+    sch = SCHEMES[name]
+    if sch["rk"] != 4 or not reduce:
+        return cfl
+    R = sch["cascade"][0]
+    return cfl * delta ** ((2 * R + 1) / 4.0 - 1.0)
+
+
+def shu_osher(n=256, scheme="GP-MOOD7", ell_cells=6.0, csd_on=1, reduce_dt=True):
+    """Shu-Osher shock tube (Sec. 5.2.1) on [0, 9], 1D: a Mach 3 shock at
+    x = 0.5, (rho, u, p) = (3.857143, 2.629369, 10.33333) behind it, and
+    (1 + 0.2 sin(5 (x - 4.5)), 0, 1) ahead; t_end 1.8, ell = 6 Delta.  The
+    left end holds the post-shock state (fixed inflow).  The right end is
+    zero-gradient: ahead of the shock the gas is at rest at uniform pressure,
+    a state whose face fluxes do not depend on the density, and the shock
+    stays short of x = 9 up to t_end, so this equals holding the initial
+    values there."""
+    gamma = 1.4
+    left = [3.857143, 2.629369, 0.0, 10.33333]
+
+    def prim(x, y):
+        behind = x < 0.5
+        rho = np.where(behind, left[0], 1.0 + 0.2 * np.sin(5.0 * (x - 4.5)))
+        u = np.where(behind, left[1], 0.0)
+        p = np.where(behind, left[3], 1.0)
+        return rho, u, np.zeros_like(x), p
+
+    dx = 9.0 / n
+    U = cell_average(prim, n, 1, 0.0, 9.0, 0.0, dx, gamma, dim=1)
+    sch = SCHEMES[scheme]
+    return _problem(
+        name=f"shuosher_{n}_{scheme}", dim=1, nx=n, ny=1, x0=0.0, x1=9.0, y0=0.0, y1=dx,
+        bc=["dirichlet", "outflow", "outflow", "outflow"],
+        bc_prim=[left, [1.0, 0.0, 0.0, 1.0], [1.0, 0.0, 0.0, 1.0], [1.0, 0.0, 0.0, 1.0]],
+        cascade=list(sch["cascade"]), recon=sch["recon"], rk=sch["rk"],
+        cfl=scheme_cfl(scheme, dx, reduce=reduce_dt), csd_on=csd_on,
+        ell=ell_cells * dx, t_end=1.8, U0=U,
     )
 
 
