@@ -36,10 +36,28 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 128 FFMA/clk/SM
 HLLC_FLOPS = 78  # per pointwise HLLC flux, divisions and square roots counted once
 
 
-def workload(n):
+# --scheme: the default is the benchmark workload (GP-R3 cascade); the others
+# time the third-order schemes of Sec. 3.1 on the same vortex
+SCHEME_DESC = {
+    "GP-R3": ("GP-R3 cascade 7->5->3->1", 3),
+    "GP-MOOD3": ("GP-MOOD3 (GP-R1 -> FOG)", 1),
+    "POL-MOOD3": ("POL-MOOD3 (Poly3 -> FOG)", 1),
+}
+
+
+def workload(n, scheme="GP-R3"):
     from paper_2110_08683_gb300 import inputs as I
 
-    return I.vortex(n=n, R=3)
+    if scheme == "GP-R3":
+        return I.vortex(n=n, R=3)
+    p = I.vortex(n=n, R=1, cascade=[1, 0])
+    p["recon"] = "poly3" if scheme == "POL-MOOD3" else "gp"
+    return p
+
+
+def workload_name(n, scheme):
+    return (f"isentropic vortex {n}^2 periodic [-5,5]^2, {SCHEME_DESC[scheme][0]}, ell=0.5, "
+            f"SSP-RK3, CFL 0.8, HLLC")
 
 
 def faces_flops_per_face(R=3):
@@ -66,9 +84,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision):
+def ncu_traffic(precision, scheme="GP-R3"):
     """DRAM bytes per launch of the x-face kernel from the committed ncu
-    summary, or None when the kernel sources changed since the capture."""
+    summary, or None when the kernel sources changed since the capture.  Rows
+    of the default workload are keyed by the precision alone, the others by
+    precision and scheme ("fp64 POL-MOOD3")."""
+    key = precision if scheme == "GP-R3" else f"{precision} {scheme}"
     path = os.path.join(ROOT, "profiles", "faces_x_traffic.md")
     try:
         lines = open(path).read().splitlines()
@@ -77,7 +98,7 @@ def ncu_traffic(precision):
     # table rows: | precision | kernel sources sha256 | DRAM bytes per launch | ...
     for ln in lines:
         cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) >= 3 and cells[0] == precision:
+        if len(cells) >= 3 and cells[0] == key:
             if cells[1] != kernel_source_hash():
                 return None
             try:
@@ -190,12 +211,12 @@ def job_rate(units, ms, world):
     return total / (ms_max / 1e3), ms_max
 
 
-def cpu_baseline(n, steps=2):
+def cpu_baseline(n, steps=2, scheme="GP-R3"):
     """The FP64 CPU oracle as it stands, single thread, on a bounded sample:
     `steps` full SSP-RK3 steps of the same workload."""
     import oracle as O
 
-    p = workload(n)
+    p = workload(n, scheme)
     o = O.Oracle(p)
     U = p["U0"]
     t0 = time.perf_counter()
@@ -217,7 +238,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(0 if world > 1 else local)
     dev_index = local
     n = args.n
-    p = workload(n)
+    p = workload(n, args.scheme)
+    R = SCHEME_DESC[args.scheme][1]
     g = gp.GPMood(p, args.precision, eager=args.eager)
     stream = torch.cuda.Stream()
     g.set_stream(stream.cuda_stream)
@@ -287,14 +309,14 @@ def run_ours(args, world, rank, local):
     fx_ms, fx_n = kt["faces_x"] if prof else (0.0, 0)
     per_launch_s = fx_ms / 1e3 / max(fx_n, 1)
     faces = (n + 1) * n
-    flops = faces * faces_flops_per_face(3)
+    flops = faces * faces_flops_per_face(R)
     real64 = args.precision == "fp64"
     peak = FP64_PEAK_TFLOPS if real64 else FP32_PEAK_TFLOPS
     achieved = flops / per_launch_s / 1e12 if prof else 0.0
     roofline = None if not prof else {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": ncu_traffic(args.precision),
-                "kernel": "k_faces<R=3,%s,x>" % ("double" if real64 else "float"),
+                "traffic": ncu_traffic(args.precision, args.scheme),
+                "kernel": "k_faces<R=%d,%s,x>" % (R, "double" if real64 else "float"),
                 "flops_per_launch": flops, "launch_ms": round(per_launch_s * 1e3, 4),
                 "peak_source": "derived: 152 SMs x %s/clk x 2.07 GHz (of nominal; measured DFMA "
                                "1.19 TFLOP/s, FFMA 69.9 TFLOP/s)" % ("4 FP64 flop" if real64
@@ -310,8 +332,7 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if real64 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": f"isentropic vortex {n}^2 periodic [-5,5]^2, GP-R3 cascade "
-                               f"7->5->3->1, ell=0.5, SSP-RK3, CFL 0.8, HLLC",
+        "config": {"workload": workload_name(n, args.scheme),
                    "cells": n * n, "precision": args.precision,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
         "roofline": roofline,
@@ -494,7 +515,7 @@ def run_reference(args, world, rank):
     import oracle as O
 
     n = args.n
-    p = workload(n)
+    p = workload(n, args.scheme)
     o = O.Oracle(p)
     U = p["U0"]
     t = 0.0
@@ -521,8 +542,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": k, "warmup": w, "ms_per_step": el * 1e3 / k, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"isentropic vortex {n}^2 periodic [-5,5]^2, GP-R3 cascade "
-                               f"7->5->3->1, ell=0.5, SSP-RK3, CFL 0.8, HLLC",
+        "config": {"workload": workload_name(n, args.scheme),
                    "cells": n * n, "precision": "fp64", "parallelism": "host, 1 thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -538,6 +558,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--scheme", default="GP-R3", choices=sorted(SCHEME_DESC),
+                    help="GP-R3: the benchmark workload; GP-MOOD3 / POL-MOOD3: the "
+                         "third-order schemes on the same vortex")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels one by one instead of the step graphs (for per-kernel "
@@ -570,7 +593,7 @@ def main():
     line["clocks"] = clocks
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.n)
+            line["cpu_baseline"] = cpu_baseline(args.n, scheme=args.scheme)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -101,6 +101,13 @@ typedef struct {
                            loop decision after each MOOD iteration.  Same kernels, same
                            results; slower, but visible kernel by kernel to profilers
                            that cannot look inside graphs with conditional nodes */
+  int recon;            /* 0: GP reconstruction (GP-MOOD).  1: POL-MOOD3 (Sec. 3.1 (iv)):
+                           the R = 1 rung is Poly3, the quadratic of eq. poly3 fitted to
+                           the five cell averages of the R = 1 stencil (eq. p3_coeffs),
+                           at the same Gauss points; the u2 curvatures are Poly3's
+                           second derivatives (the centred differences); ell is unused.
+                           Requires R_max = 1 (the cascade Poly3 -> FOG).  Single-problem
+                           handles and gpmood_step_noalloc */
 } gpmood_options;
 
 /* per-step diagnostics of the most recent step */

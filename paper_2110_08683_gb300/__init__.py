@@ -20,6 +20,7 @@ from . import build as _build
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3, "dmr_bottom": 4, "dmr_top": 5,
       "jet": 6}
 RIEMANN = {"hllc": 0, "hll": 1}
+RECON = {"gp": 0, "poly3": 1}  # poly3: POL-MOOD3 (Sec. 3.1 (iv)), R_max = 1
 FP64, FP32 = 0, 1
 
 E_CODES = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "device allocation failed",
@@ -51,7 +52,7 @@ class Options(C.Structure):
         ("ncascade", C.c_int), ("cascade", C.c_int * 4), ("precision", C.c_int),
         ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
         ("max_mood_iters", C.c_int), ("riemann", C.c_int), ("rk", C.c_int),
-        ("eager", C.c_int),
+        ("eager", C.c_int), ("recon", C.c_int),
     ]
 
 
@@ -159,6 +160,7 @@ def make_options(prob, precision=FP64, eager=False):
     o.max_mood_iters = int(prob.get("max_iters", 0))
     o.rk = int(prob.get("rk", 3))
     o.riemann = RIEMANN[prob.get("riemann", "hllc")]
+    o.recon = RECON[prob.get("recon", "gp")]
     o.eager = 1 if eager else 0
     return o
 

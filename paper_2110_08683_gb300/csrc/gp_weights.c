@@ -245,3 +245,144 @@ int gpw_second_derivative_1d(double dx, double ell, int* da, int* db, double* wx
   }
   return n;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Poly3 of POL-MOOD3 (Sec. 3.1 (iv), eq. poly3 and eq. p3_coeffs): the       */
+/* quadratic p = c0 + c1 x + c2 x^2 + c3 y + c4 y^2 whose means over the five  */
+/* cells of the R = 1 stencil equal their cell averages.  The xy monomial has  */
+/* zero mean on each of the five cells and cannot be fitted; it is left out.   */
+/* With M[m][k] the mean of monomial k over stencil cell m, p(x*) =            */
+/* phi(x*)^T M^{-1} qbar, so the weights at a point are z = M^{-T} phi(x*):   */
+/* one small solve per point, in binary128 (cell units, origin at the centre). */
+/* ------------------------------------------------------------------------- */
+
+/* Gaussian elimination with partial pivoting on A x = b (n x n, row-major,
+   both overwritten; x returned in b).  Returns -1 on a zero pivot. */
+static int gesv(int n, f128* A, f128* b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsf128(A[r * n + c]) > fabsf128(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0) return -1;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) {
+        f128 t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t;
+      }
+      f128 t = b[c]; b[c] = b[piv]; b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      f128 f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    for (int k = r + 1; k < n; ++k) b[r] -= A[r * n + k] * b[k];
+    b[r] /= A[r * n + r];
+  }
+  return 0;
+}
+
+/* the monomials 1, x, x^2, y, y^2 at a point, and their means over the unit
+   cell centred at (a, b); nk = 3 keeps the x monomials only (1D) */
+static void poly3_phi(f128 x, f128 y, f128* phi) {
+  phi[0] = 1; phi[1] = x; phi[2] = x * x; phi[3] = y; phi[4] = y * y;
+}
+static void poly3_means(f128 a, f128 b, f128* mu) {
+  const f128 v = 1.0F128 / 12; /* mean of s^2 over [-1/2, 1/2] */
+  mu[0] = 1; mu[1] = a; mu[2] = a * a + v; mu[3] = b; mu[4] = b * b + v;
+}
+
+/* z = M^{-T} rhs over the stencil cells cell[0..nk-1] (offsets a, b) */
+static int poly3_weights_at(int nk, const int* ca, const int* cb, const f128* rhs, f128* z) {
+  f128 MT[25];
+  for (int m = 0; m < nk; ++m) {
+    f128 mu[5];
+    poly3_means((f128)ca[m], (f128)cb[m], mu);
+    for (int k = 0; k < nk; ++k) MT[k * nk + m] = mu[k]; /* row k = monomial k */
+  }
+  for (int k = 0; k < nk; ++k) z[k] = rhs[k];
+  if (gesv(nk, MT, z) != 0) return -1;
+  /* the exact weights are small rationals; where one is zero the elimination
+     leaves binary128 round-off, which is cleared */
+  f128 big = 0;
+  for (int k = 0; k < nk; ++k) big = fabsf128(z[k]) > big ? fabsf128(z[k]) : big;
+  for (int k = 0; k < nk; ++k)
+    if (fabsf128(z[k]) < 1e-25F128 * big) z[k] = 0;
+  return 0;
+}
+
+int gpw_poly3(gpw_radius* out) {
+  memset(out, 0, sizeof(*out));
+  int n = gpw_stencil(1, out->da, out->db);
+  int q = 2; /* the two-point Gauss rule of the R = 1 faces */
+  out->n = n;
+  out->q = q;
+  f128 gq[4], wq[4];
+  gauss_q(q, gq, wq);
+  for (int face = 0; face < 2; ++face)
+    for (int k = 0; k < q; ++k) {
+      f128 xs = face == 0 ? 0.5F128 : gq[k];
+      f128 ys = face == 0 ? gq[k] : 0.5F128;
+      f128 phi[5], z[5];
+      poly3_phi(xs, ys, phi);
+      if (poly3_weights_at(n, out->da, out->db, phi, z) != 0) return -2;
+      for (int m = 0; m < n; ++m) out->z[face][k][m] = (double)z[m];
+    }
+  for (int k = 0; k < q; ++k) {
+    out->g[k] = (double)gq[k];
+    out->w[k] = (double)wq[k];
+  }
+  return 0;
+}
+
+/* 1D: the quadratic c0 + c1 x + c2 x^2 on the cells a = -1, 0, 1, laid out
+   like gpw_solve_1d's R = 1 table (row b = 0, both Gauss slots the same
+   vector, Gauss weights (1/2, 1/2)) */
+int gpw_poly3_1d(gpw_radius* out) {
+  memset(out, 0, sizeof(*out));
+  int n = gpw_stencil(1, out->da, out->db);
+  out->n = n;
+  out->q = 2;
+  const int ca[3] = {-1, 0, 1}, cb[3] = {0, 0, 0};
+  f128 phi[5], z[5];
+  poly3_phi(0.5F128, 0, phi);
+  if (poly3_weights_at(3, ca, cb, phi, z) != 0) return -2;
+  for (int m = 0; m < n; ++m) {
+    double zm = out->db[m] == 0 ? (double)z[out->da[m] + 1] : 0.0;
+    out->z[0][0][m] = out->z[0][1][m] = zm;
+  }
+  f128 gq[4], wq[4];
+  gauss_q(2, gq, wq);
+  for (int k = 0; k < 2; ++k) {
+    out->g[k] = (double)gq[k];
+    out->w[k] = 0.5;
+  }
+  return 0;
+}
+
+/* u2 curvatures of POL-MOOD3 (eq. u2_curvature): the second derivatives of
+   Poly3 at the cell centre, d^2 p / dx^2 = 2 c2 and d^2 p / dy^2 = 2 c4, in
+   physical units, as weights z = M^{-T} phi'' on the 5-point R = 1 table;
+   one_d: the 3-cell fit, wyy zero */
+int gpw_second_derivative_poly3(int one_d, double dx, double dy, int* da, int* db,
+                                double* wxx, double* wyy) {
+  int n = gpw_stencil(1, da, db);
+  f128 rx[5] = {0, 0, 2, 0, 0}, ry[5] = {0, 0, 0, 0, 2}, zx[5], zy[5];
+  if (one_d) {
+    const int ca[3] = {-1, 0, 1}, cb[3] = {0, 0, 0};
+    if (poly3_weights_at(3, ca, cb, rx, zx) != 0) return -2;
+    for (int m = 0; m < n; ++m) {
+      wxx[m] = db[m] == 0 ? (double)(zx[da[m] + 1] / ((f128)dx * dx)) : 0.0;
+      wyy[m] = 0.0;
+    }
+    return n;
+  }
+  if (poly3_weights_at(n, da, db, rx, zx) != 0) return -2;
+  if (poly3_weights_at(n, da, db, ry, zy) != 0) return -2;
+  for (int m = 0; m < n; ++m) {
+    wxx[m] = (double)(zx[m] / ((f128)dx * dx));
+    wyy[m] = (double)(zy[m] / ((f128)dy * dy));
+  }
+  return n;
+}

@@ -31,6 +31,17 @@ int gpw_solve_1d(int R, double dx, double ell, gpw_radius* out);
 int gpw_second_derivative_1d(double dx, double ell, int* da, int* db, double* wxx,
                              double* wyy);
 
+/* POL-MOOD3 (Sec. 3.1 (iv)): Poly3, the quadratic of eq. poly3 fitted to the
+   five cell averages of the R = 1 stencil (eq. p3_coeffs), evaluated at the
+   face Gauss points; the same layout as gpw_solve(1, ...).  Returns 0 or -2 */
+int gpw_poly3(gpw_radius* out);
+/* the 1D Poly3 (three cells) laid out like gpw_solve_1d(1, ...) */
+int gpw_poly3_1d(gpw_radius* out);
+/* POL-MOOD3's u2 curvature weights: Poly3's second derivatives at the cell
+   centre, physical units, on the 5-point table; returns 5 or -2 */
+int gpw_second_derivative_poly3(int one_d, double dx, double dy, int* da, int* db,
+                                double* wxx, double* wyy);
+
 #ifdef __cplusplus
 }
 #endif

@@ -581,6 +581,8 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
   if (o.rk != 0 && o.rk != 3 && o.rk != 4) return GPMOOD_E_INVAL;
   if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
+  if (o.recon != 0 && o.recon != 1) return GPMOOD_E_INVAL;
+  if (o.recon == 1 && R_max != 1) return GPMOOD_E_INVAL;  // POL-MOOD3: Poly3 -> FOG
 
   gpmood_t h = new (std::nothrow) gpmood_s;
   if (!h) return GPMOOD_E_OOM;
@@ -639,14 +641,17 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
                                       : 64 + 4 * (grid->nx > grid->ny ? grid->nx : grid->ny);
 
-  // GP weights of every radius of the cascade, binary128 -> double / float
+  // weights of every radius of the cascade, binary128 -> double / float:
+  // GP, or Poly3 on the R = 1 rung of POL-MOOD3
+  const bool poly3 = o.recon == 1;
   gpw_radius wr[4];
   memset(wr, 0, sizeof(wr));
   for (int k = 0; k < nc; ++k) {
     int R = cascade[k];
     if (R == 0) continue;
-    const int rc = one_d ? gpw_solve_1d(R, g.dx, ell, &wr[R])
-                         : gpw_solve(R, g.dx, g.dy, ell, &wr[R]);
+    int rc;
+    if (poly3) rc = one_d ? gpw_poly3_1d(&wr[R]) : gpw_poly3(&wr[R]);
+    else rc = one_d ? gpw_solve_1d(R, g.dx, ell, &wr[R]) : gpw_solve(R, g.dx, g.dy, ell, &wr[R]);
     if (rc != 0) {
       delete h;
       return GPMOOD_E_WEIGHTS;
@@ -654,8 +659,10 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   }
   int da[25], db[25];
   double d2x[25], d2y[25];
-  const int nd2 = one_d ? gpw_second_derivative_1d(g.dx, ell, da, db, d2x, d2y)
-                        : gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y);
+  const int nd2 =
+      poly3 ? gpw_second_derivative_poly3(one_d ? 1 : 0, g.dx, g.dy, da, db, d2x, d2y)
+      : one_d ? gpw_second_derivative_1d(g.dx, ell, da, db, d2x, d2y)
+              : gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y);
   if (nd2 != 5) {
     delete h;
     return GPMOOD_E_WEIGHTS;
@@ -1073,6 +1080,8 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
   if (o.rk == 4) return GPMOOD_E_INVAL;  // SSP-RK3 only: the scratch holds three states
   if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
+  if (o.recon != 0 && o.recon != 1) return GPMOOD_E_INVAL;
+  if (o.recon == 1 && R_max != 1) return GPMOOD_E_INVAL;
 
   // the temporary handle lives on the host stack
   gpmood_s hs;
@@ -1151,11 +1160,14 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   for (int k = 0; k < nc; ++k) {
     int R = cascade[k];
     if (R == 0) continue;
-    if (gpw_solve(R, g.dx, g.dy, ell, &wr[R]) != 0) return GPMOOD_E_WEIGHTS;
+    const int rc = o.recon == 1 ? gpw_poly3(&wr[R]) : gpw_solve(R, g.dx, g.dy, ell, &wr[R]);
+    if (rc != 0) return GPMOOD_E_WEIGHTS;
   }
   int da[25], db[25];
   double d2x[25], d2y[25];
-  if (gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y) != 5) return GPMOOD_E_WEIGHTS;
+  const int nd2 = o.recon == 1 ? gpw_second_derivative_poly3(0, g.dx, g.dy, da, db, d2x, d2y)
+                               : gpw_second_derivative(g.dx, g.dy, ell, da, db, d2x, d2y);
+  if (nd2 != 5) return GPMOOD_E_WEIGHTS;
   fill_weights<double>(wr, R_max, d2x, d2y, h->pw64, h->dw64);
   fill_weights<float>(wr, R_max, d2x, d2y, h->pw32, h->dw32);
 

@@ -526,6 +526,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
   if (o.rk != 0 && o.rk != 3) return GPMOOD_E_INVAL;  // batches step with SSP-RK3
   if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
+  if (o.recon != 0) return GPMOOD_E_INVAL;  // GP reconstruction only
   const int H = R_max + 1 > 2 ? R_max + 1 : 2;
   const int minn = H > 3 ? H : 3;
   // every problem shares the weights: the same ell/dx and ell/dy
