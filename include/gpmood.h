@@ -160,8 +160,30 @@ int gpmood_step(gpmood_t h, double cfl, double* dt_out);
 /* The same with a given Delta t (> 0) instead of the CFL rule. */
 int gpmood_step_dt(gpmood_t h, double dt);
 
-/* Step until t_end, clipping the last step; the step count goes to nsteps_out. */
+/* Step until t_end, clipping the last step; the step count goes to nsteps_out.
+   Graph handles queue the steps in chunks and wait once per chunk; steps
+   queued past t_end do nothing (see gpmood_step_async). */
 int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out);
+
+/*
+ * Queue one step like gpmood_step(h, cfl, NULL) on the handle's stream and
+ * return without waiting for it or reading anything back.  Each captured
+ * step graph opens with a gate: once a step has failed (GPMOOD_E_DT,
+ * GPMOOD_E_MOOD_CAP) the queued steps after it do nothing, so the steps
+ * that ran are always a prefix of those queued.  The failure is reported by
+ * the next gpmood_sync (or gpmood_step / gpmood_run); a failed step leaves
+ * the time and the step count where they were.  Every call that reads the
+ * state, the time or the flags waits for the queued steps first.  Eager and
+ * profiled handles step synchronously here.
+ */
+int gpmood_step_async(gpmood_t h, double cfl);
+
+/* Wait for the queued steps; GPMOOD_OK or the latched step error. */
+int gpmood_sync(gpmood_t h);
+
+/* Kernels launched by the handle's steps since the state was set, counted
+   on the device (queued steps included, after waiting for them). */
+int gpmood_launch_count(gpmood_t h, long long* count);
 
 /*
  * Diagnostics of the last step (waits).  order_out (nullable, host) receives

@@ -5,8 +5,9 @@ libgpmood.so (built in-tree by ``build.build()``).  There is no CPU fallback:
 loading fails loudly if the library is missing or no CUDA device is present.
 
 Function names follow the C ABI (gpmood_create, gpmood_set_state,
-gpmood_get_state, gpmood_step, gpmood_step_dt, gpmood_run, gpmood_flags,
-gpmood_destroy, gpmood_strerror); ``GPMood`` wraps a handle.
+gpmood_get_state, gpmood_step, gpmood_step_dt, gpmood_run, gpmood_step_async,
+gpmood_sync, gpmood_launch_count, gpmood_flags, gpmood_destroy,
+gpmood_strerror); ``GPMood`` wraps a handle.
 """
 from __future__ import annotations
 
@@ -89,6 +90,9 @@ def load(build_if_missing=True):
     L.gpmood_step.argtypes = [p, d, C.POINTER(d)]
     L.gpmood_step_dt.argtypes = [p, d]
     L.gpmood_run.argtypes = [p, d, d, C.POINTER(C.c_longlong)]
+    L.gpmood_step_async.argtypes = [p, d]
+    L.gpmood_sync.argtypes = [p]
+    L.gpmood_launch_count.argtypes = [p, C.POINTER(C.c_longlong)]
     L.gpmood_flags.argtypes = [p, p, p, C.POINTER(Stats)]
     L.gpmood_destroy.argtypes = [p]
     L.gpmood_strerror.argtypes = [i]
@@ -213,6 +217,20 @@ def gpmood_run(h, t_end, cfl):
     return n.value
 
 
+def gpmood_step_async(h, cfl):
+    _check(load().gpmood_step_async(h, cfl), "gpmood_step_async")
+
+
+def gpmood_sync(h):
+    _check(load().gpmood_sync(h), "gpmood_sync")
+
+
+def gpmood_launch_count(h):
+    n = C.c_longlong(0)
+    _check(load().gpmood_launch_count(h, C.byref(n)), "gpmood_launch_count")
+    return n.value
+
+
 def gpmood_flags(h, nx, ny, maps=True, nstages=3):
     """final radii and first-pass troubled maps [S][ny][nx] and the stats of
     the last step (S = 3 for SSP-RK3, 5 for SSP-RK4)"""
@@ -320,6 +338,16 @@ class GPMood:
 
     def run(self, t_end, cfl=None):
         return gpmood_run(self.h, t_end, self.prob["cfl"] if cfl is None else cfl)
+
+    def step_async(self, cfl=None):
+        """queue one step without waiting (errors surface at sync())"""
+        gpmood_step_async(self.h, self.prob["cfl"] if cfl is None else cfl)
+
+    def sync(self):
+        gpmood_sync(self.h)
+
+    def launch_count(self):
+        return gpmood_launch_count(self.h)
 
     @property
     def nstages(self):

@@ -64,10 +64,31 @@ __global__ void k_dt_finalize(Scalars* sc) {
   sc->count[0] = sc->count[1] = 0;
 }
 
-__global__ void k_finish_step(Scalars* sc) {
+// end of a step: a failed step (non-finite dt, MOOD cap) leaves the time and
+// the step count where they were.  `base` is the step's launch count without
+// the MOOD iterations (4 kernels each), added to the running count.
+__global__ void k_finish_step(Scalars* sc, int base) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  sc->t += sc->dt;
-  sc->nsteps += 1;
+  if (sc->err == 0) {
+    sc->t += sc->dt;
+    sc->nsteps += 1;
+  }
+  long long n = base;
+  for (int s = 0; s < 5; ++s) n += 4 * sc->iters[s];
+  sc->launches += n;
+}
+
+// gate of an asynchronous graph step: the step runs while no error is latched
+// and, for a clipped run, while t < t_end (the host's own loop test).  Once
+// closed the gate stays closed for the following steps, so the steps that ran
+// are always a prefix of those launched.
+__global__ void k_step_gate(Scalars* sc, cudaGraphConditionalHandle hif) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Control c = sc->ctl;
+  bool go = sc->err == 0;
+  if (c.clip && !(sc->t < c.t_end * (1.0 - 1e-14))) go = false;
+  if (!go) sc->launches += 1;  // the gate alone
+  cudaGraphSetConditional(hif, go ? 1u : 0u);
 }
 
 

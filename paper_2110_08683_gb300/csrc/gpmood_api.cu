@@ -51,8 +51,17 @@ struct gpmood_s {
   // captured step graphs [buffer rotation][profiled] and their streams
   Control ctl;  // host copy of the step controls
   int eager;    // stream launches instead of the captured step graph
-  cudaStream_t cs, cs2;
+  cudaStream_t cs, cs2, cs3;   // capture streams: step, MOOD loop body, gated step body
   cudaGraphExec_t gexec[5][3];  // [rotation][plain, profiled, recording]
+  // asynchronous steps: plain step graphs open with a gate (an IF node), so
+  // steps can be queued without reading anything back; the host settles its
+  // buffer rotation from the device's step count when it next synchronises
+  int gated_ok;              // 0 not yet known, 1 plain graphs gated, -1 gating unavailable
+  int pend;                  // steps queued since the last settle
+  int sync_cur;              // rotation at the last settle
+  long long sync_nsteps;     // device step count at the last settle
+  Control ctl_dev;           // controls last copied to the device
+  int ctl_valid;
   cudaEvent_t gev[64];
   int gev_cls[32];
   int gev_n, gev_pairs;
@@ -111,6 +120,7 @@ void free_all(gpmood_t h) {
       if (h->gexec[r][p]) cudaGraphExecDestroy(h->gexec[r][p]);
   if (h->cs) cudaStreamDestroy(h->cs);
   if (h->cs2) cudaStreamDestroy(h->cs2);
+  if (h->cs3) cudaStreamDestroy(h->cs3);
   void* adj[] = {h->aX, h->aXr, h->aG, h->av, h->aw, h->amu, h->ax.L, h->ax.R, h->ax.K,
                  h->ay.L, h->ay.R, h->ay.K, h->aord};
   for (void* p : adj) cudaFree(p);
@@ -219,6 +229,37 @@ int pull_scalars(gpmood_t h) {
   return 0;
 }
 
+// the host's view after a step it waited for
+void mark_synced(gpmood_t h) {
+  h->sync_cur = h->cur;
+  h->sync_nsteps = h->hsc->nsteps;
+  h->pend = 0;
+}
+
+int step_error(gpmood_t h);
+int step_launches(const Scalars& s, int nstages, int gated);
+
+// wait for the queued asynchronous steps and settle the buffer rotation: the
+// steps that ran are a prefix of those queued (the gate closes for good), and
+// every successful one advanced the device's step count, so the rotation is
+// the one at the last settle advanced by that count.  A failed step leaves
+// the rotation, the time and the count where they were.  Returns a CUDA
+// error only; a step error stays latched in the device scalars and in
+// last_status.
+int settle(gpmood_t h) {
+  if (!h->pend) return 0;
+  int rc = pull_scalars(h);
+  if (rc) return rc;
+  const long long m = h->hsc->nsteps - h->sync_nsteps;
+  const int nb = h->sch.nbuf;
+  h->cur = (int)((h->sync_cur + (m % nb) * h->sch.advance) % nb);
+  h->launches = step_launches(*h->hsc, h->sch.nstages, 1);
+  mark_synced(h);
+  const int e = step_error(h);
+  h->last_status = e;
+  return 0;
+}
+
 void write_control(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
                    double* tape = nullptr, uint8_t* otape = nullptr) {
   h->ctl.tape = tape;
@@ -234,13 +275,22 @@ int push_control(gpmood_t h) {
   // pageable source: staged by the driver at the call, so the host copy may
   // change right after
   CK(cudaMemcpyAsync(&h->sc->ctl, &h->ctl, sizeof(Control), cudaMemcpyHostToDevice, h->stream));
+  h->ctl_dev = h->ctl;
+  h->ctl_valid = 1;
   return 0;
 }
 
-// kernels launched by one step: dt (2), per stage fill, faces x/y, update,
-// begin (5), 4 per MOOD iteration, finish (1)
-int step_launches(const Scalars& s, int nstages) {
-  int n = 2 + nstages * 5 + 1;
+// the same, skipped when the device already holds these controls
+int push_control_if_changed(gpmood_t h) {
+  if (h->ctl_valid && memcmp(&h->ctl_dev, &h->ctl, sizeof(Control)) == 0) return 0;
+  return push_control(h);
+}
+
+// kernels launched by one step: the gate of a gated graph (1), dt (2), per
+// stage fill, faces x/y, update, begin (5), 4 per MOOD iteration, finish (1)
+int step_base_launches(int nstages, int gated) { return (gated ? 1 : 0) + 2 + nstages * 5 + 1; }
+int step_launches(const Scalars& s, int nstages, int gated) {
+  int n = step_base_launches(nstages, gated);
   for (int k = 0; k < nstages; ++k) n += 4 * s.iters[k];
   return n;
 }
@@ -328,11 +378,12 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     if (otape) CK(cudaMemcpyAsync(otape + s * nc, h->ord + s * nc, nc, cudaMemcpyDeviceToDevice,
                                   h->stream));
   }
-  CK(launch_finish(h->sc, h->stream));
+  CK(launch_finish(h->sc, step_base_launches(h->sch.nstages, 0), h->stream));
   rc = pull_scalars(h);
   if (rc) return rc;
-  h->launches = step_launches(*h->hsc, h->sch.nstages);
+  h->launches = step_launches(*h->hsc, h->sch.nstages, 0);
   h->cur = buf_of(h, a, h->sch.advance);
+  mark_synced(h);
   h->last_status = GPMOOD_OK;
   return GPMOOD_OK;
 }
@@ -350,8 +401,7 @@ void rec_event(gpmood_t h, int prof, int cls, int open, cudaStream_t st) {
 
 template <class Real>
 int capture_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const DirectW<Real>& D,
-                  int prof, int record) {
-  cudaStream_t st = h->cs;
+                  int prof, int record, cudaStream_t st) {
   StageArgs<Real> A = stage_args<Real>(h, s, rot);
   const int ix = buf_of(h, rot, h->sch.st[s].in);
   if (record) {
@@ -409,20 +459,69 @@ int capture_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const Dire
   return 0;
 }
 
-int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out) {
+// capture the step graph of rotation `cur`.  Plain graphs (gated = 1) put
+// the whole step inside an IF node opened by k_step_gate, so that queued
+// steps after an error or past t_end do nothing; profiled and recording
+// graphs (read back after every step) have no gate.
+int capture_step_impl(gpmood_t h, int cur, int prof, int record, int gated,
+                      cudaGraphExec_t* out) {
   const int a = cur;
   cudaStream_t st = h->cs;
   h->gev_n = 0;
   CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int rc = 0;
-  rec_event(h, prof, GPMOOD_K_DT, 1, st);
-  if (launch_dt(h->U[a], h->Uf[a], h->g, h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
-  rec_event(h, prof, GPMOOD_K_DT, 0, st);
+  cudaStream_t bs = st;  // the stream the step body is captured on
+  cudaGraphNode_t ifnode = nullptr;
+  int body_open = 0;
+  if (gated) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t graph;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle hif;
+    cudaGraphNodeParams cp = {};
+    if (cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, nullptr, nullptr, nullptr) !=
+            cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&hif, graph, 0, cudaGraphCondAssignDefault) !=
+            cudaSuccess ||
+        launch_gate(h->sc, hif, st) != cudaSuccess ||
+        cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, &deps, nullptr, &ndeps) !=
+            cudaSuccess) {
+      rc = GPMOOD_E_CUDA;
+    } else {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = hif;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      if (cudaGraphAddNode(&ifnode, graph, deps, nullptr, ndeps, &cp) != cudaSuccess ||
+          cudaStreamBeginCaptureToGraph(h->cs3, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                        0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        rc = GPMOOD_E_CUDA;
+      else {
+        bs = h->cs3;
+        body_open = 1;
+      }
+    }
+  }
+  if (!rc) {
+    rec_event(h, prof, GPMOOD_K_DT, 1, bs);
+    if (launch_dt(h->U[a], h->Uf[a], h->g, h->sc, bs) != cudaSuccess) rc = GPMOOD_E_CUDA;
+    rec_event(h, prof, GPMOOD_K_DT, 0, bs);
+  }
   for (int s = 0; s < h->sch.nstages && !rc; ++s)
     rc = h->precision == GPMOOD_FP32
-             ? capture_stage<float>(h, s, a, h->pw32, h->dw32, prof, record)
-             : capture_stage<double>(h, s, a, h->pw64, h->dw64, prof, record);
-  if (!rc && launch_finish(h->sc, st) != cudaSuccess) rc = GPMOOD_E_CUDA;
+             ? capture_stage<float>(h, s, a, h->pw32, h->dw32, prof, record, bs)
+             : capture_stage<double>(h, s, a, h->pw64, h->dw64, prof, record, bs);
+  if (!rc && launch_finish(h->sc, step_base_launches(h->sch.nstages, gated), bs) != cudaSuccess)
+    rc = GPMOOD_E_CUDA;
+  if (body_open) {
+    cudaGraph_t tmp = nullptr;
+    if (cudaStreamEndCapture(h->cs3, &tmp) != cudaSuccess) rc = rc ? rc : GPMOOD_E_CUDA;
+    if (!rc && cudaStreamUpdateCaptureDependencies(st, &ifnode, nullptr, 1,
+                                                   cudaStreamSetCaptureDependencies) !=
+                   cudaSuccess)
+      rc = GPMOOD_E_CUDA;
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(st, &graph);
   if (!rc && ee != cudaSuccess) rc = GPMOOD_E_CUDA;
@@ -434,19 +533,36 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
   return GPMOOD_OK;
 }
 
+int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out) {
+  const int want_gate = !prof && !record && h->gated_ok >= 0;
+  int rc = capture_step_impl(h, cur, prof, record, want_gate, out);
+  if (rc && want_gate && h->gated_ok == 0) {
+    // the driver refused the gated graph: plain graphs without the gate, and
+    // asynchronous steps run synchronously from now on
+    h->gated_ok = -1;
+    rc = capture_step_impl(h, cur, prof, record, 0, out);
+  }
+  if (!rc && want_gate) h->gated_ok = 1;
+  if (!rc) h->last_status = GPMOOD_OK;
+  return rc;
+}
+
 int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
                double* tape = nullptr, uint8_t* otape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
+  int rc = settle(h);
+  if (rc) return rc;
   if (h->eager) return do_step(h, cfl, fixed_dt, clip, t_end, tape, otape);
   const int record = tape ? 1 : 0;
   const int prof = (h->prof_on && !record) ? 1 : 0;
   cudaGraphExec_t& ge = h->gexec[h->cur][record ? 2 : prof];
   if (!ge) {
-    int rc = capture_step(h, h->cur, prof, record, &ge);
+    rc = capture_step(h, h->cur, prof, record, &ge);
     if (rc) return rc;
   }
+  const int gated = !record && !prof && h->gated_ok == 1;
   write_control(h, cfl, fixed_dt, clip, t_end, tape, otape);
-  int rc = push_control(h);
+  rc = push_control(h);
   if (rc) return rc;
   CK(cudaGraphLaunch(ge, h->stream));
   rc = pull_scalars(h);
@@ -466,11 +582,35 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     h->prof_n[GPMOOD_K_UPDATE] += 2 * S;
     for (int k = 0; k < S; ++k) h->prof_n[GPMOOD_K_MOOD] += 4 * s.iters[k];
   }
+  mark_synced(h);
   rc = step_error(h);
   if (rc) return rc;
-  h->launches = step_launches(*h->hsc, h->sch.nstages);
+  h->launches = step_launches(*h->hsc, h->sch.nstages, gated);
   h->cur = buf_of(h, h->cur, h->sch.advance);
+  mark_synced(h);
   h->last_status = GPMOOD_OK;
+  return GPMOOD_OK;
+}
+
+// queue one step without waiting (plain gated graphs).  Eager handles,
+// profiled steps and handles whose driver refused the gate step
+// synchronously instead.
+int graph_step_async(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end) {
+  if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
+  if (h->eager || h->prof_on || h->gated_ok < 0) return graph_step(h, cfl, fixed_dt, clip, t_end);
+  cudaGraphExec_t& ge = h->gexec[h->cur][0];
+  if (!ge) {
+    int rc = capture_step(h, h->cur, 0, 0, &ge);
+    if (rc) return rc;
+    if (h->gated_ok < 0) return graph_step(h, cfl, fixed_dt, clip, t_end);
+  }
+  write_control(h, cfl, fixed_dt, clip, t_end);
+  int rc = push_control_if_changed(h);
+  if (rc) return rc;
+  CK(cudaGraphLaunch(ge, h->stream));
+  // assume the step runs; settle() corrects the rotation if it did not
+  h->cur = buf_of(h, h->cur, h->sch.advance);
+  h->pend += 1;
   return GPMOOD_OK;
 }
 
@@ -499,8 +639,13 @@ cudaError_t launch_dt(const double* X, const float* Xf, const Grid& g, Scalars* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(Scalars* sc, cudaStream_t st) {
-  k_finish_step<<<1, 32, 0, st>>>(sc);
+cudaError_t launch_finish(Scalars* sc, int base, cudaStream_t st) {
+  k_finish_step<<<1, 32, 0, st>>>(sc, base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate(Scalars* sc, cudaGraphConditionalHandle hif, cudaStream_t st) {
+  k_step_gate<<<1, 32, 0, st>>>(sc, hif);
   return cudaGetLastError();
 }
 
@@ -712,7 +857,8 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
     return GPMOOD_E_CUDA;
   }
   bool evok = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&h->cs3, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 64 && evok; ++k) evok = cudaEventCreate(&h->gev[k]) == cudaSuccess;
   if (!evok) {
     free_all(h);
@@ -727,6 +873,8 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
 
 int gpmood_set_stream(gpmood_t h, void* stream) {
   if (!h) return GPMOOD_E_INVAL;
+  int rc = settle(h);  // queued steps finish on the old stream
+  if (rc) return rc;
   h->stream = (cudaStream_t)stream;
   return GPMOOD_OK;
 }
@@ -756,12 +904,18 @@ int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
   CK(cudaMemcpyAsync(h->sc, h->hsc, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->has_state = 1;
+  h->pend = 0;  // queued steps (if any) ran before the copies above
+  h->sync_cur = 0;
+  h->sync_nsteps = 0;
+  h->ctl_valid = 0;  // the device controls were zeroed with the scalars
   return GPMOOD_OK;
 }
 
 int gpmood_set_time(gpmood_t h, double t) {
   if (!h || !isfinite(t)) return GPMOOD_E_INVAL;
   if (!h->has_state) return GPMOOD_E_NOSTATE;
+  int rc = settle(h);
+  if (rc) return rc;
   CK(cudaMemcpyAsync(&h->sc->t, &t, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return GPMOOD_OK;
@@ -770,6 +924,8 @@ int gpmood_set_time(gpmood_t h, double t) {
 int gpmood_get_state(gpmood_t h, double* U, int on_device) {
   if (!h || !U) return GPMOOD_E_INVAL;
   if (!h->has_state) return GPMOOD_E_NOSTATE;
+  int rc = settle(h);
+  if (rc) return rc;
   const Grid& g = h->g;
   for (int v = 0; v < 4; ++v) {
     const double* src = h->U[h->cur] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
@@ -796,23 +952,71 @@ int gpmood_step_dt(gpmood_t h, double dt) {
   return graph_step(h, 1.0, dt, 0, 0.0);
 }
 
+int gpmood_step_async(gpmood_t h, double cfl) {
+  if (!h || !(cfl > 0.0)) return GPMOOD_E_INVAL;
+  return graph_step_async(h, cfl, 0.0, 0, 0.0);
+}
+
+int gpmood_sync(gpmood_t h) {
+  if (!h) return GPMOOD_E_INVAL;
+  if (!h->has_state) return GPMOOD_E_NOSTATE;
+  int rc = settle(h);
+  if (rc) return rc;
+  rc = pull_scalars(h);
+  if (rc) return rc;
+  return step_error(h);
+}
+
+int gpmood_launch_count(gpmood_t h, long long* count) {
+  if (!h || !count) return GPMOOD_E_INVAL;
+  if (!h->has_state) return GPMOOD_E_NOSTATE;
+  int rc = settle(h);
+  if (rc) return rc;
+  rc = pull_scalars(h);
+  if (rc) return rc;
+  *count = h->hsc->launches;
+  return GPMOOD_OK;
+}
+
+// steps clipped to t_end.  Graph handles queue them in chunks sized from the
+// last time step and wait once per chunk; the gate turns the steps queued
+// past t_end into no-ops.
 int gpmood_run(gpmood_t h, double t_end, double cfl, long long* nsteps_out) {
   if (!h || !(cfl > 0.0)) return GPMOOD_E_INVAL;
   if (!h->has_state) return GPMOOD_E_NOSTATE;
-  long long n = 0;
-  int rc = pull_scalars(h);
+  int rc = settle(h);
   if (rc) return rc;
-  while (h->hsc->t < t_end * (1.0 - 1e-14)) {
-    rc = graph_step(h, cfl, 0.0, 1, t_end);
+  rc = pull_scalars(h);
+  if (rc) return rc;
+  const long long n0 = h->hsc->nsteps;
+  const double stop = t_end * (1.0 - 1e-14);
+  while (h->hsc->t < stop) {
+    const double t = h->hsc->t, dt = h->hsc->dt;
+    long long est = 1;
+    if (dt > 0.0 && isfinite(dt)) est = (long long)ceil((t_end - t) / dt) + 1;
+    const int chunk = (int)(est < 1 ? 1 : (est > 64 ? 64 : est));
+    for (int k = 0; k < chunk; ++k) {
+      rc = graph_step_async(h, cfl, 0.0, 1, t_end);
+      if (rc) return rc;
+      // a step taken synchronously (eager or profiled handles) has updated
+      // the host scalars: stop at t_end as the device gate would
+      if (!h->pend && !(h->hsc->t < stop)) break;
+    }
+    rc = settle(h);
     if (rc) return rc;
-    ++n;
+    rc = pull_scalars(h);
+    if (rc) return rc;
+    rc = step_error(h);
+    if (rc) return rc;
   }
-  if (nsteps_out) *nsteps_out = n;
+  if (nsteps_out) *nsteps_out = h->hsc->nsteps - n0;
   return GPMOOD_OK;
 }
 
 int gpmood_flags(gpmood_t h, uint8_t* order_out, uint8_t* first_out, gpmood_stats* stats_out) {
   if (!h) return GPMOOD_E_INVAL;
+  int rc0 = settle(h);
+  if (rc0) return rc0;
   const size_t nc = (size_t)h->g.nx * h->g.ny;
   const size_t S = (size_t)h->sch.nstages;
   if (order_out) CK(cudaMemcpyAsync(order_out, h->ord, S * nc, cudaMemcpyDeviceToHost, h->stream));
@@ -848,6 +1052,8 @@ int gpmood_last_launches(gpmood_t h) { return h ? h->launches : 0; }
 
 int gpmood_profile(gpmood_t h, int enable) {
   if (!h) return GPMOOD_E_INVAL;
+  int rc = settle(h);
+  if (rc) return rc;
   CK(cudaStreamSynchronize(h->stream));
   h->prof_on = enable ? 1 : 0;
   if (enable)
@@ -901,11 +1107,13 @@ int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>
     CK(cudaMemcpyAsync(A.ord, otape + s * nc, nc, cudaMemcpyDeviceToDevice, h->stream));
     CK(LaunchA<Real>::frozen_stage(A, h->g, D, h->stream));
   }
-  CK(launch_finish(h->sc, h->stream));
+  CK(launch_finish(h->sc, 0, h->stream));  // replay steps are not in the launch count
   rc = pull_scalars(h);
   if (rc) return rc;
+  mark_synced(h);
   if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
   h->cur = buf_of(h, a, h->sch.advance);
+  mark_synced(h);
   return GPMOOD_OK;
 }
 
@@ -993,6 +1201,8 @@ extern "C" {
 int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
   if (!h || !otape || !(dt > 0.0) || h->g.dim != 2 || h->sch.nstages != 3) return GPMOOD_E_INVAL;
   if (!h->has_state) return GPMOOD_E_NOSTATE;
+  int rc = settle(h);
+  if (rc) return rc;
   return h->precision == GPMOOD_FP32 ? frozen_step<float>(h, otape, dt, h->dw32)
                                      : frozen_step<double>(h, otape, dt, h->dw64);
 }
@@ -1002,7 +1212,9 @@ int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, do
   if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0) || h->g.dim != 2 ||
       h->sch.nstages != 3 || h->g.riemann != 0)  // the reverse Riemann solver is HLLC's
     return GPMOOD_E_INVAL;
-  int rc = adj_buffers(h);
+  int rc = settle(h);
+  if (rc) return rc;
+  rc = adj_buffers(h);
   if (rc) return rc;
   return h->precision == GPMOOD_FP32
              ? step_adjoint<float>(h, tape, otape, dt, t, lam_in, lam_out, h->pw32, h->dw32)

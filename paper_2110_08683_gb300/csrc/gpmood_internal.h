@@ -57,6 +57,7 @@ struct Scalars {
   unsigned int stamp_cur;       // stamp of the cells in the current queue
   int iters[5], nbad_first[5], nbad_total[5], nfog_pad[5];  // per RK stage
   long long nsteps;
+  long long launches;           // kernels launched by graph steps since the state was set
   int nactive;                  // batches: problems still advancing in this step
 };
 

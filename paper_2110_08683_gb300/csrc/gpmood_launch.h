@@ -56,7 +56,8 @@ cudaError_t launch_fill(double* X, float* Xf, const Grid& g, const Scalars* sc, 
                         cudaStream_t st);
 // Xf: float shadow of X (FP32 path: the CFL rate in float) or null
 cudaError_t launch_dt(const double* X, const float* Xf, const Grid& g, Scalars* sc, cudaStream_t st);
-cudaError_t launch_finish(Scalars* sc, cudaStream_t st);
+cudaError_t launch_finish(Scalars* sc, int base, cudaStream_t st);
+cudaError_t launch_gate(Scalars* sc, cudaGraphConditionalHandle hif, cudaStream_t st);
 cudaError_t launch_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
                               cudaStream_t st);
 cudaError_t launch_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
