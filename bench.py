@@ -286,13 +286,18 @@ def run_ours(args, world, rank, local):
                 g.step()
         torch.cuda.synchronize()
         g.profile(True)
+        q0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        q1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         with torch.cuda.stream(stream):
             for k in range(args.steps):
                 flush.zero_()
+                q0[k].record(stream)
                 g.step()
+                q1[k].record(stream)
         torch.cuda.synchronize()
         kt = g.kernel_times()
         g.profile(False)
+        prof_step_ms = sum(a.elapsed_time(b) for a, b in zip(q0, q1)) / args.steps
     value, ms_max = job_rate(n * n * args.steps, ms, world)
 
     # end to end through the public API with host buffers: every step copies
@@ -353,6 +358,12 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
         "roofline": roofline,
         "kernel_shares": shares if prof else None,
+        # the profiled pass: event-timed kernel classes against the whole step
+        # (the difference is the graph's scheduling between kernels, the
+        # conditional nodes and the host round trip of the profiled steps)
+        "step_anatomy": None if not prof else {
+            "kernel_classes_ms_per_step": round(total_kernel_ms / args.steps, 4),
+            "profiled_step_ms": round(prof_step_ms, 4)},
         "launch_mode": "eager" if args.eager else "graph, steps queued without host round trips",
         "gpu_launches": int(allreduce_sum(launches, world)),
         "e2e": e2e,
