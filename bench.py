@@ -239,6 +239,7 @@ def run_ours(args, world, rank, local):
     dev_index = local
     n = args.n
     p = workload(n, args.scheme)
+    p["serial_launch"] = 1 if args.serial_launch else 0
     R = SCHEME_DESC[args.scheme][1]
     g = gp.GPMood(p, args.precision, eager=args.eager)
     stream = torch.cuda.Stream()
@@ -364,7 +365,9 @@ def run_ours(args, world, rank, local):
         "step_anatomy": None if not prof else {
             "kernel_classes_ms_per_step": round(total_kernel_ms / args.steps, 4),
             "profiled_step_ms": round(prof_step_ms, 4)},
-        "launch_mode": "eager" if args.eager else "graph, steps queued without host round trips",
+        "launch_mode": ("eager" if args.eager else "graph, steps queued without host round trips")
+                       + (", stream order" if args.serial_launch
+                          else ", programmatic dependent launch"),
         "gpu_launches": int(allreduce_sum(launches, world)),
         "e2e": e2e,
     }
@@ -585,6 +588,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--serial-launch", action="store_true",
+                    help="plain stream order between the step's kernels instead of "
+                         "programmatic dependent launch")
     ap.add_argument("--scheme", default="GP-R3", choices=sorted(SCHEME_DESC),
                     help="GP-R3: the benchmark workload; GP-MOOD3 / POL-MOOD3: the "
                          "third-order schemes on the same vortex")

@@ -108,6 +108,10 @@ typedef struct {
                            second derivatives (the centred differences); ell is unused.
                            Requires R_max = 1 (the cascade Poly3 -> FOG).  Single-problem
                            handles and gpmood_step_noalloc */
+  int serial_launch;    /* 0: the kernels of a step are launched with programmatic
+                           dependent launch (each is scheduled while its predecessor
+                           drains and waits for it before touching memory); 1: plain
+                           stream order.  Same results */
 } gpmood_options;
 
 /* per-step diagnostics of the most recent step */

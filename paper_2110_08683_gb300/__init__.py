@@ -53,7 +53,7 @@ class Options(C.Structure):
         ("ncascade", C.c_int), ("cascade", C.c_int * 4), ("precision", C.c_int),
         ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
         ("max_mood_iters", C.c_int), ("riemann", C.c_int), ("rk", C.c_int),
-        ("eager", C.c_int), ("recon", C.c_int),
+        ("eager", C.c_int), ("recon", C.c_int), ("serial_launch", C.c_int),
     ]
 
 
@@ -165,6 +165,7 @@ def make_options(prob, precision=FP64, eager=False):
     o.rk = int(prob.get("rk", 3))
     o.riemann = RIEMANN[prob.get("riemann", "hllc")]
     o.recon = RECON[prob.get("recon", "gp")]
+    o.serial_launch = int(prob.get("serial_launch", 0))
     o.eager = 1 if eager else 0
     return o
 

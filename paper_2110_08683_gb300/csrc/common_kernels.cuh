@@ -7,6 +7,8 @@
 namespace gpm {
 
 __global__ void k_fill_ghosts(double* X, float* Xf, Grid g, const Scalars* sc, double tfrac) {
+  pdl_wait();
+  pdl_trigger();
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   fill_ghost(X, Xf, g, sc->t + tfrac * sc->dt, tid);
 }
@@ -15,6 +17,8 @@ __global__ void k_fill_ghosts(double* X, float* Xf, Grid g, const Scalars* sc, d
 // CFL form; positive doubles order like their bit patterns
 // Xf: the float shadow of X on the FP32 path (the rate in float), else null
 __global__ void k_dt_reduce(const double* X, const float* Xf, Grid g, Scalars* sc) {
+  pdl_wait();
+  pdl_trigger();
   if (sc->ctl.fixed_dt > 0.0) return;
   double best = 0.0;
   bool bad = false;
@@ -43,6 +47,8 @@ __global__ void k_dt_reduce(const double* X, const float* Xf, Grid g, Scalars* s
 // the step: a given dt (ctl.fixed_dt > 0) or the CFL step, clipped to
 // ctl.t_end when ctl.clip != 0; zeroes the per-step counters
 __global__ void k_dt_finalize(Scalars* sc) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const Control c = sc->ctl;
   double dt;
@@ -68,6 +74,8 @@ __global__ void k_dt_finalize(Scalars* sc) {
 // the step count where they were.  `base` is the step's launch count without
 // the MOOD iterations (4 kernels each), added to the running count.
 __global__ void k_finish_step(Scalars* sc, int base) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (sc->err == 0) {
     sc->t += sc->dt;
@@ -83,6 +91,8 @@ __global__ void k_finish_step(Scalars* sc, int base) {
 // closed the gate stays closed for the following steps, so the steps that ran
 // are always a prefix of those launched.
 __global__ void k_step_gate(Scalars* sc, cudaGraphConditionalHandle hif) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const Control c = sc->ctl;
   bool go = sc->err == 0;
@@ -93,6 +103,8 @@ __global__ void k_step_gate(Scalars* sc, cudaGraphConditionalHandle hif) {
 
 
 __global__ void k_mood_lower(MoodArgs M, uint8_t* ord, Cascade C) {
+  pdl_wait();
+  pdl_trigger();
   const int slot = M.sc->slot;
   const int n = M.sc->count[slot];
   const int* queue = M.queue[slot];
@@ -120,6 +132,8 @@ __device__ __forceinline__ void mood_decide(Scalars* sc, int stage, int n,
 
 // after the first pass (which filled queue 0)
 __global__ void k_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int n = sc->count[0];
   sc->slot = 0;
@@ -132,6 +146,8 @@ __global__ void k_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle 
 
 // after one MOOD iteration (which filled the other queue)
 __global__ void k_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int s = sc->slot, ns = s ^ 1;
   const int n = sc->count[ns];

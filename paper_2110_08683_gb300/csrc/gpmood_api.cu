@@ -57,6 +57,7 @@ struct gpmood_s {
   // steps can be queued without reading anything back; the host settles its
   // buffer rotation from the device's step count when it next synchronises
   int gated_ok;              // 0 not yet known, 1 plain graphs gated, -1 gating unavailable
+  int pdl;                   // 1: programmatic dependent launch between step kernels
   int pend;                  // steps queued since the last settle
   int sync_cur;              // rotation at the last settle
   long long sync_nsteps;     // device step count at the last settle
@@ -359,6 +360,7 @@ int copy_interior(gpmood_t h, const double* Xg, double* out) {
 int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
             double* tape = nullptr, uint8_t* otape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
+  g_pdl = h->pdl;
   const int a = h->cur;
   write_control(h, cfl, fixed_dt, clip, t_end);
   int rc = push_control(h);
@@ -535,7 +537,15 @@ int capture_step_impl(gpmood_t h, int cur, int prof, int record, int gated,
 
 int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out) {
   const int want_gate = !prof && !record && h->gated_ok >= 0;
+  g_pdl = h->pdl;
   int rc = capture_step_impl(h, cur, prof, record, want_gate, out);
+  if (rc && h->pdl) {
+    // the driver refused programmatic edges in the step graph: plain
+    // stream order from now on
+    h->pdl = 0;
+    g_pdl = 0;
+    rc = capture_step_impl(h, cur, prof, record, want_gate, out);
+  }
   if (rc && want_gate && h->gated_ok == 0) {
     // the driver refused the gated graph: plain graphs without the gate, and
     // asynchronous steps run synchronously from now on
@@ -621,12 +631,13 @@ int graph_step_async(gpmood_t h, double cfl, double fixed_dt, int clip, double t
 // ---------------------------------------------------------------------------
 namespace gpm {
 
+thread_local int g_pdl = 0;
+
 cudaError_t launch_fill(double* X, float* Xf, const Grid& g, const Scalars* sc, double tfrac,
                         cudaStream_t st) {
   long long n = (long long)g.ny * 2 * g.H + (long long)2 * g.H * (g.nx + 2 * g.H);
   int blocks = (int)((n + 255) / 256);
-  k_fill_ghosts<<<blocks, 256, 0, st>>>(X, Xf, g, sc, tfrac);
-  return cudaGetLastError();
+  return launch_k(k_fill_ghosts, dim3(blocks), dim3(256), st, X, Xf, g, sc, tfrac);
 }
 
 cudaError_t launch_dt(const double* X, const float* Xf, const Grid& g, Scalars* sc,
@@ -634,36 +645,31 @@ cudaError_t launch_dt(const double* X, const float* Xf, const Grid& g, Scalars* 
   long long n = (long long)g.nx * g.ny;
   int blocks = (int)((n + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_dt_reduce<<<blocks, 256, 0, st>>>(X, Xf, g, sc);
-  k_dt_finalize<<<1, 32, 0, st>>>(sc);
-  return cudaGetLastError();
+  cudaError_t e = launch_k(k_dt_reduce, dim3(blocks), dim3(256), st, X, Xf, g, sc);
+  if (e != cudaSuccess) return e;
+  return launch_k(k_dt_finalize, dim3(1), dim3(32), st, sc);
 }
 
 cudaError_t launch_finish(Scalars* sc, int base, cudaStream_t st) {
-  k_finish_step<<<1, 32, 0, st>>>(sc, base);
-  return cudaGetLastError();
+  return launch_k(k_finish_step, dim3(1), dim3(32), st, sc, base);
 }
 
 cudaError_t launch_gate(Scalars* sc, cudaGraphConditionalHandle hif, cudaStream_t st) {
-  k_step_gate<<<1, 32, 0, st>>>(sc, hif);
-  return cudaGetLastError();
+  return launch_k(k_step_gate, dim3(1), dim3(32), st, sc, hif);
 }
 
 cudaError_t launch_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
                               cudaStream_t st) {
-  k_mood_begin<<<1, 32, 0, st>>>(sc, stage, hc, use_graph);
-  return cudaGetLastError();
+  return launch_k(k_mood_begin, dim3(1), dim3(32), st, sc, stage, hc, use_graph);
 }
 
 cudaError_t launch_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
                             cudaStream_t st) {
-  k_mood_end<<<1, 32, 0, st>>>(sc, stage, hc, use_graph);
-  return cudaGetLastError();
+  return launch_k(k_mood_end, dim3(1), dim3(32), st, sc, stage, hc, use_graph);
 }
 
 cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, cudaStream_t st) {
-  k_mood_lower<<<kMoodBlocks, 256, 0, st>>>(M, ord, C);
-  return cudaGetLastError();
+  return launch_k(k_mood_lower, dim3(kMoodBlocks), dim3(256), st, M, ord, C);
 }
 
 }  // namespace gpm
@@ -781,6 +787,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->det.delta = fmin(g.dx, g.dy);
   h->precision = o.precision;
   h->eager = o.eager ? 1 : 0;
+  h->pdl = o.serial_launch ? 0 : 1;
   // a safety net only: radii never rise, so the loop ends; chains of
   // re-detected neighbours can take O(grid width) iterations
   h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
@@ -1095,6 +1102,7 @@ namespace {
 template <class Real>
 int frozen_step(gpmood_t h, const uint8_t* otape, double dt, const DirectW<Real>& D) {
   const int a = h->cur;
+  g_pdl = h->pdl;
   write_control(h, 1.0, dt, 0, 0.0);
   int rc = push_control(h);
   if (rc) return rc;

@@ -13,6 +13,15 @@ constexpr int kSegCells = 32; // cells per warp segment in the face kernels
 constexpr int kSegFaces = kSegCells - 1;
 constexpr int kFaceWarps = 8; // warps per face-kernel block
 
+// programmatic dependent launch: a step kernel launched while its
+// predecessor drains waits here, before touching memory, until the
+// predecessor has completed and its writes are visible (a no-op without the
+// launch attribute); pdl_trigger lets the successor be scheduled early
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // geometry and boundary data, passed by value to every kernel
 struct Grid {
   int nx, ny, H;          // interior cells and ghost layers

@@ -192,9 +192,22 @@ __device__ __forceinline__ Real pressure_ir(const Real* U, Real ir, Real gm1, Re
 // domain (non-positive or non-finite density or pressure) is undefined
 __device__ __forceinline__ void qnan(double& x) { x = __longlong_as_double(0x7ff8000000000000ll); }
 __device__ __forceinline__ void qnan(float& x) { x = __int_as_float(0x7fc00000); }
+// x > 0 and finite, decided on the integer bits (positive finite values are
+// the bit patterns strictly between +0 and +inf; NaN and negatives fall
+// outside): the same answer as the two comparisons without denormal
+// flushing, taken off the floating-point pipes
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool pos_finite(float x) {
+  const int b = __float_as_int(x);
+  return b > 0 && b < 0x7f800000;
+}
 template <class Real>
 __device__ __forceinline__ bool solver_domain(Real rL, Real rR, Real pL, Real pR) {
-  return rL > Real(0) && rR > Real(0) && pL > Real(0) && pR > Real(0);
+  // rho > 0 and p > 0 (non-finite inputs give a NaN flux anyway)
+  return pos_finite(rL) && pos_finite(rR) && pos_finite(pL) && pos_finite(pR);
 }
 
 // x-direction HLLC flux; pL/pR return the pressures of the two states so the
@@ -623,8 +636,8 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
     }
     // face-state check: finite and positive density and pressure (the
     // solver's sound speed needs gamma p / rho > 0; NaN fails the test)
-    badL |= !(SL[q][0] > Real(0) && pl > Real(0) && finite_r(SL[q][0]) && finite_r(pl));
-    badR |= !(SM[q][0] > Real(0) && pr > Real(0) && finite_r(SM[q][0]) && finite_r(pr));
+    badL |= !(pos_finite(SL[q][0]) && pos_finite(pl));
+    badR |= !(pos_finite(SM[q][0]) && pos_finite(pr));
   };
   // the Gauss points in mirror pairs (g, -g), each pair summed first: a
   // mirror image of the problem that reverses the points sums alike
@@ -656,6 +669,8 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
 template <int R, class Real, int DIR, int FW>
 __global__ void __launch_bounds__(32 * FW) k_faces(StageArgs<Real> A, Grid g,
                                                    const __grid_constant__ ParityW<Real> W) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ FaceTile<R, Real, FW> tile;
   faces_block<R, Real, DIR, FW>(A, g, W, DIR == 0 ? blockIdx.x : blockIdx.y,
                                 DIR == 0 ? blockIdx.y : blockIdx.x, tile);
@@ -833,6 +848,8 @@ __device__ __forceinline__ void update_cell_w(const StageArgs<Real>& A, const Gr
 template <class Real>
 __global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g, Detect D,
                                                       const __grid_constant__ DirectW<Real> Wd) {
+  pdl_wait();
+  pdl_trigger();
   update_cell_w<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, blockIdx.x * blockDim.x + threadIdx.x,
                       blockIdx.y * blockDim.y + threadIdx.y, 0);
 }
@@ -936,8 +953,8 @@ __device__ void face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, i
       riemann_x<Real>(g.riemann, a, b, gam, h, pl, pr);
       f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
     }
-    badL |= !(UL[0] > Real(0) && pl > Real(0) && finite_r(UL[0]) && finite_r(pl));
-    badR |= !(UR[0] > Real(0) && pr > Real(0) && finite_r(UR[0]) && finite_r(pr));
+    badL |= !(pos_finite(UL[0]) && pos_finite(pl));
+    badR |= !(pos_finite(UR[0]) && pos_finite(pr));
   };
   // mirror pairs (g, -g) summed first, in the order of the first-pass sweep
 #pragma unroll
@@ -1069,6 +1086,8 @@ template <class Real>
 __global__ void __launch_bounds__(128) k_mood_faces(StageArgs<Real> A, MoodArgs M, Grid g,
                                                     const __grid_constant__ DirectW<Real> Wd,
                                                     Cascade C) {
+  pdl_wait();
+  pdl_trigger();
   const int slot = M.sc->slot;
   const int n = M.sc->count[slot];
   const int* queue = M.queue[slot];
@@ -1083,6 +1102,8 @@ template <class Real>
 __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs M, Grid g,
                                                      Detect D,
                                                      const __grid_constant__ DirectW<Real> Wd) {
+  pdl_wait();
+  pdl_trigger();
   const int slot = M.sc->slot;
   const int n = M.sc->count[slot];
   const int* queue = M.queue[slot];
@@ -1208,6 +1229,8 @@ template <int R, class Real, int DIR, int FW>
 __global__ void __launch_bounds__(32 * FW) k_faces_batch(StageArgs<Real> B, const Prob* probs,
                                                          const Scalars* psc, const Item* items,
                                                          const __grid_constant__ ParityW<Real> W) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ FaceTile<R, Real, FW> tile;
   // the item's problem, read from shared memory on demand like kernel
   // parameters

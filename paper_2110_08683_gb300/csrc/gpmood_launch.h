@@ -5,6 +5,29 @@
 
 namespace gpm {
 
+// programmatic dependent launch between the kernels of a step: the next
+// kernel is scheduled while its predecessor drains and waits in
+// griddepcontrol.wait (pdl_wait, its first statement) until the predecessor
+// has completed and its writes are visible.  Set per thread by the API
+// around a capture or an eager step.
+extern thread_local int g_pdl;
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <class Real>
 struct Launch {
   // first pass: x (dir 0) or y (dir 1) faces at the top radius

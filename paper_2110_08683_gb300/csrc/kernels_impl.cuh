@@ -13,12 +13,10 @@ static cudaError_t faces_r(int dir, const StageArgs<Real>& A, const Grid& g,
   dim3 blk(32, kFaceWarps);
   if (dir == 0) {
     dim3 gx((g.nx + 1 + kSegFaces - 1) / kSegFaces, (g.ny + kFaceWarps - 1) / kFaceWarps);
-    k_faces<R, Real, 0, kFaceWarps><<<gx, blk, 0, st>>>(A, g, W);
-  } else {
-    dim3 gy((g.nx + kFaceWarps - 1) / kFaceWarps, (g.ny + 1 + kSegFaces - 1) / kSegFaces);
-    k_faces<R, Real, 1, kFaceWarps><<<gy, blk, 0, st>>>(A, g, W);
+    return launch_k(k_faces<R, Real, 0, kFaceWarps>, gx, blk, st, A, g, W);
   }
-  return cudaGetLastError();
+  dim3 gy((g.nx + kFaceWarps - 1) / kFaceWarps, (g.ny + 1 + kSegFaces - 1) / kSegFaces);
+  return launch_k(k_faces<R, Real, 1, kFaceWarps>, gy, blk, st, A, g, W);
 }
 
 template <class Real>
@@ -37,22 +35,19 @@ cudaError_t Launch<Real>::update_first(const StageArgs<Real>& A, const Grid& g, 
                                        const DirectW<Real>& Wd, cudaStream_t st) {
   dim3 blk(32, 8);
   dim3 grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-  k_update_first<Real><<<grd, blk, 0, st>>>(A, g, D, Wd);
-  return cudaGetLastError();
+  return launch_k(k_update_first<Real>, grd, blk, st, A, g, D, Wd);
 }
 
 template <class Real>
 cudaError_t Launch<Real>::mood_faces(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
                                      const DirectW<Real>& Wd, const Cascade& C, cudaStream_t st) {
-  k_mood_faces<Real><<<2 * kMoodBlocks, 128, 0, st>>>(A, M, g, Wd, C);
-  return cudaGetLastError();
+  return launch_k(k_mood_faces<Real>, dim3(2 * kMoodBlocks), dim3(128), st, A, M, g, Wd, C);
 }
 
 template <class Real>
 cudaError_t Launch<Real>::mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
                                       const Detect& D, const DirectW<Real>& Wd, cudaStream_t st) {
-  k_mood_update<Real><<<kMoodBlocks, 256, 0, st>>>(A, M, g, D, Wd);
-  return cudaGetLastError();
+  return launch_k(k_mood_update<Real>, dim3(kMoodBlocks), dim3(256), st, A, M, g, D, Wd);
 }
 
 template <int R, class Real, int FW>

@@ -104,3 +104,27 @@ def test_launch_count_is_counted_on_the_device():
     g.sync()
     assert g.launch_count() - n0 == 5 * (1 + 2 + 3 * 5 + 1)
     g.close()
+
+
+@pytest.mark.parametrize("eager", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_programmatic_launch_equals_stream_order(precision, eager):
+    """Programmatic dependent launch only overlaps the scheduling of a
+    kernel with the end of its predecessor (every step kernel waits for its
+    predecessor before touching memory): bit-identical results to plain
+    stream order, MOOD iterations included."""
+    p = _quads()
+    out = []
+    for serial in (0, 1):
+        q = dict(p, serial_launch=serial)
+        g = gp.GPMood(q, precision, eager=eager)
+        g.set_state(q["U0"])
+        for _ in range(4):
+            g.step_async()
+        g.sync()
+        o, f, st = g.flags()
+        out.append((g.get_state(), o, f, st))
+        g.close()
+    (U0, o0, f0, s0), (U1, o1, f1, s1) = out
+    assert np.array_equal(U0, U1) and np.array_equal(o0, o1) and np.array_equal(f0, f1)
+    assert s0["iters"] == s1["iters"] and sum(s0["nbad_first"]) > 0
