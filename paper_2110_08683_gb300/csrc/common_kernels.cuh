@@ -284,4 +284,34 @@ __global__ void k_lincomb(double* out, double a, const double* x, double b, cons
     out[t] = b == 0.0 ? a * x[t] : a * x[t] + b * y[t];
 }
 
+// interior cell averages [4][ny][nx] (src: device memory or pinned host
+// memory read over the chip-to-chip link) into a ghosted state X and, on the
+// FP32 path, its float shadow Xf: one pass, coalesced on both sides
+__global__ void k_set_interior(const double* __restrict__ src, double* X, float* Xf, Grid g) {
+  const long long n = 4LL * g.nx * g.ny;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / ((long long)g.nx * g.ny));
+    const long long r = t - (long long)v * g.nx * g.ny;
+    const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+    const long long k = v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H);
+    const double x = src[t];
+    X[k] = x;
+    if (Xf) Xf[k] = (float)x;
+  }
+}
+
+// the interior of a ghosted state X out to [4][ny][nx] (device memory or
+// pinned host memory written over the chip-to-chip link)
+__global__ void k_get_interior(const double* X, double* __restrict__ dst, Grid g) {
+  const long long n = 4LL * g.nx * g.ny;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(t / ((long long)g.nx * g.ny));
+    const long long r = t - (long long)v * g.nx * g.ny;
+    const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+    dst[t] = X[v * g.vstride + (long long)(j + g.H) * g.pitch + (i + g.H)];
+  }
+}
+
 }  // namespace gpm

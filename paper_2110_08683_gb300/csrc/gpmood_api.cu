@@ -102,6 +102,20 @@ void prim_to_cons(const double* P, double gam, double* U) {
   U[3] = P[3] / (gam - 1.0) + 0.5 * P[0] * (P[1] * P[1] + P[2] * P[2]);
 }
 
+// a pointer kernels may dereference: device memory as given (on_device), or
+// page-locked host memory through its device mapping; null for pageable
+// host memory, which goes through the driver's staged copies
+const double* device_view(const double* p, int on_device) {
+  if (on_device) return p;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return (const double*)a.devicePointer;
+  return nullptr;
+}
+
 int set_err(gpmood_t h, int code) {
   if (h) h->last_status = code;
   return code;
@@ -890,17 +904,25 @@ int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
   if (!h || !U) return GPMOOD_E_INVAL;
   const Grid& g = h->g;
   h->cur = 0;
-  for (int v = 0; v < 4; ++v) {
-    double* dst = h->U[0] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
-    const double* src = U + (size_t)v * g.nx * g.ny;
-    CK(cudaMemcpy2DAsync(dst, sizeof(double) * g.pitch, src, sizeof(double) * g.nx,
-                         sizeof(double) * g.nx, g.ny,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                         h->stream));
-  }
-  if (h->Uf[0]) {
-    k_to_real<float><<<152 * 8, 256, 0, h->stream>>>(h->U[0], h->Uf[0], 4 * g.vstride);
+  const double* src = device_view(U, on_device);
+  if (src) {
+    // one kernel reads the cell averages (device memory, or pinned host
+    // memory straight over the chip-to-chip link) into the ghosted layout
+    // and the float shadow
+    k_set_interior<<<152 * 8, 256, 0, h->stream>>>(src, h->U[0], h->Uf[0], g);
     CK(cudaGetLastError());
+  } else {
+    // pageable host memory: staged copies by the driver
+    for (int v = 0; v < 4; ++v) {
+      double* dst = h->U[0] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
+      const double* s = U + (size_t)v * g.nx * g.ny;
+      CK(cudaMemcpy2DAsync(dst, sizeof(double) * g.pitch, s, sizeof(double) * g.nx,
+                           sizeof(double) * g.nx, g.ny, cudaMemcpyHostToDevice, h->stream));
+    }
+    if (h->Uf[0]) {
+      k_to_real<float><<<152 * 8, 256, 0, h->stream>>>(h->U[0], h->Uf[0], 4 * g.vstride);
+      CK(cudaGetLastError());
+    }
   }
   // MOOD stamps restart with the scalars
   CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * (size_t)g.nx * g.ny, h->stream));
@@ -934,13 +956,17 @@ int gpmood_get_state(gpmood_t h, double* U, int on_device) {
   int rc = settle(h);
   if (rc) return rc;
   const Grid& g = h->g;
-  for (int v = 0; v < 4; ++v) {
-    const double* src = h->U[h->cur] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
-    double* dst = U + (size_t)v * g.nx * g.ny;
-    CK(cudaMemcpy2DAsync(dst, sizeof(double) * g.nx, src, sizeof(double) * g.pitch,
-                         sizeof(double) * g.nx, g.ny,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                         h->stream));
+  double* dst = const_cast<double*>(device_view(U, on_device));
+  if (dst) {
+    k_get_interior<<<152 * 8, 256, 0, h->stream>>>(h->U[h->cur], dst, g);
+    CK(cudaGetLastError());
+  } else {
+    for (int v = 0; v < 4; ++v) {
+      const double* s = h->U[h->cur] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
+      CK(cudaMemcpy2DAsync(U + (size_t)v * g.nx * g.ny, sizeof(double) * g.nx, s,
+                           sizeof(double) * g.pitch, sizeof(double) * g.nx, g.ny,
+                           cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   CK(cudaStreamSynchronize(h->stream));
   return GPMOOD_OK;

@@ -128,3 +128,30 @@ def test_programmatic_launch_equals_stream_order(precision, eager):
     (U0, o0, f0, s0), (U1, o1, f1, s1) = out
     assert np.array_equal(U0, U1) and np.array_equal(o0, o1) and np.array_equal(f0, f1)
     assert s0["iters"] == s1["iters"] and sum(s0["nbad_first"]) > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_state_io_through_pinned_host_memory(precision):
+    """set_state / get_state on page-locked host buffers go through one
+    kernel that reads or writes the host memory directly; pageable buffers
+    through the driver's staged copies.  Both give the same steps."""
+    torch = pytest.importorskip("torch")
+    p = _quads()
+    shape = p["U0"].shape
+    Up = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    Up[...] = p["U0"]
+    a, b = gp.GPMood(p, precision), gp.GPMood(p, precision)
+    a.set_state(p["U0"])
+    b.set_state(Up)
+    for _ in range(2):
+        a.step()
+        b.step()
+    Oa = a.get_state()
+    Ob = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    b.get_state(Ob)
+    assert np.array_equal(Oa, Ob)
+    # and back in from the pinned result
+    b.set_state(Ob)
+    assert np.array_equal(b.get_state(), Oa)
+    a.close()
+    b.close()
