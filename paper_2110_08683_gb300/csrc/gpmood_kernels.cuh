@@ -780,11 +780,13 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
 template <class Real>
 __device__ __forceinline__ void candidate(const StageArgs<Real>& A, const Grid& g, int i, int j,
                                           double dt, double* Y) {
+  // h dt / dx and h dt / dy once; per variable two differences and two fmas
+  const double hdt = A.h * dt, cx = hdt * g.inv_dx, cy = hdt * g.inv_dy;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     double fe = A.Fx[fxidx(g, v, i + 1, j)], fw = A.Fx[fxidx(g, v, i, j)];
     double gn = A.Fy[fyidx(g, v, i, j + 1)], gs = A.Fy[fyidx(g, v, i, j)];
-    Y[v] = A.X[gidx(g, v, i, j)] - (A.h * dt) * ((fe - fw) * g.inv_dx + (gn - gs) * g.inv_dy);
+    Y[v] = fma(-cx, fe - fw, fma(-cy, gn - gs, A.X[gidx(g, v, i, j)]));
   }
 }
 
@@ -794,7 +796,9 @@ __device__ __forceinline__ void combine_store(const StageArgs<Real>& A, const Gr
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     long long k = gidx(g, v, i, j);
-    const double o = A.ca != 0.0 ? fma(A.ca, A.U0[k], A.cb * Y[v]) : A.cb * Y[v];
+    // the first stage's combination is the candidate itself (ca = 0, cb = 1)
+    const double o = A.ca != 0.0 ? fma(A.ca, A.U0[k], A.cb * Y[v])
+                                 : (A.cb == 1.0 ? Y[v] : A.cb * Y[v]);
     A.out[k] = o;
     if constexpr (sizeof(Real) == sizeof(float)) A.outr[k] = (float)o;
     if (A.out2) A.out2[k] = fma(A.wa, A.W[k], A.wb * Y[v]);
