@@ -506,21 +506,36 @@ __device__ __forceinline__ void tile_load(FaceTile<R, Real, FW>& T_, const TX* X
                                           int seg, int band) {
   constexpr int TF = FaceTile<R, Real, FW>::TF;
   constexpr int TS = FaceTile<R, Real, FW>::TS;
-  auto& tile = T_.t;
-  const int lane = threadIdx.x, warp = threadIdx.y;
+  constexpr int NE = TS * TF;                 // tile cells of one variable
+  constexpr int NT = 32 * FW;                 // threads of the block
+  constexpr int NP = (NE + NT - 1) / NT;      // tile cells per thread
+  Real* tile = &T_.t[0][0][0];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
   const int fast0 = seg * kSegFaces - 1 - R;  // first tile cell along the sweep
   const int slow0 = band * FW - R;            // first tile cell across it
-  for (int e = warp * 32 + lane; e < 4 * TS * TF; e += 32 * FW) {
-    const int v = e / (TS * TF), r = e - v * (TS * TF);
+  // the cells this thread stages, worked out once for the four variables:
+  // consecutive threads take consecutive cells along x (coalesced loads)
+  long long off[NP];
+  int soff[NP];
+  bool ok[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int r = tid + p * NT;
     int sl, fa;
-    if (DIR == 0) { sl = r / TF; fa = r - sl * TF; }  // consecutive threads along x
-    else { fa = r / TS; sl = r - fa * TS; }           // consecutive threads along x
+    if (DIR == 0) { sl = r / TF; fa = r - sl * TF; }
+    else { fa = r / TS; sl = r - fa * TS; }
     const int i = DIR == 0 ? fast0 + fa : slow0 + sl;
     const int j = DIR == 0 ? slow0 + sl : fast0 + fa;
-    Real val = Real(0);
-    if (i >= -g.H && i < g.nx + g.H && j >= -g.H && j < g.ny + g.H) val = (Real)__ldg(X + gidx(g, v, i, j));
-    tile[v][sl][fa] = val;
+    ok[p] = i >= -g.H && i < g.nx + g.H && j >= -g.H && j < g.ny + g.H;
+    off[p] = gidx(g, 0, i, j);  // dereferenced only when ok
+    soff[p] = sl * TF + fa;
   }
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (tid + p * NT < NE)
+        tile[v * NE + soff[p]] = ok[p] ? (Real)__ldg(X + off[p] + v * g.vstride) : Real(0);
 }
 
 // states at all Gauss points of the two faces of one tile cell across the
