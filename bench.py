@@ -314,7 +314,7 @@ def run_ours(args, world, rank, local):
             flush.zero_()
             f0[k].record(stream)
             g.set_state(Uh)
-            g.step()
+            g.step_async()  # get_state waits for it
             g.get_state(Uo)
             f1[k].record(stream)
             Uh[...] = Uo
