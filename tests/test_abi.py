@@ -66,3 +66,21 @@ def test_batch_binding_marshals_and_rejects_mixed_weights():
     with pytest.raises(gp.GpmoodError) as e:
         gp.GPMoodBatch([a, b])
     assert e.value.code == -1
+
+
+def test_create_rejects_poly3_beyond_radius_one_before_touching_the_device():
+    # POL-MOOD3 is the cascade Poly3 -> FOG: R_max must be 1; unknown
+    # reconstruction codes are refused too
+    from paper_2110_08683_gb300 import inputs as I
+
+    p = I.vortex(n=16, R=3)
+    p["recon"] = "poly3"
+    h = ctypes.c_void_p()
+    rc = gp.load().gpmood_create(ctypes.byref(gp.make_grid(p)), 1.4, 3, 0.5,
+                                 ctypes.byref(gp.make_options(p)), ctypes.byref(h))
+    assert rc == -1 and not h.value
+    o = gp.make_options(I.vortex(n=16, R=1, cascade=[1, 0]))
+    o.recon = 7
+    rc = gp.load().gpmood_create(ctypes.byref(gp.make_grid(p)), 1.4, 1, 0.5, ctypes.byref(o),
+                                 ctypes.byref(h))
+    assert rc == -1 and not h.value
