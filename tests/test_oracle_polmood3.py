@@ -189,3 +189,23 @@ def test_shu_osher_without_csd_is_more_diffusive():
     assert off["GP-MOOD3"] < on["GP-MOOD3"] and off["GP-MOOD5"] < on["GP-MOOD5"] - 0.08
     assert off["GP-MOOD5"] - on["GP-MOOD3"] < 0.6 * (on["GP-MOOD5"] - on["GP-MOOD3"])
     assert off["POL-MOOD3"] < off["GP-MOOD3"]
+
+
+def test_shu_osher_set_up():
+    # Sec. 5.2.1: the Mach 3 shock at x = 0.5 on [0, 9], the sinusoid ahead of
+    # it at rest under unit pressure; cell averages of the printed states
+    p = I.shu_osher(n=256, scheme="GP-MOOD7")
+    U = p["U0"][:, 0, :]
+    dx = 9.0 / 256
+    x = (np.arange(256) + 0.5) * dx
+    left = x < 0.5 - dx
+    assert np.allclose(U[0][left], 3.857143) and np.allclose(U[1][left], 3.857143 * 2.629369)
+    right = x > 0.5 + dx
+    # the average of 1 + 0.2 sin(5 (x - 4.5)) over a cell, by the exact integral
+    lo, hi = x[right] - dx / 2, x[right] + dx / 2
+    mean = 1.0 + 0.2 * (np.cos(5 * (lo - 4.5)) - np.cos(5 * (hi - 4.5))) / (5 * dx)
+    assert np.abs(U[0][right] - mean).max() < 1e-12
+    assert np.abs(U[1][right]).max() == 0.0 and np.allclose(U[3][right], 1.0 / 0.4)
+    assert p["bc"][:2] == ["dirichlet", "outflow"] and p["t_end"] == 1.8
+    assert abs(p["ell"] - 6 * dx) < 1e-15 and p["rk"] == 4 and p["cascade"] == [3, 1, 0]
+    assert abs(p["cfl"] - 0.8 * dx ** 0.75) < 1e-15  # Delta^((2R+1)/4 - 1), R = 3
