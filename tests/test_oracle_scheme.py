@@ -481,3 +481,93 @@ def test_detect_csd_rejects_strong_compression():
     Y = U[:, 3, 3].copy()
     Y[0] = 1.1
     assert o.detect_cell(_ghost(o, U), 3, 3, Y) == O.ACCEPT_DMP
+
+
+# --------------------------------------------------------------------------
+# ghost cells, written out from the boundary rules: x ghosts of the interior
+# rows first, then the y ghosts of every column from the (possibly x-ghost)
+# cells they copy; mirror ghosts reflect cell -1-m onto m with the normal
+# momentum negated
+# --------------------------------------------------------------------------
+def _cons(P, gamma=1.4):
+    r, u, v, p = P
+    return np.array([r, r * u, r * v, p / (gamma - 1.0) + 0.5 * r * (u * u + v * v)])
+
+
+@pytest.mark.parametrize("kinds", [("periodic",) * 4, ("reflect", "outflow", "outflow", "reflect"),
+                                   ("dirichlet", "reflect", "reflect", "outflow")])
+def test_ghost_fill_follows_the_boundary_rules(kinds):
+    nx, ny = 7, 5
+    p = I.uniform(nx, ny, R=2, bc="outflow")
+    p["bc"] = list(kinds)
+    p["bc_prim"] = [[1.2, 0.3, -0.1, 0.9], [0.8, -0.2, 0.4, 1.1], [1.5, 0.1, 0.2, 0.7],
+                    [0.6, 0.0, -0.3, 1.3]]
+    rng = np.random.default_rng(11)
+    U = rng.uniform(0.5, 2.0, (4, ny, nx))
+    o = O.Oracle(p)
+    H = o.H
+    Xg = o.fill_ghosts(U, 0.0)
+
+    def along_x(i, j):
+        if 0 <= i < nx:
+            return U[:, j, i]
+        side = 0 if i < 0 else 1
+        k = -i if i < 0 else i - nx + 1
+        kind = kinds[side]
+        if kind == "periodic":
+            return U[:, j, i % nx]
+        if kind == "outflow":
+            return U[:, j, 0 if side == 0 else nx - 1]
+        if kind == "reflect":
+            s = U[:, j, k - 1 if side == 0 else nx - k].copy()
+            s[1] = -s[1]
+            return s
+        return _cons(p["bc_prim"][side])
+
+    def expect(i, j):
+        if 0 <= j < ny:
+            return along_x(i, j)
+        side = 2 if j < 0 else 3
+        k = -j if j < 0 else j - ny + 1
+        kind = kinds[side]
+        if kind == "periodic":
+            return along_x(i, j % ny)
+        if kind == "outflow":
+            return along_x(i, 0 if side == 2 else ny - 1)
+        if kind == "reflect":
+            s = along_x(i, k - 1 if side == 2 else ny - k).copy()
+            s[2] = -s[2]
+            return s
+        return _cons(p["bc_prim"][side])
+
+    for j in range(-H, ny + H):
+        for i in range(-H, nx + H):
+            np.testing.assert_array_equal(Xg[:, j + H, i + H], expect(i, j), err_msg=str((i, j)))
+
+
+def test_dmr_ghosts_follow_the_wall_and_the_moving_shock():
+    # bottom: the post-shock state left of the wall's start x = 1/6, a
+    # reflecting wall right of it; top: post-shock left of the shock line
+    # x_s(t) = 1/6 + (1 + 20 t)/sqrt(3) at the ghost-cell centres, pre-shock right
+    p = I.dmr(nx=32, ny=8, R=1)
+    o = O.Oracle(p)
+    H, nx, ny = o.H, 32, 8
+    rng = np.random.default_rng(3)
+    U = rng.uniform(0.5, 2.0, (4, ny, nx))
+    t = 0.05
+    Xg = o.fill_ghosts(U, t)
+    dx = 4.0 / nx
+    post, pre = _cons(p["dmr_post"]), _cons(p["dmr_pre"])
+    xs = 1.0 / 6.0 + (1.0 + 20.0 * t) / np.sqrt(3.0)
+    for i in range(nx):
+        xc = (i + 0.5) * dx
+        for k in range(1, H + 1):
+            bottom = Xg[:, H - k, i + H]
+            if xc < 1.0 / 6.0:
+                np.testing.assert_array_equal(bottom, post)
+            else:
+                s = U[:, k - 1, i].copy()
+                s[2] = -s[2]
+                np.testing.assert_array_equal(bottom, s)
+            top = Xg[:, ny - 1 + k + H, i + H]
+            np.testing.assert_array_equal(top, post if xc < xs else pre)
