@@ -571,3 +571,27 @@ def test_dmr_ghosts_follow_the_wall_and_the_moving_shock():
                 np.testing.assert_array_equal(bottom, s)
             top = Xg[:, ny - 1 + k + H, i + H]
             np.testing.assert_array_equal(top, post if xc < xs else pre)
+
+
+def test_edp1_face_radius_is_the_smaller_of_the_two_cells():
+    """Sec. 3.6, EDP1: a face takes the lower radius of its two cells.  With
+    one cell lowered to R = 1 in an R = 3 map, that cell's flux divergence is
+    the all-R1 one (its four faces drop to R1), cells away from it keep the
+    all-R3 divergence, and its east neighbour differs from both (one face at
+    R1, three at R3)."""
+    n = 12
+    p = I.density_wave(n=n, amp=0.2, R=3, ell=0.1)
+    o = O.Oracle(p)
+    U = p["U0"]
+    ci, cj = 5, 6
+    mixed = np.full((n, n), 3, np.uint8)
+    mixed[cj, ci] = 1
+    F3 = o.residual(U, np.full((n, n), 3, np.uint8))
+    F1 = o.residual(U, np.full((n, n), 1, np.uint8))
+    Fm = o.residual(U, mixed)
+    np.testing.assert_array_equal(Fm[:, cj, ci], F1[:, cj, ci])
+    far = np.ones((n, n), bool)
+    far[cj - 1:cj + 2, ci - 1:ci + 2] = False
+    np.testing.assert_array_equal(Fm[:, far], F3[:, far])
+    east = Fm[:, cj, ci + 1]
+    assert np.abs(east - F3[:, cj, ci + 1]).max() > 0 and np.abs(east - F1[:, cj, ci + 1]).max() > 0
