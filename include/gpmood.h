@@ -19,7 +19,12 @@
  *    destroy).  Pointers passed in are borrowed for the duration of the call.
  *  - Work is ordered on the handle's CUDA stream (the legacy default stream
  *    unless gpmood_set_stream gave another).  Calls that return host data
- *    synchronise that stream.
+ *    synchronise that stream; gpmood_step_async returns without waiting and
+ *    every later call that reads the state, the time or the flags waits for
+ *    the queued steps first.
+ *  - Also in the ABI: HLL fluxes (Sec. 5.3), the five-stage SSP-RK4 (eq. rk4),
+ *    POL-MOOD3 (Sec. 3.1 (iv)), the 1D method, the reverse mode of the step,
+ *    batches of independent problems and an allocation-free step.
  *  - State arrays are conservative cell averages U = (rho, rho u, rho v, rho E)
  *    in double precision, structure-of-arrays: U[v*ny*nx + j*nx + i] for
  *    variable v < 4, row j < ny, column i < nx (no ghost cells).
