@@ -19,8 +19,11 @@
  *   Sec. 3.8  SSP-RK3 (eq. rk3)
  *   Sec. 4    Steps 1-10
  *   App. B    GP second-derivative weights
- * Readings of points the paper leaves open are listed in the repository's
- * design notes; the ones that shape code are repeated where they apply.
+ * Where the paper leaves a point open, the reading taken is stated in a
+ * comment at the code it shapes (for example: z normalised by its signed sum
+ * so that z^T 1 = 1; the diamond |a|+|b| <= R stencil; the per-direction CFL
+ * bound; density alone in DMP, plateau and u2; the queued cells and their
+ * face neighbours re-detected after each MOOD iteration).
  */
 #define __STDC_WANT_IEC_60559_TYPES_EXT__
 #include <math.h>
