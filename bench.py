@@ -1,11 +1,21 @@
 """Benchmark of the GB300 GP-MOOD hot path.
 
-Workload: the 2D isentropic vortex on the periodic square [-5,5]^2 at 512^2
-cells, GP-R3 with the 7->5->3->1 cascade (ell = 0.5), SSP-RK3 at CFL 0.8 --
-one step is one full SSP-RK3 step (three stages, each with its MOOD loop,
-ghost fill and the time-step reduction).  Metric: cell-updates per second.
+Default workload: the Mach-10 double Mach reflection on [0,4] x [0,1] at
+4096 x 1024 cells (the largest single-GPU configuration), GP-R3 with the
+7->5->3->1 cascade (ell = 12 dx), HLLC, SSP-RK3 at CFL 0.8, MOOD active from
+the first step.  One step is one full SSP-RK3 step (three stages, each with
+its ghost fill, face sweeps, update + detection and MOOD loop, and the
+time-step reduction).  Metric: cell-updates per second.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+The default line times the FP64 path and adds, on the same workload, an
+`fp32` record (FP32 reconstruction, Riemann solver and detection; FP64 state
+and stage accumulation), an `adjoint` record (the 1024^2 periodic shear layer,
+GP-R2, 200 steps with checkpoints every 20: reverse / forward time), the
+512^2 isentropic vortex in FP64 (`vortex_512`), and the FP64 CPU oracle on a
+bounded sample of the workload, single-threaded and on all host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload dmr|vortex]
+                    [--precision fp64|fp32] [--only]
     python bench.py --impl reference ...    (the FP64 CPU oracle on the host)
 
 Under torchrun (N > 1) every rank runs its own replica of the workload on its
@@ -18,7 +28,9 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,33 +42,43 @@ sys.path.insert(0, ROOT)
 
 METRIC = "2D Euler GP-MOOD cell-updates/s"
 UNIT = "cell-updates/s"
-N_DEFAULT = 512
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12  # 128 FFMA/clk/SM
 HLLC_FLOPS = 78  # per pointwise HLLC flux, divisions and square roots counted once
+# the oracle's bounded sample of the double Mach reflection: the same problem
+# at 1/16 of the cells (it recomputes every face in every MOOD iteration, so
+# one full-size step takes minutes on one core)
+ORACLE_SAMPLE = (1024, 256)
 
 
 # --scheme: the default is the benchmark workload (GP-R3 cascade); the others
-# time the third-order schemes of Sec. 3.1 on the same vortex
+# time the third-order schemes of Sec. 3.1 on the same problem
 SCHEME_DESC = {
     "GP-R3": ("GP-R3 cascade 7->5->3->1", 3),
     "GP-MOOD3": ("GP-MOOD3 (GP-R1 -> FOG)", 1),
     "POL-MOOD3": ("POL-MOOD3 (Poly3 -> FOG)", 1),
 }
+DEFAULT_SIZE = {"dmr": (4096, 1024), "vortex": (512, 512)}
 
 
-def workload(n, scheme="GP-R3"):
+def workload(kind, nx, ny, scheme="GP-R3"):
     from paper_2110_08683_gb300 import inputs as I
 
-    if scheme == "GP-R3":
-        return I.vortex(n=n, R=3)
-    p = I.vortex(n=n, R=1, cascade=[1, 0])
-    p["recon"] = "poly3" if scheme == "POL-MOOD3" else "gp"
+    R = SCHEME_DESC[scheme][1]
+    if kind == "dmr":
+        p = I.dmr(nx=nx, ny=ny, R=R, cascade=None if scheme == "GP-R3" else [1, 0])
+    else:
+        p = I.vortex(n=nx, R=R, cascade=None if scheme == "GP-R3" else [1, 0])
+    if scheme != "GP-R3":
+        p["recon"] = "poly3" if scheme == "POL-MOOD3" else "gp"
     return p
 
 
-def workload_name(n, scheme):
-    return (f"isentropic vortex {n}^2 periodic [-5,5]^2, {SCHEME_DESC[scheme][0]}, ell=0.5, "
+def workload_name(kind, nx, ny, scheme="GP-R3"):
+    if kind == "dmr":
+        return (f"Mach-10 double Mach reflection {nx}x{ny} on [0,4]x[0,1], "
+                f"{SCHEME_DESC[scheme][0]}, ell=12dx, SSP-RK3, CFL 0.8, HLLC")
+    return (f"isentropic vortex {nx}^2 periodic [-5,5]^2, {SCHEME_DESC[scheme][0]}, ell=0.5, "
             f"SSP-RK3, CFL 0.8, HLLC")
 
 
@@ -84,18 +106,28 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision, scheme="GP-R3"):
-    """DRAM bytes per launch of the x-face kernel from the committed ncu
-    summary, or None when the kernel sources changed since the capture.  Rows
-    of the default workload are keyed by the precision alone, the others by
-    precision and scheme ("fp64 POL-MOOD3")."""
-    key = precision if scheme == "GP-R3" else f"{precision} {scheme}"
+def algorithmic_flops_per_face(R=3):
+    """The reconstruction and Riemann work of one face as the method states
+    it: the left and right states at q Gauss points, 4 variables, each a dot
+    product of length N (8 q N FMA, 2 flop each), q HLLC fluxes and the
+    Gauss sum of 4 variables (q FMA each)."""
+    N = 2 * R * R + 2 * R + 1
+    q = R + 1
+    return 2 * 8 * q * N + q * HLLC_FLOPS + 2 * 4 * q
+
+
+def ncu_traffic(precision, kind, scheme="GP-R3"):
+    """DRAM bytes per launch of the x-face kernel on this workload from the
+    committed ncu summary, or None when the kernel sources changed since the
+    capture.  Rows are keyed by workload and precision ("dmr fp64"), with the
+    scheme appended for the third-order schemes ("vortex fp64 POL-MOOD3")."""
+    key = f"{kind} {precision}" + ("" if scheme == "GP-R3" else f" {scheme}")
     path = os.path.join(ROOT, "profiles", "faces_x_traffic.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    # table rows: | precision | kernel sources sha256 | DRAM bytes per launch | ...
+    # table rows: | workload precision | kernel sources sha256 | DRAM bytes per launch | ...
     for ln in lines:
         cells = [c.strip() for c in ln.strip().strip("|").split("|")]
         if len(cells) >= 3 and cells[0] == key:
@@ -215,58 +247,138 @@ def job_rate(units, ms, world):
     return total / (ms_max / 1e3), ms_max
 
 
-def cpu_baseline(n, steps=2, scheme="GP-R3"):
-    """The FP64 CPU oracle as it stands, single thread, on a bounded sample:
-    `steps` full SSP-RK3 steps of the same workload."""
+def host_info():
+    """Host cores, CPU model and the oracle's compiler flags (for the CPU
+    baseline's record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
     import oracle as O
 
-    p = workload(n, scheme)
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine(),
+            "machine": platform.machine(), "oracle_flags": " ".join(O.CFLAGS)}
+
+
+def _oracle_worker(kind, nx, ny, scheme, steps, barrier, queue):
+    """One replica of the oracle's bounded sample: `steps` full SSP-RK3 steps
+    of the workload from its initial state, timed between two clock reads
+    after all replicas have set up."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle as O
+
+    p = workload(kind, nx, ny, scheme)
     o = O.Oracle(p)
-    U = p["U0"]
-    t0 = time.perf_counter()
-    t = 0.0
+    U, t = p["U0"], 0.0
+    if barrier is not None:
+        barrier.wait()
+    t0 = time.monotonic()
     for _ in range(steps):
         U, st, _, _ = o.step(U, t)
         t += st["dt"]
-    el = time.perf_counter() - t0
-    return {"value": n * n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full SSP-RK3 steps of the {n}^2 vortex, 1 thread, {el:.1f} s"}
+    t1 = time.monotonic()
+    o.close()
+    queue.put((nx * ny * steps, t0, t1))
 
 
-def run_ours(args, world, rank, local):
-    import numpy as np
+def oracle_replicas(kind, nx, ny, scheme, steps, procs):
+    """`procs` replicas of the oracle's sample at once, one process each
+    (spawned: no CUDA state is inherited): total cell-updates over the span
+    from the first start to the last finish."""
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    queue = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(kind, nx, ny, scheme, steps, barrier, queue))
+          for _ in range(procs)]
+    for q in ps:
+        q.start()
+    res = [queue.get() for _ in ps]
+    for q in ps:
+        q.join()
+    units = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / span, span
+
+
+def oracle_sample(kind):
+    """The oracle's bounded sample of a workload: grid and steps."""
+    if kind == "dmr":
+        return ORACLE_SAMPLE[0], ORACLE_SAMPLE[1], 1
+    return DEFAULT_SIZE[kind][0], DEFAULT_SIZE[kind][1], 2
+
+
+def sample_text(kind, nx, ny, steps):
+    if kind == "dmr":
+        return (f"{steps} full SSP-RK3 step(s) from t = 0 of the same double Mach reflection at "
+                f"{nx}x{ny} (1/16 of the cells: the oracle recomputes every face in every MOOD "
+                f"iteration, so a full-size step takes minutes on one core)")
+    return f"{steps} full SSP-RK3 steps from t = 0 of the {nx}^2 vortex"
+
+
+def cpu_baseline(kind, scheme="GP-R3"):
+    """The FP64 CPU oracle as it stands on a bounded sample of the workload:
+    one replica on one core, then one replica on every host core at once."""
+    nx, ny, steps = oracle_sample(kind)
+    one, span1 = oracle_replicas(kind, nx, ny, scheme, steps, 1)
+    P = os.cpu_count() or 1
+    allv, spanP = oracle_replicas(kind, nx, ny, scheme, steps, P)
+    return {"value": allv, "unit": UNIT, "cores": P, "kind": "oracle",
+            "sample": sample_text(kind, nx, ny, steps) + f", one replica per core on {P} cores, "
+                      f"{spanP:.1f} s",
+            "single_thread": {"value": one, "unit": UNIT, "cores": 1, "seconds": round(span1, 2)},
+            "host": host_info()}
+
+
+def measure(kind, nx, ny, precision, scheme, steps, warmup, world, local, eager=False,
+            serial=False, profile=True, e2e=True, clocks=True):
+    """Time `steps` queued steps of the workload (after `warmup`), then a
+    profiled pass for the per-class shares and the x-face kernel's launch
+    time, then the end-to-end pass through the public calls with host
+    buffers."""
     import torch
 
     import paper_2110_08683_gb300 as gp
 
-    torch.cuda.set_device(0 if world > 1 else local)
-    dev_index = local
-    n = args.n
-    p = workload(n, args.scheme)
-    p["serial_launch"] = 1 if args.serial_launch else 0
-    R = SCHEME_DESC[args.scheme][1]
-    g = gp.GPMood(p, args.precision, eager=args.eager)
+    p = workload(kind, nx, ny, scheme)
+    p["serial_launch"] = 1 if serial else 0
+    R = SCHEME_DESC[scheme][1]
+    g = gp.GPMood(p, precision, eager=eager)
     stream = torch.cuda.Stream()
     g.set_stream(stream.cuda_stream)
     # L2 (129 MB) is flushed between timed steps by writing 256 MB
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     g.set_state(p["U0"])
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             g.step_async()
     g.sync()
     torch.cuda.synchronize()
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sampler = ClockSampler(dev_index)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(local) if clocks else None
     # timed region: the steps are queued back to back (the host reads nothing
     # between them), each bracketed by events, an L2 flush between steps
     launches0 = g.launch_count()
+    st0 = g.flags(maps=False)[2]
     barrier(world)
     torch.cuda.synchronize()
-    sampler.start()
+    if sampler:
+        sampler.start()
     with torch.cuda.stream(stream):
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()
             e0[k].record(stream)
             g.step_async()
@@ -274,16 +386,19 @@ def run_ours(args, world, rank, local):
     g.sync()
     torch.cuda.synchronize()
     barrier(world)
-    sampler.stop()
+    if sampler:
+        sampler.stop()
     launches = g.launch_count() - launches0
+    st1 = g.flags(maps=False)[2]
     ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    value, ms_max = job_rate(nx * ny * steps, ms, world)
 
     # second timed pass for the per-class shares and the dominant kernel's
     # duration: the profiled step graphs carry event nodes around every
     # kernel class (read back after each step).  Captured on first use, so a
     # few steps run before the counters are reset.
-    prof = not args.eager  # per-kernel events exist in the graph mode only
-    kt = {}
+    prof = profile and not eager  # per-kernel events exist in the graph mode only
+    kt, prof_step_ms, fr = {}, None, []
     if prof:
         g.profile(True)
         with torch.cuda.stream(stream):
@@ -291,93 +406,120 @@ def run_ours(args, world, rank, local):
                 g.step()
         torch.cuda.synchronize()
         g.profile(True)
-        q0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        q1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        q0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        q1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         with torch.cuda.stream(stream):
-            for k in range(args.steps):
+            for k in range(steps):
                 flush.zero_()
                 q0[k].record(stream)
                 g.step()
                 q1[k].record(stream)
+                st = g.flags(maps=False)[2]
+                fr.append((st["nbad_first"], st["iters"]))
         torch.cuda.synchronize()
         kt = g.kernel_times()
         g.profile(False)
-        prof_step_ms = sum(a.elapsed_time(b) for a, b in zip(q0, q1)) / args.steps
-    value, ms_max = job_rate(n * n * args.steps, ms, world)
+        prof_step_ms = sum(a.elapsed_time(b) for a, b in zip(q0, q1)) / steps
 
-    # end to end through the public API with host buffers: every step copies
-    # the state in from pinned host memory and reads the result back
-    Uh = torch.empty((4, n, n), dtype=torch.float64, pin_memory=True).numpy()
-    Uh[...] = p["U0"]
-    Uo = torch.empty((4, n, n), dtype=torch.float64, pin_memory=True).numpy()
-    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier(world)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.zero_()
-            f0[k].record(stream)
-            g.set_state(Uh)
-            g.step_async()  # get_state waits for it
-            g.get_state(Uo)
-            f1[k].record(stream)
-            Uh[...] = Uo
-    torch.cuda.synchronize()
-    barrier(world)
-    e2e_value, _ = job_rate(n * n * args.steps, sum(a.elapsed_time(b) for a, b in zip(f0, f1)),
-                            world)
-    e2e = {"value": e2e_value, "unit": UNIT,
-           "h2d_bytes_per_step": int(Uh.nbytes), "d2h_bytes_per_step": int(Uo.nbytes)}
+    e2e_rec = None
+    if e2e:
+        # end to end through the public API with host buffers: every step
+        # copies the state in from pinned host memory and reads it back
+        Uh = torch.empty((4, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+        Uh[...] = p["U0"]
+        Uo = torch.empty((4, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+        f0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        f1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier(world)
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.zero_()
+                f0[k].record(stream)
+                g.set_state(Uh)
+                g.step_async()  # get_state waits for it
+                g.get_state(Uo)
+                f1[k].record(stream)
+                Uh[...] = Uo
+        torch.cuda.synchronize()
+        barrier(world)
+        e2e_value, _ = job_rate(nx * ny * steps,
+                                sum(a.elapsed_time(b) for a, b in zip(f0, f1)), world)
+        e2e_rec = {"value": e2e_value, "unit": UNIT,
+                   "h2d_bytes_per_step": int(Uh.nbytes), "d2h_bytes_per_step": int(Uo.nbytes)}
+    g.close()
 
     # roofline of the dominant kernel: the first-pass x-face kernel
-    fx_ms, fx_n = kt["faces_x"] if prof else (0.0, 0)
-    per_launch_s = fx_ms / 1e3 / max(fx_n, 1)
-    faces = (n + 1) * n
-    flops = faces * faces_flops_per_face(R)
-    real64 = args.precision == "fp64"
-    peak = FP64_PEAK_TFLOPS if real64 else FP32_PEAK_TFLOPS
-    achieved = flops / per_launch_s / 1e12 if prof else 0.0
-    roofline = None if not prof else {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": ncu_traffic(args.precision, args.scheme),
-                "kernel": "k_faces<R=%d,%s,x>" % (R, "double" if real64 else "float"),
-                "flops_per_launch": flops, "launch_ms": round(per_launch_s * 1e3, 4),
-                "timing": "event nodes around every x-face launch in the step graph, "
-                          "second timed pass of the same steps (L2 flushed between steps)",
-                "peak_source": "derived: 152 SMs x %s/clk x 2.07 GHz (of nominal; measured DFMA "
-                               "1.19 TFLOP/s, FFMA 69.9 TFLOP/s)" % ("4 FP64 flop" if real64
-                                                                     else "256 FP32 flop")}
+    real64 = precision == "fp64"
+    roofline = None
+    if prof:
+        fx_ms, fx_n = kt["faces_x"]
+        per_launch_s = fx_ms / 1e3 / max(fx_n, 1)
+        faces = (nx + 1) * ny
+        peak = FP64_PEAK_TFLOPS if real64 else FP32_PEAK_TFLOPS
+        alg = faces * algorithmic_flops_per_face(R)
+        exe = faces * faces_flops_per_face(R)
+        roofline = {
+            "bound": "alu", "achieved": round(alg / per_launch_s / 1e12, 4),
+            "peak": round(peak, 4), "unit": "TFLOP/s",
+            "frac": round(alg / per_launch_s / 1e12 / peak, 4),
+            "traffic": ncu_traffic(precision, kind, scheme),
+            "kernel": "k_faces<R=%d,%s,x>" % (R, "double" if real64 else "float"),
+            "flops_per_launch": alg,
+            "flops_per_face": algorithmic_flops_per_face(R),
+            "count": "algorithmic: 8 q N reconstruction FMA (2 flop), q HLLC at %d flop, the "
+                     "Gauss sum; per x face, x (nx+1) ny faces a launch" % HLLC_FLOPS,
+            "executed": {"flops_per_face": faces_flops_per_face(R), "flops_per_launch": exe,
+                         "achieved": round(exe / per_launch_s / 1e12, 4),
+                         "frac": round(exe / per_launch_s / 1e12 / peak, 4),
+                         "count": "the kernel's own arithmetic after the parity-sum "
+                                  "reconstruction (mirror-orbit sums, q/2 dot products, "
+                                  "butterflies)"},
+            "launch_ms": round(per_launch_s * 1e3, 4),
+            "timing": "event nodes around every x-face launch in the step graph, second timed "
+                      "pass of the same steps (L2 flushed between steps)",
+            "peak_source": "derived: 152 SMs x %s/clk x 2.07 GHz (of nominal; measured DFMA "
+                           "1.19 TFLOP/s, FFMA 69.9 TFLOP/s)" % ("4 FP64 flop" if real64
+                                                                 else "256 FP32 flop")}
     total_kernel_ms = sum(v[0] for v in kt.values())
     shares = {k: round(v[0] / total_kernel_ms, 4) if total_kernel_ms else None
-              for k, v in kt.items()}
-
-    g.close()
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+              for k, v in kt.items()} if prof else None
+    ncell = nx * ny
+    mood = None
+    if fr:
+        nb = [b for f in fr for b in f[0]]
+        it = [i for f in fr for i in f[1]]
+        mood = {"first_pass_flag_fraction_mean": round(sum(nb) / len(nb) / ncell, 6),
+                "first_pass_flag_fraction_max": round(max(nb) / ncell, 6),
+                "iterations_per_stage_mean": round(sum(it) / len(it), 2),
+                "iterations_per_stage_max": max(it)}
+    return {
+        "value": value, "ms_per_step": ms_max / steps,
         "dtype": "f64" if real64 else "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": workload_name(n, args.scheme),
-                   "cells": n * n, "precision": args.precision,
-                   "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
-        "roofline": roofline,
-        "kernel_shares": shares if prof else None,
+        "config": {"workload": workload_name(kind, nx, ny, scheme), "cells": ncell,
+                   "precision": precision, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "t_start": round(st0["t"], 6), "t_end": round(st1["t"], 6)},
+        "roofline": roofline, "kernel_shares": shares,
         # the profiled pass: event-timed kernel classes against the whole step
         # (the difference is the graph's scheduling between kernels, the
         # conditional nodes and the host round trip of the profiled steps)
         "step_anatomy": None if not prof else {
-            "kernel_classes_ms_per_step": round(total_kernel_ms / args.steps, 4),
+            "kernel_classes_ms_per_step": round(total_kernel_ms / steps, 4),
             "profiled_step_ms": round(prof_step_ms, 4)},
-        "launch_mode": ("eager" if args.eager else "graph, steps queued without host round trips")
-                       + (", stream order" if args.serial_launch
-                          else ", programmatic dependent launch"),
+        "mood": mood,
+        "launch_mode": ("eager" if eager else "graph, steps queued without host round trips")
+                       + (", stream order" if serial else ", programmatic dependent launch"),
         "gpu_launches": int(allreduce_sum(launches, world)),
-        "e2e": e2e,
+        "e2e": e2e_rec,
+        "clocks": sampler.summary() if sampler else None,
     }
-    return line, sampler.summary()
 
 
+def summary_of(rec):
+    """The keys of a sub-record of the default line."""
+    keys = ("value", "ms_per_step", "dtype", "config", "roofline", "kernel_shares", "mood",
+            "e2e", "gpu_launches", "clocks")
+    return {k: rec[k] for k in keys if k in rec}
 def run_batch(args, world, rank, local):
     """Many independent four-quadrant problems of uneven sizes in one batch
     (one launch per kernel class, graph-captured MOOD loops)."""
@@ -449,7 +591,7 @@ def run_adjoint(args, world, rank, local):
     from paper_2110_08683_gb300.autograd import rollout
 
     torch.cuda.set_device(0 if world > 1 else local)
-    n = args.n
+    n = args.adjoint_n
     p = I.shear_layer(n=n, R=2, seed=0)
     g = gp.GPMood(p, args.precision, eager=args.eager)
     U0 = torch.tensor(p["U0"], device="cuda")
@@ -545,41 +687,34 @@ def adjoint_fd_check(g, p, U0, W, steps, ndir, torch):
 
 
 def run_reference(args, world, rank):
-    """The FP64 CPU oracle (the reference arm of this tier) on the host cores."""
-    import oracle as O
-
-    n = args.n
-    p = workload(n, args.scheme)
-    o = O.Oracle(p)
-    U = p["U0"]
-    t = 0.0
-    # each step is one full SSP-RK3 step of the same workload; the count is
-    # capped so that the run stays within a few minutes
-    t0 = time.perf_counter()
-    U, st, _, _ = o.step(U, t)
-    t += st["dt"]
-    one = time.perf_counter() - t0
-    budget = 150.0
-    w = min(args.warmup, max(0, int(budget / 4 / max(one, 1e-3))))
-    k = max(1, min(args.steps, int(budget / max(one, 1e-3))))
-    for _ in range(max(0, w - 1)):
-        U, st, _, _ = o.step(U, t)
-        t += st["dt"]
-    t0 = time.perf_counter()
-    for _ in range(k):
-        U, st, _, _ = o.step(U, t)
-        t += st["dt"]
-    el = time.perf_counter() - t0
-    value = n * n * k / el
-    sample = f"{k} full SSP-RK3 steps of the {n}^2 vortex (of {args.steps} requested), 1 thread"
+    """The FP64 CPU oracle (the reference arm of this tier) on the host
+    cores: one replica of the bounded sample per core, all at once, each step
+    a full SSP-RK3 step of the sample; the step count is capped so that the
+    run stays within a few minutes."""
+    kind, scheme = args.workload, args.scheme
+    nx, ny, _ = oracle_sample(kind)
+    if args.nx:  # a smaller sample (tests)
+        nx, ny = args.nx, args.ny or args.nx
+    # the cost of one step of the sample on one core sizes the run
+    one, span1 = oracle_replicas(kind, nx, ny, scheme, 1, 1)
+    budget = 120.0
+    k = max(1, min(args.steps, int(budget / max(span1, 1e-3))))
+    P = os.cpu_count() or 1
+    value, span = oracle_replicas(kind, nx, ny, scheme, k, P)
+    sample = (sample_text(kind, nx, ny, k) + f" (of {args.steps} requested), one replica per "
+              f"core on {P} cores")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": k, "warmup": w, "ms_per_step": el * 1e3 / k, "higher_is_better": True,
+        "steps": k, "warmup": 0, "ms_per_step": span * 1e3 / k, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(n, args.scheme),
-                   "cells": n * n, "precision": "fp64", "parallelism": "host, 1 thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "config": {"workload": workload_name(kind, *DEFAULT_SIZE[kind], scheme),
+                   "cells": DEFAULT_SIZE[kind][0] * DEFAULT_SIZE[kind][1], "precision": "fp64",
+                   "parallelism": f"host, {P} processes", "sample_cells": nx * ny},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+                         "sample": sample,
+                         "single_thread": {"value": one, "unit": UNIT, "cores": 1,
+                                           "seconds": round(span1, 2)},
+                         "host": host_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -587,23 +722,31 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dmr", choices=sorted(DEFAULT_SIZE),
+                    help="dmr: the 4096x1024 double Mach reflection (default); vortex: the "
+                         "512^2 isentropic vortex")
+    ap.add_argument("--nx", type=int, default=0)
+    ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--only", action="store_true",
+                    help="the main record alone (no fp32 / vortex / adjoint sub-records, no "
+                         "CPU baseline)")
     ap.add_argument("--serial-launch", action="store_true",
                     help="plain stream order between the step's kernels instead of "
                          "programmatic dependent launch")
     ap.add_argument("--scheme", default="GP-R3", choices=sorted(SCHEME_DESC),
                     help="GP-R3: the benchmark workload; GP-MOOD3 / POL-MOOD3: the "
-                         "third-order schemes on the same vortex")
+                         "third-order schemes on the same problem")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels one by one instead of the step graphs (for per-kernel "
-                         "profilers; slower, no per-kernel event timing)"),
+                         "profilers; slower, no per-kernel event timing)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time a rollout and its adjoint instead (shear layer, GP-R2)")
+    ap.add_argument("--adjoint-n", type=int, default=1024)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-fd", type=int, default=8,
                     help="random directions of the finite-difference check (0: skip)")
@@ -616,6 +759,9 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args, world, rank)), flush=True)
         return
+    import torch
+
+    torch.cuda.set_device(0 if world > 1 else local)
     if args.adjoint:
         line = run_adjoint(args, world, rank, local)
         if rank == 0:
@@ -626,11 +772,49 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
-    line, clocks = run_ours(args, world, rank, local)
-    line["clocks"] = clocks
+    kind = args.workload
+    nx = args.nx or DEFAULT_SIZE[kind][0]
+    ny = args.ny or DEFAULT_SIZE[kind][1]
+    rec = measure(kind, nx, ny, args.precision, args.scheme, args.steps, args.warmup, world,
+                  local, eager=args.eager, serial=args.serial_launch)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": rec["dtype"], "data": "synthetic"}
+    for k in ("config", "roofline", "kernel_shares", "step_anatomy", "mood", "launch_mode",
+              "gpu_launches", "e2e", "clocks"):
+        line[k] = rec[k]
+    if not args.only:
+        # the metric's other parts on the same workload: the FP32 path
+        other = "fp32" if args.precision == "fp64" else "fp64"
+        line[other] = summary_of(measure(kind, nx, ny, other, args.scheme, args.steps,
+                                         args.warmup, world, local, eager=args.eager,
+                                         serial=args.serial_launch, e2e=False))
+        if world == 1:
+            # the smallest 2D configuration (MOOD idle on the smooth vortex)
+            line["vortex_512"] = summary_of(measure("vortex", 512, 512, "fp64", args.scheme,
+                                                    args.steps, args.warmup, world, local,
+                                                    e2e=False, clocks=False))
+            # adjoint / forward time on the shear layer, checkpoints every 20 steps
+            a = run_adjoint(argparse.Namespace(**{**vars(args), "adjoint_fd": 0,
+                                                  "precision": "fp64"}), world, rank, local)
+            ck = a["adjoint"]["checkpoints_every_20"]
+            rs = a["adjoint"]["resident_tapes"]
+            line["adjoint"] = {
+                "config": a["config"]["workload"],
+                "forward_s": round(ck["forward_s"], 4),
+                "reverse_over_forward": round(ck["backward_over_plain_forward"], 3),
+                "forward_plus_reverse_over_forward": round(
+                    (ck["forward_s"] + ck["backward_s"]) / ck["forward_s"], 3),
+                "checkpoints_every": 20,
+                "resident_tapes": {"reverse_over_forward": round(rs["backward_over_plain_forward"],
+                                                                 3),
+                                   "forward_s": round(rs["forward_s"], 4),
+                                   "backward_s": round(rs["backward_s"], 4)},
+                "forward_cell_updates_per_s": a["value"]}
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.n, scheme=args.scheme)
+        if world == 1 and not args.no_cpu_baseline and not args.only:
+            line["cpu_baseline"] = cpu_baseline(kind, args.scheme)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -319,11 +319,15 @@ int gpmood_batch_destroy(gpmood_batch_t b);
  * buffers (three ghosted states, face fluxes, flag maps, queues, counters)
  * are carved out of one file-scope device array of
  * GPMOOD_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads this
- * library holds until the process exits.  That covers grids of about
- * 256 x 256 cells at R_max = 3; a grid needing more returns
+ * library holds until the process exits.  At R_max = 3 that covers square
+ * grids up to 296 x 296 cells in FP64 and 259 x 259 in FP32 (whose float
+ * shadows of the three states share the array); a grid needing more returns
  * GPMOOD_E_TOO_BIG without touching the device.
  *
- * Arguments are those of gpmood_create (grid, gamma, R_max, ell, opts) plus:
+ * Arguments are those of gpmood_create (grid, gamma, R_max, ell, opts),
+ * checked as it checks them, except that only SSP-RK3 (opts->rk 0 or 3) and
+ * two-dimensional grids (grid->dim 0 or 2) are taken; anything else returns
+ * GPMOOD_E_INVAL before the device is touched.  In addition:
  * U_in / U_out, device pointers to cell averages in the layout above (they
  * may be the same array); t, the time of U_in (time-dependent boundaries);
  * cfl > 0; dt_out (nullable, host) receives the step's Delta t; stream, a
@@ -333,8 +337,11 @@ int gpmood_batch_destroy(gpmood_batch_t b);
  * array (cudaGetSymbolAddress with that device current); make that first
  * call before any stream capture.  Every call shares the one array and
  * leaves its contents behind; the parts that must start at zero are cleared
- * at each call.  Calls that overlap on the GPU (other threads or streams)
- * race on the scratch, so serialise them.  Errors as for gpmood_step.
+ * at each call.  Calls that overlap on the same GPU (other threads or
+ * streams) race on its scratch, so serialise them.  Each GPU has its own
+ * array, and the host-side copy of the step's counters lives on the
+ * caller's stack, so calls on different GPUs share nothing.  Errors as for
+ * gpmood_step.
  */
 #define GPMOOD_NOALLOC_SCRATCH_BYTES (16u << 20)
 int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_max, double ell,

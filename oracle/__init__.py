@@ -23,15 +23,17 @@ ACCEPT_CSD, ACCEPT_PLATEAU, ACCEPT_DMP, ACCEPT_U2 = 1, 2, 3, 4
 FAIL_CAD, FAIL_PAD, FAIL_U2 = -1, -2, -3
 
 
+# no fast-math, no FMA contraction
+CFLAGS = ("gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off")
+
+
 def build(force=False):
-    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    """Compile the oracle with gcc (CFLAGS)."""
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(
-        ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, SRC, "-lm"]
-    )
+    subprocess.check_call([*CFLAGS, "-o", tmp, SRC, "-lm"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -1270,7 +1270,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GPMOOD_NOALLOC_
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices];
-Scalars g_noalloc_host_sc;  // host mirror of the scalars (pageable, shared)
 
 // device address of the scratch array on the current device
 int noalloc_scratch(unsigned char** out) {
@@ -1294,7 +1293,9 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
                                    const gpmood_options* opts, const double* U_in, double* U_out,
                                    double t, double cfl, double* dt_out, void* stream) {
   if (!grid || !U_in || !U_out || !(cfl > 0.0) || !isfinite(t)) return GPMOOD_E_INVAL;
-  if (grid->dim == 1) return GPMOOD_E_INVAL;  // two-dimensional grids only
+  // two-dimensional grids only (0 is the default 2); other values are
+  // refused as gpmood_create refuses them
+  if (grid->dim != 0 && grid->dim != 2) return GPMOOD_E_INVAL;
   if (R_max < 0 || R_max > 3 || !(gamma > 1.0) || !(ell > 0.0)) return GPMOOD_E_INVAL;
   gpmood_options o;
   memset(&o, 0, sizeof(o));
@@ -1324,7 +1325,8 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   if ((grid->bc[0] == 0) != (grid->bc[1] == 0)) return GPMOOD_E_INVAL;
   if ((grid->bc[2] == 0) != (grid->bc[3] == 0)) return GPMOOD_E_INVAL;
   if (o.precision != GPMOOD_FP64 && o.precision != GPMOOD_FP32) return GPMOOD_E_INVAL;
-  if (o.rk == 4) return GPMOOD_E_INVAL;  // SSP-RK3 only: the scratch holds three states
+  // SSP-RK3 only (0 is the default 3): the scratch holds three states
+  if (o.rk != 0 && o.rk != 3) return GPMOOD_E_INVAL;
   if (o.riemann != 0 && o.riemann != 1) return GPMOOD_E_INVAL;
   if (o.recon != 0 && o.recon != 1) return GPMOOD_E_INVAL;
   if (o.recon == 1 && R_max != 1) return GPMOOD_E_INVAL;
@@ -1438,7 +1440,12 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   h->queue[0] = (int*)p; p += sz_q;
   h->queue[1] = (int*)p; p += sz_q;
   h->sc = (Scalars*)p;
-  h->hsc = &g_noalloc_host_sc;
+  // the host mirror of the scalars lives on this call's stack (pageable
+  // memory, no allocation): calls on different devices or threads share no
+  // host state
+  Scalars host_sc;
+  memset(&host_sc, 0, sizeof(host_sc));
+  h->hsc = &host_sc;
   h->stream = (cudaStream_t)stream;
 
   // what the kernels expect to start at zero: face-CAD flags and MOOD stamps

@@ -84,3 +84,27 @@ def test_create_rejects_poly3_beyond_radius_one_before_touching_the_device():
     rc = gp.load().gpmood_create(ctypes.byref(gp.make_grid(p)), 1.4, 1, 0.5, ctypes.byref(o),
                                  ctypes.byref(h))
     assert rc == -1 and not h.value
+
+
+def test_noalloc_rejects_what_create_rejects_before_touching_the_device():
+    # only SSP-RK3 (rk 0 or 3) and two-dimensional grids (dim 0 or 2); the
+    # checks run before any CUDA call, so no device is needed
+    from paper_2110_08683_gb300 import inputs as I
+
+    p = I.quadrants(n=16, R=2, seed=1)
+    lib = gp.load()
+    dummy = ctypes.c_void_p(256)  # never dereferenced: the call fails first
+    dt = ctypes.c_double(0.0)
+
+    def call(g, o):
+        return lib.gpmood_step_noalloc(ctypes.byref(g), 1.4, 2, p["ell"], ctypes.byref(o), dummy,
+                                       dummy, 0.0, 0.8, ctypes.byref(dt), None)
+
+    for rk in (1, 2, 4, 5):
+        o = gp.make_options(p)
+        o.rk = rk
+        assert call(gp.make_grid(p), o) == -1, rk
+    for dim in (1, 3, 7, -1):
+        g = gp.make_grid(p)
+        g.dim = dim
+        assert call(g, gp.make_options(p)) == -1, dim
