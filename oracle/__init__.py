@@ -80,6 +80,7 @@ def lib():
         L.orc_gp_weights_raw.argtypes = [i, i, d, d, p]
         L.orc_d2_weights.argtypes = [i, d, d, d, p, p]
         L.orc_residual.argtypes = [p, p, p, d, p]
+        L.orc_residual_cad.argtypes = [p, p, p, d, p, p]
         L.orc_dt.argtypes = [p, p, d]
         L.orc_dt.restype = d
         L.orc_step.argtypes = [p, p, d, d, d, p, p, C.POINTER(StepStats)]
@@ -242,14 +243,17 @@ class Oracle:
         lib().orc_fill_ghosts(self.h, _ptr(U), t, _ptr(Xg))
         return Xg
 
-    def residual(self, U, ord_map, t=0.0):
+    def residual(self, U, ord_map, t=0.0, want_cad=False):
+        """F_nabla at the radii ord_map; with want_cad also the per-cell
+        face-state check at those radii (1: a state of the cell failed)."""
         U = self._state(U)
         o = np.ascontiguousarray(ord_map, dtype=np.uint8)
         Fn = np.zeros_like(U)
-        rc = lib().orc_residual(self.h, _ptr(U), _ptr(o), t, _ptr(Fn))
+        cad = np.zeros((self.ny, self.nx), dtype=np.uint8)
+        rc = lib().orc_residual_cad(self.h, _ptr(U), _ptr(o), t, _ptr(Fn), _ptr(cad))
         if rc != 0:
             raise RuntimeError(rc)
-        return Fn
+        return (Fn, cad) if want_cad else Fn
 
     def dt(self, U, cfl):
         return lib().orc_dt(self.h, _ptr(self._state(U)), cfl)

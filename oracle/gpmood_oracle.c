@@ -824,6 +824,14 @@ int orc_detect_cell(orc_ctx* c, const double* Xg, int i, int j, const double* Y4
 /* the spatial operator at fixed radii                                         */
 /* ------------------------------------------------------------------------- */
 int orc_residual(orc_ctx* c, const double* U, const uint8_t* ord, double t, double* Fn) {
+  return orc_residual_cad(c, U, ord, t, Fn, 0);
+}
+
+/* the same, and (cad_out, nullable) the face-state check of every cell at
+   these radii: 1 where a state its stencil produced on one of its faces
+   failed (Sec. 3.3.1) */
+int orc_residual_cad(orc_ctx* c, const double* U, const uint8_t* ord, double t, double* Fn,
+                     uint8_t* cad_out) {
   int nx = c->cfg.nx, ny = c->cfg.ny;
   for (size_t k = 0; k < (size_t)nx * ny; ++k) {
     int R = ord[k];
@@ -838,6 +846,7 @@ int orc_residual(orc_ctx* c, const double* U, const uint8_t* ord, double t, doub
       fnabla(c, i, j, f);
       for (int v = 0; v < NV; ++v) Fn[iidx(c, v, i, j)] = f[v];
     }
+  if (cad_out) memcpy(cad_out, c->cad, (size_t)nx * ny);
   return 0;
 }
 

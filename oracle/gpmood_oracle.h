@@ -116,6 +116,8 @@ void orc_hllc(const double* UL, const double* UR, double gamma, int dir, double*
 void orc_hll(const double* UL, const double* UR, double gamma, int dir, double* F);
 /* F_nabla (eq. fvm_F) of the interior state U at per-cell radii ord (EDP1 faces) */
 int orc_residual(orc_ctx* ctx, const double* U, const uint8_t* ord, double t, double* Fn);
+int orc_residual_cad(orc_ctx* ctx, const double* U, const uint8_t* ord, double t, double* Fn,
+                     uint8_t* cad_out);
 /* Delta t from U (per-direction CFL form) */
 double orc_dt(orc_ctx* ctx, const double* U, double cfl);
 /* one SSP-RK3 (or SSP-RK4, cfg.rk = 4) step with the MOOD loop; dt_fixed > 0

@@ -625,3 +625,100 @@ def test_fog_equals_a_textbook_godunov_loop():
         U = U / 3.0 + 2.0 / 3.0 * (U2 + dt * L(U2))
     rel = np.abs(Uo[:, 0, :] - U).max() / np.abs(U).max()
     assert rel < 1e-13, rel
+
+
+# --------------------------------------------------------------------------
+# the time step on a hand-built non-uniform state (per-direction CFL bound)
+# --------------------------------------------------------------------------
+def test_time_step_of_a_hand_built_state():
+    """A 4 x 3 grid with dx = 0.1, dy = 0.05.  Background: rho = 1, at rest,
+    p = 1/1.4, so c = 1: bounds dx/1 = 0.1 and dy/1 = 0.05.  Cell A: u = 2,
+    so (|u| + c) = 3 and dx/3 = 0.0333.  Cell B: rho = 4, v = -0.5 and
+    p = 1.5^2 * 4 / 1.4, so c = 1.5: dy/(0.5 + 1.5) = 0.025 is the smallest
+    bound of the grid.  At CFL 0.8 the step is 0.8 * 0.025 = 0.02 exactly
+    (worked by hand).  A sum-form bound, a missing sound speed, a maximum in
+    place of the minimum or dx used for both directions all give another
+    number (0.01455, inf, 0.08, 0.02667)."""
+    g = 1.4
+    p = I.uniform(4, 3, R=1, state=(1.0, 0.0, 0.0, 1.0 / g), bc="outflow")
+    p.update(x0=0.0, x1=0.4, y0=0.0, y1=0.15)
+    U = cons(np.ones((3, 4)), np.zeros((3, 4)), np.zeros((3, 4)), np.full((3, 4), 1.0 / g))
+    U[:, 1, 2] = cons(1.0, 2.0, 0.0, 1.0 / g)                 # cell A
+    U[:, 2, 0] = cons(4.0, 0.0, -0.5, 1.5 ** 2 * 4.0 / g)     # cell B
+    o = O.Oracle(p)
+    assert o.dt(U, 0.8) == pytest.approx(0.02, rel=1e-14)
+    # without cell B the bound of cell A decides: 0.8 * 0.1 / 3
+    U[:, 2, 0] = cons(1.0, 0.0, 0.0, 1.0 / g)
+    assert o.dt(U, 0.8) == pytest.approx(0.8 / 30.0, rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# the MOOD loop against brute force: re-detect every cell every iteration
+# --------------------------------------------------------------------------
+def brute_force_stage(o, X, ts, dt):
+    """Sec. 4 Steps 3-10 taken literally: start every cell at the top
+    radius; in every iteration recompute all faces at the current radii
+    (EDP1), form every candidate and run the detection on every non-FOG
+    cell (face-state check, then Steps 4-9); lower the troubled cells by one
+    cascade level; stop when no cell is troubled.  Returns the candidate,
+    final radii, first-pass map, iteration count and the number of cells
+    first troubled after the first pass (cells that only a neighbour's
+    lowering made troubled)."""
+    cas = list(o.prob["cascade"])
+    nxt = {r: cas[k + 1] for k, r in enumerate(cas[:-1])}
+    ordm = np.full((o.ny, o.nx), cas[0], dtype=np.uint8)
+    Xg = o.fill_ghosts(X, ts)
+    first, iters, late = None, 0, 0
+    ever = np.zeros((o.ny, o.nx), dtype=bool)
+    while True:
+        Fn, cad = o.residual(X, ordm, ts, want_cad=True)
+        Y = X - dt * Fn
+        bad = np.zeros((o.ny, o.nx), dtype=bool)
+        for j in range(o.ny):
+            for i in range(o.nx):
+                if ordm[j, i] == 0:
+                    continue  # Step 10: FOG is accepted as it is
+                bad[j, i] = cad[j, i] or o.detect_cell(Xg, i, j, Y[:, j, i]) < 0
+        if first is None:
+            first = bad.copy()
+        else:
+            late += int((bad & ~ever).sum())
+        ever |= bad
+        if not bad.any():
+            return Y, ordm, first, iters, late
+        iters += 1
+        for j, i in zip(*np.nonzero(bad)):
+            ordm[j, i] = nxt[int(ordm[j, i])]
+
+
+@pytest.mark.parametrize("case", ["sod_1d", "quadrants_r3", "quadrants_r2", "nan_cell"])
+def test_mood_loop_equals_brute_force_redetection(case):
+    """The oracle re-detects only the queued cells and their face
+    neighbours after each MOOD iteration (the cells whose candidate
+    changed); re-detecting every cell every iteration must give the same
+    radii, candidate and iteration count.  A loop that re-detected the
+    queued cells alone would miss the neighbours that a lowering makes
+    troubled: the cases are chosen so that such cells exist."""
+    if case == "sod_1d":
+        p = I.sod_1d(n=64, R=2)
+    elif case == "quadrants_r3":
+        p = I.quadrants(n=20, ny=18, R=3, seed=2)
+    elif case == "quadrants_r2":
+        p = I.quadrants(n=20, ny=16, R=2, seed=5)
+    else:
+        p = I.vortex(n=16, R=3)
+        p["U0"] = p["U0"].copy()
+        p["U0"][:, 8, 8] = np.nan
+    o = O.Oracle(p)
+    X = p["U0"]
+    dt = o.dt(X, 0.8) if case != "nan_cell" else 1e-3
+    Yo, ordo, firsto, iterso, _ = o.stage(X, 0.0, dt)
+    Yb, ordb, firstb, itersb, late = brute_force_stage(o, X, 0.0, dt)
+    assert np.array_equal(firsto.astype(bool), firstb)
+    assert np.array_equal(ordo, ordb), np.argwhere(ordo != ordb)[:10]
+    assert iterso == itersb
+    fin = np.isfinite(Yb)
+    assert np.array_equal(fin, np.isfinite(Yo))
+    assert np.array_equal(Yo[fin], Yb[fin])
+    if case.startswith("quadrants"):
+        assert iterso >= 2 and late > 0, (iterso, late)
