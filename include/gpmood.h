@@ -64,7 +64,10 @@ enum {
   GPMOOD_E_MOOD_CAP = -5,  /* the MOOD loop reached max_mood_iters with cells still flagged */
   GPMOOD_E_DT = -6,        /* the time step came out non-positive or not finite */
   GPMOOD_E_NOSTATE = -7,   /* step/run/get before set_state */
-  GPMOOD_E_TOO_BIG = -8    /* grid needs more than the static scratch of gpmood_step_noalloc */
+  GPMOOD_E_TOO_BIG = -8,   /* grid needs more than the static scratch of gpmood_step_noalloc */
+  GPMOOD_E_SYNC = -9       /* a grid-wide barrier of the MOOD loop kernel waited more than
+                              about a second (its blocks were not all resident); the step
+                              failed and the state is as before it */
 };
 
 /* grid and boundary description (Sec. 2.1); caller-owned, copied at create */
@@ -100,12 +103,13 @@ typedef struct {
                            Dt F(U^(3)) term of the final combination read with a minus
                            sign; each stage's MOOD candidate is its forward-Euler
                            sub-step.  Single-problem handles, no adjoint */
-  int eager;            /* 0: one captured CUDA graph per step, the MOOD loop of each stage
-                           a conditional WHILE node (no host round trip in a step);
-                           1: every kernel launched on the stream and the host reading the
-                           loop decision after each MOOD iteration.  Same kernels, same
-                           results; slower, but visible kernel by kernel to profilers
-                           that cannot look inside graphs with conditional nodes */
+  int eager;            /* 0: one captured CUDA graph per step (no host round trip in a
+                           step); 1: every kernel launched on the stream and the host
+                           reading the step's counters after each stage.  Either way the
+                           MOOD loop of a stage is one cooperative kernel that iterates on
+                           the device.  Same kernels, same results; eager is slower, but
+                           visible kernel by kernel to profilers that cannot look inside
+                           graphs with conditional nodes */
   int recon;            /* 0: GP reconstruction (GP-MOOD).  1: POL-MOOD3 (Sec. 3.1 (iv)):
                            the R = 1 rung is Poly3, the quadratic of eq. poly3 fitted to
                            the five cell averages of the R = 1 stencil (eq. p3_coeffs),

@@ -27,7 +27,8 @@ FP64, FP32 = 0, 1
 E_CODES = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "device allocation failed",
            -4: "GP covariance matrix not positive definite", -5: "MOOD iteration cap reached",
            -6: "time step not positive or not finite", -7: "no state set",
-           -8: "grid too large for the static scratch"}
+           -8: "grid too large for the static scratch",
+           -9: "a grid-wide barrier of the MOOD loop timed out"}
 
 
 class GpmoodError(RuntimeError):

@@ -44,6 +44,8 @@ struct gpmood_s {
   int has_state;
   int launches;
   int last_status;
+  int mood_blocks;  // grid of the MOOD loop kernel (co-resident blocks)
+  int coop;         // 1: the MOOD loop kernel is launched cooperatively
   // optional per-class event timing (graph steps)
   int prof_on;
   double prof_ms[GPMOOD_NKCLASS];
@@ -252,7 +254,7 @@ void mark_synced(gpmood_t h) {
 }
 
 int step_error(gpmood_t h);
-int step_launches(const Scalars& s, int nstages, int gated);
+int step_launches(const gpmood_t h, int gated);
 
 // wait for the queued asynchronous steps and settle the buffer rotation: the
 // steps that ran are a prefix of those queued (the gate closes for good), and
@@ -268,7 +270,7 @@ int settle(gpmood_t h) {
   const long long m = h->hsc->nsteps - h->sync_nsteps;
   const int nb = h->sch.nbuf;
   h->cur = (int)((h->sync_cur + (m % nb) * h->sch.advance) % nb);
-  h->launches = step_launches(*h->hsc, h->sch.nstages, 1);
+  h->launches = step_launches(h, 1);
   mark_synced(h);
   const int e = step_error(h);
   h->last_status = e;
@@ -302,17 +304,18 @@ int push_control_if_changed(gpmood_t h) {
 }
 
 // kernels launched by one step: the gate of a gated graph (1), dt (2), per
-// stage fill, faces x/y, update, begin (5), 4 per MOOD iteration, finish (1)
-int step_base_launches(int nstages, int gated) { return (gated ? 1 : 0) + 2 + nstages * 5 + 1; }
-int step_launches(const Scalars& s, int nstages, int gated) {
-  int n = step_base_launches(nstages, gated);
-  for (int k = 0; k < nstages; ++k) n += 4 * s.iters[k];
-  return n;
+// stage fill, faces x (and y in 2D), update, the MOOD loop, finish (1)
+int step_base_launches(int nstages, int dim, int gated) {
+  return (gated ? 1 : 0) + 2 + nstages * (dim == 2 ? 5 : 4) + 1;
+}
+int step_launches(const gpmood_t h, int gated) {
+  return step_base_launches(h->sch.nstages, h->g.dim, gated);
 }
 
 int step_error(gpmood_t h) {
   if (h->hsc->err & kErrDt) return set_err(h, GPMOOD_E_DT);
   if (h->hsc->err & kErrCap) return set_err(h, GPMOOD_E_MOOD_CAP);
+  if (h->hsc->err & kErrSync) return set_err(h, GPMOOD_E_SYNC);
   return GPMOOD_OK;
 }
 
@@ -336,26 +339,38 @@ int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const Parity
   return 0;
 }
 
-// ---- eager step: the host reads the loop decision after every iteration.
-// Used by gpmood_step_noalloc, which must not build graphs. ----
+// the MOOD loop of stage s: one launch; a driver that refuses the
+// cooperative launch gets a plain launch of the same co-resident grid from
+// then on (the kernel's barrier waits are bounded either way)
+template <class Real>
+int mood_loop(gpmood_t h, const StageArgs<Real>& A, int s, const DirectW<Real>& D,
+              cudaStream_t st) {
+  const MoodArgs M = mood_args<Real>(h);
+  cudaError_t e =
+      Launch<Real>::mood_loop(A, M, h->g, h->det, D, h->cas, s, h->mood_blocks, h->coop, st);
+  if (e != cudaSuccess && h->coop) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      h->coop = 0;
+      e = Launch<Real>::mood_loop(A, M, h->g, h->det, D, h->cas, s, h->mood_blocks, 0, st);
+    }
+  }
+  CK(e);
+  return 0;
+}
+
+// ---- eager step: stream launches, the host reads the scalars after every
+// stage.  Used by gpmood_step_noalloc, which must not build graphs. ----
 template <class Real>
 int eager_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const DirectW<Real>& D) {
   StageArgs<Real> A = stage_args<Real>(h, s, rot);
   const int ix = buf_of(h, rot, h->sch.st[s].in);
   int rc = first_pass<Real>(h, A, ix, s, P, D, h->stream);
   if (rc) return rc;
-  CK(launch_mood_begin(h->sc, s, 0, 0, h->stream));
-  const MoodArgs M = mood_args<Real>(h);
-  for (;;) {
-    rc = pull_scalars(h);
-    if (rc) return rc;
-    if (!h->hsc->go) break;
-    CK(launch_lower(M, A.ord, h->cas, h->stream));
-    CK(Launch<Real>::mood_faces(A, M, h->g, D, h->cas, h->stream));
-    CK(Launch<Real>::mood_update(A, M, h->g, h->det, D, h->stream));
-    CK(launch_mood_end(h->sc, s, 0, 0, h->stream));
-  }
-  return 0;
+  rc = mood_loop<Real>(h, A, s, D, h->stream);
+  if (rc) return rc;
+  return pull_scalars(h);
 }
 
 // copy the interior of a ghosted state to an interior array (device)
@@ -394,10 +409,10 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     if (otape) CK(cudaMemcpyAsync(otape + s * nc, h->ord + s * nc, nc, cudaMemcpyDeviceToDevice,
                                   h->stream));
   }
-  CK(launch_finish(h->sc, step_base_launches(h->sch.nstages, 0), h->stream));
+  CK(launch_finish(h->sc, step_base_launches(h->sch.nstages, h->g.dim, 0), h->stream));
   rc = pull_scalars(h);
   if (rc) return rc;
-  h->launches = step_launches(*h->hsc, h->sch.nstages, 0);
+  h->launches = step_launches(h, 0);
   h->cur = buf_of(h, a, h->sch.advance);
   mark_synced(h);
   h->last_status = GPMOOD_OK;
@@ -435,38 +450,10 @@ int capture_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const Dire
   rec_event(h, prof, GPMOOD_K_FACES_Y, 0, st);
   rec_event(h, prof, GPMOOD_K_UPDATE, 1, st);
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
-  // the WHILE node's condition, reset to 0 at every launch of the graph
-  cudaStreamCaptureStatus cs;
-  cudaGraph_t graph;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle hc;
-  CK(cudaGraphConditionalHandleCreate(&hc, graph, 0, cudaGraphCondAssignDefault));
-  CK(launch_mood_begin(h->sc, s, hc, 1, st));
   rec_event(h, prof, GPMOOD_K_UPDATE, 0, st);
   rec_event(h, prof, GPMOOD_K_MOOD, 1, st);
-  CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = hc;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t cnode;
-  CK(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  // the loop body, captured on the second stream into the node's graph
-  CK(cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0,
-                                   cudaStreamCaptureModeThreadLocal));
-  const MoodArgs M = mood_args<Real>(h);
-  cudaError_t e1 = launch_lower(M, A.ord, h->cas, h->cs2);
-  cudaError_t e2 = Launch<Real>::mood_faces(A, M, h->g, D, h->cas, h->cs2);
-  cudaError_t e3 = Launch<Real>::mood_update(A, M, h->g, h->det, D, h->cs2);
-  cudaError_t e4 = launch_mood_end(h->sc, s, hc, 1, h->cs2);
-  cudaGraph_t tmp;
-  CK(cudaStreamEndCapture(h->cs2, &tmp));
-  CK(e1); CK(e2); CK(e3); CK(e4);
-  CK(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  int rc = mood_loop<Real>(h, A, s, D, st);
+  if (rc) return rc;
   rec_event(h, prof, GPMOOD_K_MOOD, 0, st);
   if (record) {
     k_tape_ord<<<152, 256, 0, st>>>(A.ord, h->sc, s, (long long)h->g.nx * h->g.ny);
@@ -528,7 +515,8 @@ int capture_step_impl(gpmood_t h, int cur, int prof, int record, int gated,
     rc = h->precision == GPMOOD_FP32
              ? capture_stage<float>(h, s, a, h->pw32, h->dw32, prof, record, bs)
              : capture_stage<double>(h, s, a, h->pw64, h->dw64, prof, record, bs);
-  if (!rc && launch_finish(h->sc, step_base_launches(h->sch.nstages, gated), bs) != cudaSuccess)
+  if (!rc &&
+      launch_finish(h->sc, step_base_launches(h->sch.nstages, h->g.dim, gated), bs) != cudaSuccess)
     rc = GPMOOD_E_CUDA;
   if (body_open) {
     cudaGraph_t tmp = nullptr;
@@ -558,6 +546,12 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
     // stream order from now on
     h->pdl = 0;
     g_pdl = 0;
+    rc = capture_step_impl(h, cur, prof, record, want_gate, out);
+  }
+  if (rc && h->coop) {
+    // the driver refused a cooperative kernel node: a plain launch of the
+    // same co-resident grid
+    h->coop = 0;
     rc = capture_step_impl(h, cur, prof, record, want_gate, out);
   }
   if (rc && want_gate && h->gated_ok == 0) {
@@ -597,19 +591,18 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
       if (cudaEventElapsedTime(&ms, h->gev[2 * k], h->gev[2 * k + 1]) == cudaSuccess)
         h->prof_ms[h->gev_cls[k]] += ms;
     }
-    const Scalars& s = *h->hsc;
     const int S = h->sch.nstages;
-    h->prof_n[GPMOOD_K_DT] += 3;
+    h->prof_n[GPMOOD_K_DT] += 2;
     h->prof_n[GPMOOD_K_GHOST] += S;
     h->prof_n[GPMOOD_K_FACES_X] += S;
     h->prof_n[GPMOOD_K_FACES_Y] += h->g.dim == 2 ? S : 0;
-    h->prof_n[GPMOOD_K_UPDATE] += 2 * S;
-    for (int k = 0; k < S; ++k) h->prof_n[GPMOOD_K_MOOD] += 4 * s.iters[k];
+    h->prof_n[GPMOOD_K_UPDATE] += S;
+    h->prof_n[GPMOOD_K_MOOD] += S;
   }
   mark_synced(h);
   rc = step_error(h);
   if (rc) return rc;
-  h->launches = step_launches(*h->hsc, h->sch.nstages, gated);
+  h->launches = step_launches(h, gated);
   h->cur = buf_of(h, h->cur, h->sch.advance);
   mark_synced(h);
   h->last_status = GPMOOD_OK;
@@ -704,6 +697,7 @@ const char* gpmood_strerror(int code) {
     case GPMOOD_E_DT: return "time step not positive or not finite";
     case GPMOOD_E_NOSTATE: return "no state set";
     case GPMOOD_E_TOO_BIG: return "grid too large for the static scratch";
+    case GPMOOD_E_SYNC: return "a grid-wide barrier of the MOOD loop timed out";
     default: return "unknown error";
   }
 }
@@ -802,6 +796,13 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->precision = o.precision;
   h->eager = o.eager ? 1 : 0;
   h->pdl = o.serial_launch ? 0 : 1;
+  h->coop = 1;
+  h->mood_blocks = h->precision == GPMOOD_FP32 ? Launch<float>::mood_loop_blocks()
+                                               : Launch<double>::mood_loop_blocks();
+  if (h->mood_blocks <= 0) {
+    delete h;
+    return GPMOOD_E_CUDA;
+  }
   // a safety net only: radii never rise, so the loop ends; chains of
   // re-detected neighbours can take O(grid width) iterations
   h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
@@ -1401,6 +1402,10 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   // re-detected neighbours can take O(grid width) iterations
   h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
                                       : 64 + 4 * (grid->nx > grid->ny ? grid->nx : grid->ny);
+  h->coop = 1;
+  h->mood_blocks = h->precision == GPMOOD_FP32 ? Launch<float>::mood_loop_blocks()
+                                               : Launch<double>::mood_loop_blocks();
+  if (h->mood_blocks <= 0) return GPMOOD_E_CUDA;
 
   // GP weights: binary128 solve on the host stack
   gpw_radius wr[4];

@@ -68,10 +68,13 @@ struct Scalars {
   long long nsteps;
   long long launches;           // kernels launched by graph steps since the state was set
   int nactive;                  // batches: problems still advancing in this step
+  unsigned int bar_count;       // grid barrier of the MOOD loop kernel: arrivals
+  unsigned int bar_gen;         // and generation (count returns to 0 after each use)
 };
 
 constexpr int kErrDt = 1;       // non-finite or non-positive time step
 constexpr int kErrCap = 2;      // MOOD iteration cap reached
+constexpr int kErrSync = 4;     // a grid barrier of the MOOD loop kernel gave up waiting
 
 // parity-decomposed prediction weights of one radius for the first pass
 // (see the stencil-symmetry note in the face kernels)

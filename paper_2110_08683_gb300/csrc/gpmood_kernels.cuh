@@ -1,17 +1,19 @@
 // gpmood_kernels.cuh -- CUDA kernels of the GP-MOOD stage (sm_103a).
 //
-// One RK stage (Sec. 4, Steps 3-10) runs as
+// One RK stage (Sec. 4, Steps 3-10) of a single problem runs as
 //   fill_ghosts -> x_faces -> y_faces -> update_first    (first pass, all cells)
-//   [mood_lower -> mood_faces -> mood_update]*            (troubled cells only)
+//   mood_loop                                             (troubled cells only)
 // x_faces / y_faces reconstruct the pointwise Riemann states of eq.
 // gp_reconstructor at the Gauss points of Table QR, apply face-state CAD
 // (Sec. 3.3.1), solve HLLC and store the face-averaged flux of eq. fvm_F.
 // update_first forms the candidate of eq. fvm_discrete, runs Steps 4-9,
 // writes the SSP-RK3 combination (eq. rk3) and appends troubled cells to a
-// queue with one atomic per warp.  The MOOD kernels lower the order of queued
-// cells by one cascade level, recompute the faces whose EDP1 order changed
-// (Sec. 3.6) and re-update + re-detect the queued cells and their face
-// neighbours.
+// queue with one atomic per warp.  mood_loop iterates on the device, with
+// grid-wide barriers between its phases: it lowers the order of queued cells
+// by one cascade level, recomputes the faces whose EDP1 order changed (Sec.
+// 3.6) and re-updates + re-detects the queued cells and their face
+// neighbours, until no cell is troubled.  Batches run the same phases as one
+// kernel per phase, the loop a conditional WHILE node of the step graph.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -940,49 +942,56 @@ __device__ __forceinline__ void recon_direct(const T* X, const Grid& g, const Re
   }
 }
 
+// Riemann flux at Gauss point q of the face between cell (iL,jL) and its
+// neighbour (iR,jR) in direction DIR at radius K; badL / badR gather the
+// face-state check of the two reconstructed states
+template <int K, class Real, int DIR>
+__device__ __forceinline__ void face_point(const Real* X, const Grid& g, const DirectW<Real>& Wd,
+                                           int iL, int jL, int q, Real* f, bool& badL,
+                                           bool& badR) {
+  const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
+  const Real gam = (Real)g.gamma;
+  Real UL[4], UR[4];
+  if (K == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      UL[v] = __ldg(X + gidx(g, v, iL, jL));
+      UR[v] = __ldg(X + gidx(g, v, iR, jR));
+    }
+  } else {
+    // faces: 0 E, 1 W, 2 N, 3 S
+    recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
+    recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
+  }
+  Real pl, pr;
+  if (DIR == 0) {
+    riemann_x<Real>(g.riemann, UL, UR, gam, f, pl, pr);
+  } else {
+    Real a[4] = {UL[0], UL[2], UL[1], UL[3]};
+    Real b[4] = {UR[0], UR[2], UR[1], UR[3]};
+    Real h[4];
+    riemann_x<Real>(g.riemann, a, b, gam, h, pl, pr);
+    f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
+  }
+  badL |= !(pos_finite(UL[0]) && pos_finite(pl));
+  badR |= !(pos_finite(UR[0]) && pos_finite(pr));
+}
+
 // face between cell (iL,jL) and its neighbour (iR,jR) in direction DIR at radius K
 template <int K, class Real, int DIR>
 __device__ void face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, int iL, int jL,
                         Real* F, bool& badL, bool& badR) {
   constexpr int Q = rule_q(K);
-  const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
-  const Real gam = (Real)g.gamma;
   F[0] = F[1] = F[2] = F[3] = Real(0);
   badL = badR = false;
-  auto point = [&](int q, Real* f) {
-    Real UL[4], UR[4];
-    if (K == 0) {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        UL[v] = __ldg(X + gidx(g, v, iL, jL));
-        UR[v] = __ldg(X + gidx(g, v, iR, jR));
-      }
-    } else {
-      // faces: 0 E, 1 W, 2 N, 3 S
-      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 0 : 2][q], iL, jL, UL);
-      recon_direct<K, Real>(X, g, Wd.z[K][DIR == 0 ? 1 : 3][q], iR, jR, UR);
-    }
-    Real pl, pr;
-    if (DIR == 0) {
-      riemann_x<Real>(g.riemann, UL, UR, gam, f, pl, pr);
-    } else {
-      Real a[4] = {UL[0], UL[2], UL[1], UL[3]};
-      Real b[4] = {UR[0], UR[2], UR[1], UR[3]};
-      Real h[4];
-      riemann_x<Real>(g.riemann, a, b, gam, h, pl, pr);
-      f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
-    }
-    badL |= !(pos_finite(UL[0]) && pos_finite(pl));
-    badR |= !(pos_finite(UR[0]) && pos_finite(pr));
-  };
   // mirror pairs (g, -g) summed first, in the order of the first-pass sweep
 #pragma unroll
   for (int kk = 0; kk < (Q + 1) / 2; ++kk) {
     Real f1[4];
-    point(kk, f1);
+    face_point<K, Real, DIR>(X, g, Wd, iL, jL, kk, f1, badL, badR);
     if (Q - 1 - kk != kk) {
       Real f2[4];
-      point(Q - 1 - kk, f2);
+      face_point<K, Real, DIR>(X, g, Wd, iL, jL, Q - 1 - kk, f2, badL, badR);
 #pragma unroll
       for (int v = 0; v < 4; ++v) F[v] = fma(Wd.w[K][kk], add_rn(f1[v], f2[v]), F[v]);
     } else {
@@ -992,20 +1001,12 @@ __device__ void face_at(const Real* X, const Grid& g, const DirectW<Real>& Wd, i
   }
 }
 
+// the flux and state-check bits of the face between (iL,jL) and its
+// neighbour in direction DIR; a periodic seam face writes both copies
 template <class Real, int DIR>
-__device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const DirectW<Real>& Wd,
-                               int iL, int jL, int K) {
-  Real F[4];
-  bool bl, br;
-  switch (K) {
-    case 0: face_at<0, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-    case 1: face_at<1, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-    case 2: face_at<2, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-    default: face_at<3, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-  }
+__device__ __forceinline__ void store_face(const StageArgs<Real>& A, const Grid& g, int iL,
+                                           int jL, const Real* F, uint8_t bits) {
   const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
-  // the face's state-check bits; a periodic seam face writes both copies
-  const uint8_t bits = (uint8_t)((bl ? 1 : 0) | (br ? 2 : 0));
   if (DIR == 0) {
     int f = iR;  // face index
 #pragma unroll
@@ -1031,30 +1032,125 @@ __device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const Di
   }
 }
 
+template <class Real, int DIR>
+__device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const DirectW<Real>& Wd,
+                               int iL, int jL, int K) {
+  Real F[4];
+  bool bl, br;
+  switch (K) {
+    case 0: face_at<0, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    case 1: face_at<1, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    case 2: face_at<2, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+    default: face_at<3, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
+  }
+  store_face<Real, DIR>(A, g, iL, jL, F, (uint8_t)((bl ? 1 : 0) | (br ? 2 : 0)));
+}
+
 // face f (0 W, 1 E, 2 S, 3 N) of queued cell c: recompute it if its EDP1
 // radius changed; the face shared with another queued cell is done by the
 // west/south one
+// false when the face needs no work; else its left/lower cell (iL, jL) and
+// its new EDP1 radius K
 template <class Real>
-__device__ __forceinline__ void mood_face_item(const StageArgs<Real>& A, const Grid& g,
-                                               const DirectW<Real>& Wd, const Cascade& C,
-                                               const uint32_t* stamp, uint32_t cur, int c, int f) {
+__device__ __forceinline__ bool mood_face_plan(const StageArgs<Real>& A, const Grid& g,
+                                               const Cascade& C, const uint32_t* stamp,
+                                               uint32_t cur, int c, int f, int& iL, int& jL,
+                                               int& K) {
   const int i = c % g.nx, j = c / g.nx;
-  if (f >= 2 && g.dim == 1) return;  // no y faces in 1D
+  if (f >= 2 && g.dim == 1) return false;  // no y faces in 1D
   if (f == 0 || f == 2) {
     int nb = neighbour(g, i, j, f);
-    if (nb >= 0 && stamp[nb] == cur) return;
+    if (nb >= 0 && stamp[nb] == cur) return false;
   }
-  int iL = i, jL = j;
+  iL = i;
+  jL = j;
   if (f == 0) iL = i - 1;
   if (f == 2) jL = j - 1;
   const int iR = iL + (f < 2), jR = jL + (f >= 2);
   int nl, bl, nr, br;
   radius_pair(g, A.ord, stamp, cur, C, iL, jL, nl, bl);
   radius_pair(g, A.ord, stamp, cur, C, iR, jR, nr, br);
-  int Knew = nl < nr ? nl : nr, Kold = bl < br ? bl : br;
-  if (Knew == Kold) return;  // EDP1 order of this face unchanged
-  if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, Knew);
-  else recompute_face<Real, 1>(A, g, Wd, iL, jL, Knew);
+  K = nl < nr ? nl : nr;
+  const int Kold = bl < br ? bl : br;
+  return K != Kold;  // else the EDP1 order of this face is unchanged
+}
+
+template <class Real>
+__device__ __forceinline__ void mood_face_item(const StageArgs<Real>& A, const Grid& g,
+                                               const DirectW<Real>& Wd, const Cascade& C,
+                                               const uint32_t* stamp, uint32_t cur, int c, int f) {
+  int iL, jL, K;
+  if (!mood_face_plan<Real>(A, g, C, stamp, cur, c, f, iL, jL, K)) return;
+  if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, K);
+  else recompute_face<Real, 1>(A, g, Wd, iL, jL, K);
+}
+
+template <class Real, int DIR>
+__device__ __forceinline__ void face_point_k(int K, const Real* X, const Grid& g,
+                                             const DirectW<Real>& Wd, int iL, int jL, int q,
+                                             Real* f, bool& bl, bool& br) {
+  switch (K) {
+    case 0: face_point<0, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
+    case 1: face_point<1, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
+    case 2: face_point<2, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
+    default: face_point<3, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
+  }
+}
+
+// the MOOD face recompute of queued cells with one lane per Gauss point:
+// lane t covers cell queue[t / 16], face (t / 4) % 4, point t % 4.  Each
+// lane reconstructs its point's two states and solves its Riemann problem;
+// the group's first lane forms the Gauss sum in the order of face_at (mirror
+// pairs summed first), so the flux is the same bit for bit, with a quarter
+// of the dependent-operation chain per thread.  Called by whole warps.
+template <class Real>
+__device__ __forceinline__ void mood_faces_lanes(const StageArgs<Real>& A, const Grid& g,
+                                                 const DirectW<Real>& Wd, const Cascade& C,
+                                                 const uint32_t* stamp, uint32_t cur,
+                                                 const int* queue, int n, long long gtid0,
+                                                 long long stride) {
+  const long long L = 16LL * n;
+  const int lane = threadIdx.x & 31;
+  const int base = lane & ~3;
+  // the loop runs per warp: all 32 lanes take part in the shuffles
+  for (long long t0 = gtid0 - lane; t0 < L; t0 += stride) {
+    const long long t = t0 + lane;
+    const int q = (int)(t & 3);
+    const int f = (int)((t >> 2) & 3);
+    int iL = 0, jL = 0, K = 0;
+    bool work = false;
+    if (t < L) work = mood_face_plan<Real>(A, g, C, stamp, cur, queue[t >> 4], f, iL, jL, K);
+    const int Q = rule_q(K);
+    Real fq[4] = {Real(0), Real(0), Real(0), Real(0)};
+    bool bl = false, br = false;
+    if (work && q < Q) {
+      if (f < 2) face_point_k<Real, 0>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br);
+      else face_point_k<Real, 1>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br);
+    }
+    Real fp[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) fp[p][v] = __shfl_sync(0xffffffffu, fq[v], base + p);
+    const unsigned bbl = __ballot_sync(0xffffffffu, bl), bbr = __ballot_sync(0xffffffffu, br);
+    if (work && q == 0) {
+      // face_at's loop over (g, -g) pairs written out per rule size
+      const Real w0 = Wd.w[K][0], w1 = Wd.w[K][1];
+      Real F[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const Real z = Real(0);
+        if (Q == 4) F[v] = fma(w1, add_rn(fp[1][v], fp[2][v]), fma(w0, add_rn(fp[0][v], fp[3][v]), z));
+        else if (Q == 3) F[v] = fma(w1, fp[1][v], fma(w0, add_rn(fp[0][v], fp[2][v]), z));
+        else if (Q == 2) F[v] = fma(w0, add_rn(fp[0][v], fp[1][v]), z);
+        else F[v] = fma(w0, fp[0][v], z);
+      }
+      const uint8_t bits = (uint8_t)((((bbl >> base) & 0xFu) ? 1 : 0) |
+                                     (((bbr >> base) & 0xFu) ? 2 : 0));
+      if (f < 2) store_face<Real, 0>(A, g, iL, jL, F, bits);
+      else store_face<Real, 1>(A, g, iL, jL, F, bits);
+    }
+  }
 }
 
 // entry k (0 itself, 1 W, 2 E, 3 S, 4 N) of queued cell c's neighbourhood:
@@ -1141,6 +1237,118 @@ __global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs
       if (live) flag = mood_update_item<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, M.stamp, cur, c, k, d);
       queue_push(flag, d, next_queue, next_count);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the whole MOOD loop of one stage in one cooperative launch (Sec. 4 Step 10:
+// repeat until no cell is flagged).  Every block takes part in every phase of
+// every iteration, separated by grid-wide barriers:
+//   lower the queued cells one cascade level  | barrier
+//   recompute the faces whose EDP1 radius changed  | barrier
+//   re-update + re-detect the queued cells and their face neighbours,
+//   troubled ones into the other queue  | barrier
+// and every block reads the new queue length to take the same decision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// grid-wide barrier of a co-resident grid: the last block to arrive resets
+// the count and opens the next generation.  A wait gives up after about a
+// second (or 2^26 polls), latches kErrSync and returns false; a block that
+// sees the error leaves the loop, so no wait can outlast the limit.
+__device__ __forceinline__ bool grid_barrier(Scalars* sc) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &sc->bar_gen;
+    volatile int* err = &sc->err;
+    const unsigned g0 = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(&sc->bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(&sc->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&sc->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
+      while (*gen == g0) {
+        if (++polls > (1u << 26) || global_ns() - t0 > 1000000000ull) {
+          atomicOr(&sc->err, kErrSync);
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+    }
+    if (*err & kErrSync) good = 0;
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_mood_loop(StageArgs<Real> A, MoodArgs M, Grid g,
+                                                   Detect D,
+                                                   const __grid_constant__ DirectW<Real> Wd,
+                                                   Cascade C, int stage) {
+  pdl_wait();
+  Scalars* sc = M.sc;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // the first pass filled queue 0; queue 1 receives the first iteration's
+  // troubled cells (its count is cleared here, read after two barriers)
+  int n = *(volatile int*)&sc->count[0];
+  const int nfirst = n;
+  int slot = 0, iters = 0, total = n;
+  unsigned cur = sc->stamp_cur;
+  const int cap = sc->ctl.max_iters;
+  if (leader) sc->count[1] = 0;
+  while (n > 0) {
+    if (iters >= cap) {
+      if (leader) atomicOr(&sc->err, kErrCap);
+      break;
+    }
+    cur += 1;  // stamp of the cells of this iteration's queue
+    const int* queue = M.queue[slot];
+    for (long long q = gtid; q < n; q += stride) {
+      const int c = queue[q];
+      A.ord[c] = (uint8_t)C.next[A.ord[c]];
+      M.stamp[c] = cur;
+    }
+    if (!grid_barrier(sc)) break;
+    mood_faces_lanes<Real>(A, g, Wd, C, M.stamp, cur, queue, n, gtid, stride);
+    if (!grid_barrier(sc)) break;
+    int* next_queue = M.queue[slot ^ 1];
+    int* next_count = &sc->count[slot ^ 1];
+    for (long long t = gtid; t < 5LL * n; t += stride) {
+      int d = -1;
+      const bool flag = mood_update_item<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, M.stamp, cur,
+                                               queue[t / 5], (int)(t % 5), d);
+      queue_push(flag, d, next_queue, next_count);
+    }
+    if (!grid_barrier(sc)) break;
+    n = *(volatile int*)next_count;
+    // the queue just worked on receives the next iteration's cells
+    if (leader) sc->count[slot] = 0;
+    total += n;
+    iters += 1;
+    slot ^= 1;
+  }
+  if (leader) {
+    sc->nbad_first[stage] = nfirst;
+    sc->nbad_total[stage] = total;
+    sc->iters[stage] = iters;
+    sc->stamp_cur = cur;
+    sc->slot = slot;
+    sc->go = 0;
   }
 }
 

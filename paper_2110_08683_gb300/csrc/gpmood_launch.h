@@ -40,6 +40,13 @@ struct Launch {
                                 const DirectW<Real>& Wd, const Cascade& C, cudaStream_t st);
   static cudaError_t mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
                                  const Detect& D, const DirectW<Real>& Wd, cudaStream_t st);
+  // the whole MOOD loop of stage `stage` in one launch of `blocks` co-resident
+  // blocks (cooperative when `coop`)
+  static cudaError_t mood_loop(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
+                               const Detect& D, const DirectW<Real>& Wd, const Cascade& C,
+                               int stage, int blocks, int coop, cudaStream_t st);
+  // co-resident blocks of the MOOD loop kernel on this device (its grid)
+  static int mood_loop_blocks();
 };
 
 // replay with given radii, and the reverse-mode passes of the adjoint

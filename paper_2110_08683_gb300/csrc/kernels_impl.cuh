@@ -50,6 +50,39 @@ cudaError_t Launch<Real>::mood_update(const StageArgs<Real>& A, const MoodArgs& 
   return launch_k(k_mood_update<Real>, dim3(kMoodBlocks), dim3(256), st, A, M, g, D, Wd);
 }
 
+template <class Real>
+cudaError_t Launch<Real>::mood_loop(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
+                                    const Detect& D, const DirectW<Real>& Wd, const Cascade& C,
+                                    int stage, int blocks, int coop, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  // cooperative: the launch fails rather than run a grid whose blocks cannot
+  // all be resident at once (the barriers need them all)
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = coop ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_mood_loop<Real>, A, M, g, D, Wd, C, stage);
+}
+
+template <class Real>
+int Launch<Real>::mood_loop_blocks() {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mood_loop<Real>, 256, 0) !=
+          cudaSuccess || sms <= 0 || occ <= 0) {
+    cudaGetLastError();
+    return 0;
+  }
+  // two blocks an SM where they fit: enough warps to hide the FP64 latency
+  // of the few cells an iteration works on, few arrivals per barrier
+  return sms * (occ < 2 ? occ : 2);
+}
+
 template <int R, class Real, int FW>
 static cudaError_t faces_batch_r(int dir, const StageArgs<Real>& B, const Prob* probs,
                                  const Scalars* psc, const Item* items, int nitems, int blocks,

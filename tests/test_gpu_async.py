@@ -92,10 +92,12 @@ def test_failure_stops_the_queued_steps():
     g2.close()
 
 
-def test_launch_count_is_counted_on_the_device():
-    # the smooth vortex: no MOOD iteration, so every step launches the gate,
-    # the two time-step kernels, five kernels a stage and the finishing one
-    p = I.vortex(n=64, R=3)
+@pytest.mark.parametrize("problem", ["vortex", "quadrants"])
+def test_launch_count_is_counted_on_the_device(problem):
+    # every step launches the gate, the two time-step kernels, five kernels a
+    # stage (ghost fill, x and y faces, update, the MOOD loop) and the
+    # finishing one, whether MOOD iterates (quadrants) or not (the vortex)
+    p = I.vortex(n=64, R=3) if problem == "vortex" else I.quadrants(n=64, R=3, seed=4)
     g = gp.GPMood(p)
     g.set_state(p["U0"])
     n0 = g.launch_count()
@@ -103,6 +105,8 @@ def test_launch_count_is_counted_on_the_device():
         g.step_async()
     g.sync()
     assert g.launch_count() - n0 == 5 * (1 + 2 + 3 * 5 + 1)
+    if problem == "quadrants":
+        assert sum(g.flags(maps=False)[2]["iters"]) > 0
     g.close()
 
 

@@ -133,6 +133,24 @@ def test_discontinuous_run_l1_at_t_end():
     assert L1 <= 1e-8, L1
 
 
+@pytest.mark.parametrize("seed", [11, 3, 0])
+def test_quadrants_to_the_batch_end_time(seed):
+    """Four-quadrant problems of the batch configuration run freely to its
+    end time t = 0.25 on a 40^2 grid: the same step count as the oracle and
+    an L1 density difference of at most 1e-8 (the criterion for
+    discontinuous flows at t_end)."""
+    p = I.quadrants(n=40, R=3, seed=seed)
+    g, o = pair(p)
+    g.set_state(p["U0"])
+    ng = g.run(0.25)
+    Ug = g.get_state()
+    Uo, no, to = o.run(p["U0"], 0.25)
+    L1 = np.abs(Ug[0] - Uo[0]).mean()
+    print(f"seed {seed}: {ng} steps to t = 0.25, L1 density difference {L1:.2e}")
+    assert ng == no
+    assert L1 <= 1e-8, L1
+
+
 def test_mood_cap_is_reported_not_hung():
     p = I.quadrants(n=32, R=3, seed=1)
     p["max_iters"] = 1
@@ -215,8 +233,9 @@ def test_fp32_dmr_positivity():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_eager_launches_equal_the_step_graph(precision):
-    """The eager mode (stream launches, host-driven MOOD loop) runs the same
-    kernels in the same order as the captured step graph: equal bit for bit,
+    """The eager mode (stream launches, the host reads the scalars after
+    every stage) runs the same kernels in the same order as the captured step
+    graph: equal bit for bit,
     flags and MOOD counters included, on a problem where MOOD is active."""
     p = I.quadrants(n=48, ny=40, R=3, seed=1)
     res = []
