@@ -82,16 +82,21 @@ def workload_name(kind, nx, ny, scheme="GP-R3"):
             f"SSP-RK3, CFL 0.8, HLLC")
 
 
-def faces_flops_per_face(R=3):
+def faces_flops_per_face(R=3, fused=False):
     """Arithmetic of one first-pass face launch per face: the parity sums of
     the cell (4 variables), the q/2 parity dot products of length N and the
-    butterflies, then q HLLC fluxes and the Gauss sum."""
+    butterflies, then q HLLC fluxes and the Gauss sum.  The fused kernel's
+    block of 8 x 32 cells owns 7 x 31 faces of each direction: it forms the
+    sums of its 256 cells once, x states on 224 of them, y states on 256."""
     N = 2 * R * R + 2 * R + 1
     q = R + 1
-    sums = 2 * R * 2 + (R * (R - 1) // 2) * 8
+    sums = 4 * (2 * R * 2 + (R * (R - 1) // 2) * 8)
     pairs, middle = q // 2, q % 2
-    recon = 4 * (sums + 2 * N * (pairs + middle) + 8 * pairs + 2 * middle)
-    return recon + q * (HLLC_FLOPS + 8)
+    dots = 4 * (2 * N * (pairs + middle) + 8 * pairs + 2 * middle)
+    riemann = q * (HLLC_FLOPS + 8)
+    if not fused:
+        return sums + dots + riemann
+    return (256 * sums + (224 + 256) * dots) / (2 * 7 * 31) + riemann
 
 
 FACE_KERNEL_SOURCES = ("gpmood_kernels.cuh", "gpmood_internal.h", "kernels_impl.cuh")
@@ -454,21 +459,26 @@ def measure(kind, nx, ny, precision, scheme, steps, warmup, world, local, eager=
     if prof:
         fx_ms, fx_n = kt["faces_x"]
         per_launch_s = fx_ms / 1e3 / max(fx_n, 1)
-        faces = (nx + 1) * ny
+        # the fused kernel solves both directions' faces in one launch
+        fused = kt["faces_y"][1] == 0
+        faces = (nx + 1) * ny + (nx * (ny + 1) if fused else 0)
         peak = FP64_PEAK_TFLOPS if real64 else FP32_PEAK_TFLOPS
         alg = faces * algorithmic_flops_per_face(R)
-        exe = faces * faces_flops_per_face(R)
+        exe = faces * faces_flops_per_face(R, fused)
         roofline = {
             "bound": "alu", "achieved": round(alg / per_launch_s / 1e12, 4),
             "peak": round(peak, 4), "unit": "TFLOP/s",
             "frac": round(alg / per_launch_s / 1e12 / peak, 4),
             "traffic": ncu_traffic(precision, kind, scheme),
-            "kernel": "k_faces<R=%d,%s,x>" % (R, "double" if real64 else "float"),
+            "kernel": ("k_faces_xy<R=%d,%s> (x and y faces)" if fused else "k_faces<R=%d,%s,x>")
+                      % (R, "double" if real64 else "float"),
             "flops_per_launch": alg,
             "flops_per_face": algorithmic_flops_per_face(R),
             "count": "algorithmic: 8 q N reconstruction FMA (2 flop), q HLLC at %d flop, the "
-                     "Gauss sum; per x face, x (nx+1) ny faces a launch" % HLLC_FLOPS,
-            "executed": {"flops_per_face": faces_flops_per_face(R), "flops_per_launch": exe,
+                     "Gauss sum; per face, x %s faces a launch"
+                     % (HLLC_FLOPS, "(nx+1) ny + nx (ny+1)" if fused else "(nx+1) ny"),
+            "executed": {"flops_per_face": round(faces_flops_per_face(R, fused), 1),
+                         "flops_per_launch": exe,
                          "achieved": round(exe / per_launch_s / 1e12, 4),
                          "frac": round(exe / per_launch_s / 1e12 / peak, 4),
                          "count": "the kernel's own arithmetic after the parity-sum "
@@ -570,7 +580,10 @@ def run_batch(args, world, rank, local):
                                f"states, GP-R3 cascade 7->5->3->1, ell=12dx, CFL 0.8, one batch",
                    "cells": cells, "precision": args.precision,
                    "parallelism": f"replicas x{world}", "l2": "flushed between timed steps"},
-        "autotuned": {"warps_xy": b.tuning()[0]},
+        "autotuned": {"face_kernel": ("fused x+y" if b.tuning()[0] == [0, 0]
+                                      else "one sweep per direction"),
+                      "warps_xy": b.tuning()[0], "face_items": b.tuning()[1],
+                      "update_blocks": b.grids()[0], "mood_blocks": b.grids()[1]},
         "mood_last_step": st,
         "clocks": sampler.summary(),
     }
@@ -580,10 +593,11 @@ def run_batch(args, world, rank, local):
 
 def run_adjoint(args, world, rank, local):
     """Forward rollout and its reverse mode on the smooth periodic shear layer
-    (GP-R2, MOOD radii frozen from the forward, 200 steps), once with
-    checkpoints every 20 steps and segments stepped again in the reverse
-    pass, once with every step's tape kept resident: the reverse pass's time
-    over that of the plain forward rollout."""
+    (GP-R2, MOOD radii frozen from the forward, 200 steps): with checkpoints
+    every 20 steps and segments stepped again in the reverse pass, keeping
+    their face states (the default) or not, and with every step's tape kept
+    resident.  Each reverse pass's time is set against the plain forward
+    rollout (steps queued back to back, nothing recorded)."""
     import torch
 
     import paper_2110_08683_gb300 as gp
@@ -602,19 +616,30 @@ def run_adjoint(args, world, rank, local):
     g.set_state(p["U0"])
     for _ in range(args.warmup):
         g.step()
-    # an untimed short rollout and its reverse mode in both tape strategies:
-    # captures the recording graphs and allocates the adjoint buffers
-    for every in (None, 20):
+    # untimed short rollouts and their reverse modes in every tape strategy:
+    # capture the recording graphs and allocate the adjoint buffers
+    for every, states in ((None, True), (20, True), (20, False)):
         Uw = U0.clone().requires_grad_()
-        (rollout(Uw, g, max(args.warmup, 3), every=every) * W).sum().backward()
+        (rollout(Uw, g, max(args.warmup, 3), every=every, states=states) * W).sum().backward()
     torch.cuda.synchronize()
     steps = args.adjoint_steps
+    # the plain forward rollout
+    g.set_state(U0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.step_async()
+    g.sync()
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
     modes = {}
-    for name, every in (("checkpoints_every_20", 20), ("resident_tapes", None)):
+    for name, every, states in (("checkpoints_every_20", 20, True),
+                                ("checkpoints_every_20_no_state_tape", 20, False),
+                                ("resident_tapes", None, True)):
         U0r = U0.clone().requires_grad_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        UN = rollout(U0r, g, steps, every=every)
+        UN = rollout(U0r, g, steps, every=every, states=states)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         J = (UN * W).sum()
@@ -622,12 +647,10 @@ def run_adjoint(args, world, rank, local):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         modes[name] = {"forward_s": t1 - t0, "backward_s": t2 - t1,
-                       "grad_norm": float(U0r.grad.norm())}
+                       "grad_norm": float(U0r.grad.norm()),
+                       "backward_over_plain_forward": (t2 - t1) / fwd,
+                       "forward_plus_backward_over_plain_forward": (t2 - t0) / fwd}
         del UN, J, U0r
-    # the forward cost: the rollout that keeps only checkpoints (plain steps)
-    fwd = modes["checkpoints_every_20"]["forward_s"]
-    for m in modes.values():
-        m["backward_over_plain_forward"] = m["backward_s"] / fwd
     # finite differences resolve the FP64 map only (FP32: eps_32 / h ~ 6%)
     fd = None
     if args.adjoint_fd and args.precision == "fp64":
@@ -641,6 +664,7 @@ def run_adjoint(args, world, rank, local):
                                f"field, GP-R2 cascade 5->3->1, ell=12dx, {steps} steps, "
                                "J = integral of rho over [0.4,0.6]^2",
                    "cells": n * n, "precision": args.precision},
+        "plain_forward_s": fwd,
         "adjoint": modes,
         "fd_check": fd,
     }
@@ -799,18 +823,15 @@ def main():
             a = run_adjoint(argparse.Namespace(**{**vars(args), "adjoint_fd": 0,
                                                   "precision": "fp64"}), world, rank, local)
             ck = a["adjoint"]["checkpoints_every_20"]
-            rs = a["adjoint"]["resident_tapes"]
             line["adjoint"] = {
                 "config": a["config"]["workload"],
-                "forward_s": round(ck["forward_s"], 4),
+                "plain_forward_s": round(a["plain_forward_s"], 4),
                 "reverse_over_forward": round(ck["backward_over_plain_forward"], 3),
                 "forward_plus_reverse_over_forward": round(
-                    (ck["forward_s"] + ck["backward_s"]) / ck["forward_s"], 3),
-                "checkpoints_every": 20,
-                "resident_tapes": {"reverse_over_forward": round(rs["backward_over_plain_forward"],
-                                                                 3),
-                                   "forward_s": round(rs["forward_s"], 4),
-                                   "backward_s": round(rs["backward_s"], 4)},
+                    ck["forward_plus_backward_over_plain_forward"], 3),
+                "checkpoints_every": 20, "face_state_tapes": True,
+                "modes": {k: {kk: round(vv, 4) for kk, vv in m.items()}
+                          for k, m in a["adjoint"].items()},
                 "forward_cell_updates_per_s": a["value"]}
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and not args.only:

@@ -33,6 +33,7 @@
 #ifndef GPMOOD_H
 #define GPMOOD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -121,6 +122,10 @@ typedef struct {
                            dependent launch (each is scheduled while its predecessor
                            drains and waits for it before touching memory); 1: plain
                            stream order.  Same results */
+  int split_faces;      /* 0: on two-dimensional grids one kernel solves the x and the y
+                           faces of the first pass, every cell forming its stencil sums
+                           once for both; 1: one kernel per direction.  Same results,
+                           bit for bit */
 } gpmood_options;
 
 /* per-step diagnostics of the most recent step */
@@ -263,12 +268,26 @@ int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches);
  *   on the first call and waits for the stream.  Where a reconstructed state
  *   has non-positive pressure the Riemann solver's branch is decided by NaN
  *   comparisons; the adjoint follows the branch the forward took.
+ * gpmood_step_record_states / gpmood_step_adjoint_states: the same with a
+ *   state tape (caller-owned device memory of gpmood_state_tape_bytes bytes
+ *   per step): the recorded step also keeps the reconstructed states every
+ *   final face flux was solved from (eq. gp_reconstructor at the face's EDP1
+ *   radius, the Gauss points of Table QR), and the adjoint reads them instead
+ *   of reconstructing them again.  Two-dimensional grids.  The gradient is the
+ *   same, bit for bit; the state tape spends device memory (8 q N_faces reals
+ *   a stage, q the top radius's rule) to save the reconstruction's arithmetic.
  */
 int gpmood_step_record(gpmood_t h, double cfl, double dt_fixed, double* tape, uint8_t* otape,
                        double* dt_out);
 int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt);
 int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
                         const double* lam_in, double* lam_out);
+int gpmood_state_tape_bytes(gpmood_t h, size_t* bytes);
+int gpmood_step_record_states(gpmood_t h, double cfl, double dt_fixed, double* tape,
+                              uint8_t* otape, void* stape, double* dt_out);
+int gpmood_step_adjoint_states(gpmood_t h, const double* tape, const uint8_t* otape,
+                               const void* stape, double dt, double t, const double* lam_in,
+                               double* lam_out);
 
 /*
  * Batches: many independent problems of uneven sizes advanced together.
@@ -304,9 +323,15 @@ int gpmood_batch_run(gpmood_batch_t b, double t_end, double cfl, long long* nste
    total (nullable) gets the summed MOOD statistics of the last step */
 int gpmood_batch_info(gpmood_batch_t b, double* t, double* dt, long long* nsteps,
                       gpmood_stats* total);
-/* the autotuner's choice per sweep (x, y): warps per block and the number
-   of work items (blocks); GPMOOD_E_NOSTATE before the first step */
+/* the autotuner's choice of first-pass face kernel, made on the first step:
+   per sweep (x, y) the warps per block (4 or 8) and the number of work items
+   (blocks), or warps = {0, 0} for the kernel that solves both directions,
+   blocks then its work items; GPMOOD_E_NOSTATE before the first step */
 int gpmood_batch_tuning(gpmood_batch_t b, int* warps, int* blocks);
+/* the update kernel's tuned grid (blocks walking the update items) and the
+   grid of the MOOD loop kernel (co-resident blocks); GPMOOD_E_NOSTATE before
+   the first step */
+int gpmood_batch_grids(gpmood_batch_t b, int* update_blocks, int* mood_blocks);
 int gpmood_batch_profile(gpmood_batch_t b, int enable);
 int gpmood_batch_kernel_times(gpmood_batch_t b, double* ms, long long* launches);
 int gpmood_batch_destroy(gpmood_batch_t b);
@@ -324,7 +349,7 @@ int gpmood_batch_destroy(gpmood_batch_t b);
  * are carved out of one file-scope device array of
  * GPMOOD_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads this
  * library holds until the process exits.  At R_max = 3 that covers square
- * grids up to 296 x 296 cells in FP64 and 259 x 259 in FP32 (whose float
+ * grids up to 292 x 292 cells in FP64 and 256 x 256 in FP32 (whose float
  * shadows of the three states share the array); a grid needing more returns
  * GPMOOD_E_TOO_BIG without touching the device.
  *

@@ -55,6 +55,7 @@ class Options(C.Structure):
         ("sigma_v", C.c_double), ("sigma_p", C.c_double), ("csd_off", C.c_int),
         ("max_mood_iters", C.c_int), ("riemann", C.c_int), ("rk", C.c_int),
         ("eager", C.c_int), ("recon", C.c_int), ("serial_launch", C.c_int),
+        ("split_faces", C.c_int),
     ]
 
 
@@ -103,6 +104,9 @@ def load(build_if_missing=True):
     L.gpmood_step_record.argtypes = [p, d, d, p, p, C.POINTER(d)]
     L.gpmood_step_frozen.argtypes = [p, p, d]
     L.gpmood_step_adjoint.argtypes = [p, p, p, d, d, p, p]
+    L.gpmood_state_tape_bytes.argtypes = [p, C.POINTER(C.c_size_t)]
+    L.gpmood_step_record_states.argtypes = [p, d, d, p, p, p, C.POINTER(d)]
+    L.gpmood_step_adjoint_states.argtypes = [p, p, p, p, d, d, p, p]
     L.gpmood_batch_create.argtypes = [C.POINTER(Grid), i, d, i, C.POINTER(d), C.POINTER(Options),
                                       C.POINTER(p)]
     L.gpmood_batch_set_stream.argtypes = [p, p]
@@ -112,6 +116,7 @@ def load(build_if_missing=True):
     L.gpmood_batch_run.argtypes = [p, d, d, C.POINTER(C.c_longlong)]
     L.gpmood_batch_info.argtypes = [p, p, p, p, C.POINTER(Stats)]
     L.gpmood_batch_tuning.argtypes = [p, p, p]
+    L.gpmood_batch_grids.argtypes = [p, p, p]
     L.gpmood_batch_profile.argtypes = [p, i]
     L.gpmood_batch_kernel_times.argtypes = [p, p, p]
     L.gpmood_batch_destroy.argtypes = [p]
@@ -167,6 +172,7 @@ def make_options(prob, precision=FP64, eager=False):
     o.riemann = RIEMANN[prob.get("riemann", "hllc")]
     o.recon = RECON[prob.get("recon", "gp")]
     o.serial_launch = int(prob.get("serial_launch", 0))
+    o.split_faces = int(prob.get("split_faces", 0))
     o.eager = 1 if eager else 0
     return o
 
@@ -372,6 +378,27 @@ class GPMood:
                                          C.c_void_p(otape_ptr), C.byref(out)), "step_record")
         return out.value
 
+    def state_tape_bytes(self):
+        """device bytes of one recorded step's face-state tape"""
+        n = C.c_size_t(0)
+        _check(load().gpmood_state_tape_bytes(self.h, C.byref(n)), "state_tape_bytes")
+        return n.value
+
+    def step_record_states(self, tape_ptr, otape_ptr, stape_ptr, cfl=None, dt=0.0):
+        out = C.c_double(0.0)
+        cfl = (self.prob["cfl"] if cfl is None else cfl) if dt <= 0.0 else 0.0
+        _check(load().gpmood_step_record_states(self.h, cfl, dt, C.c_void_p(tape_ptr),
+                                                C.c_void_p(otape_ptr), C.c_void_p(stape_ptr),
+                                                C.byref(out)), "step_record_states")
+        return out.value
+
+    def step_adjoint_states(self, tape_ptr, otape_ptr, stape_ptr, dt, t, lam_in_ptr,
+                            lam_out_ptr):
+        _check(load().gpmood_step_adjoint_states(self.h, C.c_void_p(tape_ptr),
+                                                 C.c_void_p(otape_ptr), C.c_void_p(stape_ptr),
+                                                 dt, t, C.c_void_p(lam_in_ptr),
+                                                 C.c_void_p(lam_out_ptr)), "step_adjoint_states")
+
     def step_frozen(self, otape_ptr, dt):
         _check(load().gpmood_step_frozen(self.h, C.c_void_p(otape_ptr), dt), "step_frozen")
 
@@ -469,6 +496,12 @@ class GPMoodBatch:
         b = (C.c_int * 2)()
         rc = load().gpmood_batch_tuning(self.h, w, b)
         return (list(w), list(b)) if rc == 0 else None
+
+    def grids(self):
+        """(update-kernel blocks, MOOD-loop blocks) after the first step"""
+        u, m = C.c_int(0), C.c_int(0)
+        rc = load().gpmood_batch_grids(self.h, C.byref(u), C.byref(m))
+        return (u.value, m.value) if rc == 0 else None
 
     def profile(self, enable=True):
         _check(load().gpmood_batch_profile(self.h, 1 if enable else 0), "profile")

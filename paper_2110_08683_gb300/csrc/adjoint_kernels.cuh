@@ -315,6 +315,46 @@ __global__ void __launch_bounds__(32 * FW) k_adj_faces_sweep(
   }
 }
 
+// pass 1 from the face states a recorded step kept (its state tape): one
+// thread per face of direction DIR, no reconstruction.  tL / tR: the
+// direction's left and right states [4][qt][faces] of the stage.  The states
+// are those the forward solved from, so the result equals the sweep's.
+template <class Real, int DIR>
+__global__ void __launch_bounds__(128) k_adj_faces_stored(
+    const Real* tL, const Real* tR, int qt, const double* vin, const uint8_t* ord, Grid g,
+    const __grid_constant__ ParityW<Real> W, const __grid_constant__ DirectW<Real> Wd,
+    AdjFaces A) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= A.nf) return;
+  int i, j;
+  if (DIR == 0) {
+    i = (int)(f % (g.nx + 1));
+    j = (int)(f / (g.nx + 1));
+  } else {
+    i = (int)(f % g.nx);
+    j = (int)(f / g.nx);
+  }
+  const int iL = DIR == 0 ? i - 1 : i, jL = DIR == 0 ? j : j - 1;
+  const int top = Wd.top;
+  const int K = face_radius(g, ord, top, iL, jL, i, j);
+  A.K[f] = (uint8_t)K;
+  double ad[4];
+  face_cotangent<DIR>(vin, g, iL, jL, i, j, ad);
+  const Real a[4] = {(Real)ad[0], (Real)ad[1], (Real)ad[2], (Real)ad[3]};
+  const Real gam = (Real)g.gamma;
+  const int Q = rule_q(K);
+  for (int q = 0; q < Q; ++q) {
+    Real UL[4], UR[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      UL[v] = tL[((long long)v * qt + q) * A.nf + f];
+      UR[v] = tR[((long long)v * qt + q) * A.nf + f];
+    }
+    const Real w = K == top ? W.w[q] : Wd.w[K][q];
+    adj_point<Real, DIR>(UL, UR, gam, w, a, q, (Real*)A.L, (Real*)A.R, f, A.nf);
+  }
+}
+
 // index of offset (a,b) in the radius-K stencil (order b = -K..K, a = -K..K)
 __device__ __forceinline__ int stencil_index(int K, int a, int b) {
   int m = 0;

@@ -100,62 +100,6 @@ __global__ void k_step_gate(Scalars* sc, cudaGraphConditionalHandle hif) {
 }
 
 
-__global__ void k_mood_lower(MoodArgs M, uint8_t* ord, Cascade C) {
-  pdl_wait();
-  pdl_trigger();
-  const int slot = M.sc->slot;
-  const int n = M.sc->count[slot];
-  const int* queue = M.queue[slot];
-  const uint32_t cur = M.sc->stamp_cur;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    int c = queue[q];
-    ord[c] = (uint8_t)C.next[ord[c]];
-    M.stamp[c] = cur;
-  }
-}
-
-// decide whether another MOOD iteration runs; mirrors it into sc->go and,
-// inside a captured graph, into the WHILE node's condition
-__device__ __forceinline__ void mood_decide(Scalars* sc, int stage, int n,
-                                            cudaGraphConditionalHandle hc, int use_graph) {
-  int go = n > 0;
-  if (go && sc->iters[stage] >= sc->ctl.max_iters) {
-    sc->err |= kErrCap;
-    go = 0;
-  }
-  if (go) sc->stamp_cur += 1;  // fresh stamp for the queue about to be worked on
-  sc->go = go;
-  if (use_graph) cudaGraphSetConditional(hc, go ? 1u : 0u);
-}
-
-// after the first pass (which filled queue 0)
-__global__ void k_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph) {
-  pdl_wait();
-  pdl_trigger();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int n = sc->count[0];
-  sc->slot = 0;
-  sc->count[1] = 0;
-  sc->nbad_first[stage] = n;
-  sc->nbad_total[stage] = n;
-  sc->iters[stage] = 0;
-  mood_decide(sc, stage, n, hc, use_graph);
-}
-
-// after one MOOD iteration (which filled the other queue)
-__global__ void k_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph) {
-  pdl_wait();
-  pdl_trigger();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int s = sc->slot, ns = s ^ 1;
-  const int n = sc->count[ns];
-  sc->nbad_total[stage] += n;
-  sc->iters[stage] += 1;
-  sc->count[s] = 0;
-  sc->slot = ns;
-  mood_decide(sc, stage, n, hc, use_graph);
-}
-
 // ---------------------------------------------------------------------------
 // adjoint helpers
 // ---------------------------------------------------------------------------

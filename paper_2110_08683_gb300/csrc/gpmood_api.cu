@@ -32,7 +32,7 @@ struct gpmood_s {
   uint8_t* fb;     // face-state check bits: x faces, then y faces
   uint8_t* ord;    // [S][nc], S stages
   uint8_t* first;  // [S][nc]
-  uint32_t* stamp;
+  uint32_t* stamp;  // two arrays of ncell MOOD stamps (odd and even values)
   int* queue[2];
   Scalars* sc;     // device
   Scalars* hsc;    // pinned host mirror
@@ -45,6 +45,7 @@ struct gpmood_s {
   int launches;
   int last_status;
   int mood_blocks;  // grid of the MOOD loop kernel (co-resident blocks)
+  int split_faces;  // 1: one first-pass face kernel per direction
   int coop;         // 1: the MOOD loop kernel is launched cooperatively
   // optional per-class event timing (graph steps)
   int prof_on;
@@ -278,9 +279,10 @@ int settle(gpmood_t h) {
 }
 
 void write_control(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
-                   double* tape = nullptr, uint8_t* otape = nullptr) {
+                   double* tape = nullptr, uint8_t* otape = nullptr, void* stape = nullptr) {
   h->ctl.tape = tape;
   h->ctl.otape = otape;
+  h->ctl.stape = stape;
   h->ctl.cfl = cfl;
   h->ctl.fixed_dt = fixed_dt;
   h->ctl.clip = clip;
@@ -305,11 +307,13 @@ int push_control_if_changed(gpmood_t h) {
 
 // kernels launched by one step: the gate of a gated graph (1), dt (2), per
 // stage fill, faces x (and y in 2D), update, the MOOD loop, finish (1)
-int step_base_launches(int nstages, int dim, int gated) {
-  return (gated ? 1 : 0) + 2 + nstages * (dim == 2 ? 5 : 4) + 1;
+int step_base_launches(int nstages, int face_kernels, int gated) {
+  return (gated ? 1 : 0) + 2 + nstages * (3 + face_kernels) + 1;
 }
+// first-pass face kernels a stage: 1 (fused, or 1D), 2 (split 2D)
+int face_kernels(const gpmood_t h) { return (h->g.dim == 2 && h->split_faces) ? 2 : 1; }
 int step_launches(const gpmood_t h, int gated) {
-  return step_base_launches(h->sch.nstages, h->g.dim, gated);
+  return step_base_launches(h->sch.nstages, face_kernels(h), gated);
 }
 
 int step_error(gpmood_t h) {
@@ -325,16 +329,27 @@ MoodArgs mood_args(gpmood_t h) {
   M.queue[0] = h->queue[0];
   M.queue[1] = h->queue[1];
   M.stamp = h->stamp;
+  M.stamp_stride = (long long)h->g.nx * h->g.ny;
   M.sc = h->sc;
   return M;
+}
+
+// the first-pass faces of both directions: one fused launch on 2D grids
+// (split_faces = 0), else one launch per direction (x only in 1D)
+template <class Real>
+cudaError_t faces_both(gpmood_t h, const StageArgs<Real>& A, const ParityW<Real>& P,
+                       cudaStream_t st) {
+  if (h->g.dim == 2 && !h->split_faces) return Launch<Real>::faces_xy(h->cas.top, A, h->g, P, st);
+  cudaError_t e = Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st);
+  if (e == cudaSuccess && h->g.dim == 2) e = Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st);
+  return e;
 }
 
 template <class Real>
 int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const ParityW<Real>& P,
                const DirectW<Real>& D, cudaStream_t st) {
   CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
-  CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
-  if (h->g.dim == 2) CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
+  CK(faces_both<Real>(h, A, P, st));
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
   return 0;
 }
@@ -387,11 +402,12 @@ int copy_interior(gpmood_t h, const double* Xg, double* out) {
 // the eager step; with a tape it also records the three stage inputs
 // (interior, [3][4][ny][nx]) and the final radii of the three stages
 int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
-            double* tape = nullptr, uint8_t* otape = nullptr) {
+            double* tape = nullptr, uint8_t* otape = nullptr, void* stape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
   g_pdl = h->pdl;
   const int a = h->cur;
-  write_control(h, cfl, fixed_dt, clip, t_end);
+  // the face kernels write the state tape (if any) themselves
+  write_control(h, cfl, fixed_dt, clip, t_end, nullptr, nullptr, stape);
   int rc = push_control(h);
   if (rc) return rc;
   CK(launch_dt(h->U[a], h->Uf[a], h->g, h->sc, h->stream));
@@ -409,7 +425,7 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     if (otape) CK(cudaMemcpyAsync(otape + s * nc, h->ord + s * nc, nc, cudaMemcpyDeviceToDevice,
                                   h->stream));
   }
-  CK(launch_finish(h->sc, step_base_launches(h->sch.nstages, h->g.dim, 0), h->stream));
+  CK(launch_finish(h->sc, step_base_launches(h->sch.nstages, face_kernels(h), 0), h->stream));
   rc = pull_scalars(h);
   if (rc) return rc;
   h->launches = step_launches(h, 0);
@@ -420,8 +436,7 @@ int do_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
 }
 
 // ---- graph step: one captured graph per buffer rotation; the MOOD loop of
-// every stage is a conditional WHILE node whose body ends with the kernel
-// that decides the next iteration, so a step needs no host round trip ----
+// every stage iterates inside its kernel, so a step needs no host round trip ----
 void rec_event(gpmood_t h, int prof, int cls, int open, cudaStream_t st) {
   if (!prof) return;
   int k = h->gev_n;
@@ -442,12 +457,19 @@ int capture_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const Dire
   rec_event(h, prof, GPMOOD_K_GHOST, 1, st);
   CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
   rec_event(h, prof, GPMOOD_K_GHOST, 0, st);
-  rec_event(h, prof, GPMOOD_K_FACES_X, 1, st);
-  CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
-  rec_event(h, prof, GPMOOD_K_FACES_X, 0, st);
-  rec_event(h, prof, GPMOOD_K_FACES_Y, 1, st);
-  if (h->g.dim == 2) CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
-  rec_event(h, prof, GPMOOD_K_FACES_Y, 0, st);
+  if (h->g.dim == 2 && !h->split_faces) {
+    // both directions in one kernel, timed as the x-face class
+    rec_event(h, prof, GPMOOD_K_FACES_X, 1, st);
+    CK(Launch<Real>::faces_xy(h->cas.top, A, h->g, P, st));
+    rec_event(h, prof, GPMOOD_K_FACES_X, 0, st);
+  } else {
+    rec_event(h, prof, GPMOOD_K_FACES_X, 1, st);
+    CK(Launch<Real>::faces(h->cas.top, 0, A, h->g, P, st));
+    rec_event(h, prof, GPMOOD_K_FACES_X, 0, st);
+    rec_event(h, prof, GPMOOD_K_FACES_Y, 1, st);
+    if (h->g.dim == 2) CK(Launch<Real>::faces(h->cas.top, 1, A, h->g, P, st));
+    rec_event(h, prof, GPMOOD_K_FACES_Y, 0, st);
+  }
   rec_event(h, prof, GPMOOD_K_UPDATE, 1, st);
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
   rec_event(h, prof, GPMOOD_K_UPDATE, 0, st);
@@ -516,7 +538,7 @@ int capture_step_impl(gpmood_t h, int cur, int prof, int record, int gated,
              ? capture_stage<float>(h, s, a, h->pw32, h->dw32, prof, record, bs)
              : capture_stage<double>(h, s, a, h->pw64, h->dw64, prof, record, bs);
   if (!rc &&
-      launch_finish(h->sc, step_base_launches(h->sch.nstages, h->g.dim, gated), bs) != cudaSuccess)
+      launch_finish(h->sc, step_base_launches(h->sch.nstages, face_kernels(h), gated), bs) != cudaSuccess)
     rc = GPMOOD_E_CUDA;
   if (body_open) {
     cudaGraph_t tmp = nullptr;
@@ -566,11 +588,11 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
 }
 
 int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
-               double* tape = nullptr, uint8_t* otape = nullptr) {
+               double* tape = nullptr, uint8_t* otape = nullptr, void* stape = nullptr) {
   if (!h->has_state) return set_err(h, GPMOOD_E_NOSTATE);
   int rc = settle(h);
   if (rc) return rc;
-  if (h->eager) return do_step(h, cfl, fixed_dt, clip, t_end, tape, otape);
+  if (h->eager) return do_step(h, cfl, fixed_dt, clip, t_end, tape, otape, stape);
   const int record = tape ? 1 : 0;
   const int prof = (h->prof_on && !record) ? 1 : 0;
   cudaGraphExec_t& ge = h->gexec[h->cur][record ? 2 : prof];
@@ -579,7 +601,7 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     if (rc) return rc;
   }
   const int gated = !record && !prof && h->gated_ok == 1;
-  write_control(h, cfl, fixed_dt, clip, t_end, tape, otape);
+  write_control(h, cfl, fixed_dt, clip, t_end, tape, otape, stape);
   rc = push_control(h);
   if (rc) return rc;
   CK(cudaGraphLaunch(ge, h->stream));
@@ -595,7 +617,7 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     h->prof_n[GPMOOD_K_DT] += 2;
     h->prof_n[GPMOOD_K_GHOST] += S;
     h->prof_n[GPMOOD_K_FACES_X] += S;
-    h->prof_n[GPMOOD_K_FACES_Y] += h->g.dim == 2 ? S : 0;
+    h->prof_n[GPMOOD_K_FACES_Y] += (h->g.dim == 2 && h->split_faces) ? S : 0;
     h->prof_n[GPMOOD_K_UPDATE] += S;
     h->prof_n[GPMOOD_K_MOOD] += S;
   }
@@ -663,20 +685,6 @@ cudaError_t launch_finish(Scalars* sc, int base, cudaStream_t st) {
 
 cudaError_t launch_gate(Scalars* sc, cudaGraphConditionalHandle hif, cudaStream_t st) {
   return launch_k(k_step_gate, dim3(1), dim3(32), st, sc, hif);
-}
-
-cudaError_t launch_mood_begin(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
-                              cudaStream_t st) {
-  return launch_k(k_mood_begin, dim3(1), dim3(32), st, sc, stage, hc, use_graph);
-}
-
-cudaError_t launch_mood_end(Scalars* sc, int stage, cudaGraphConditionalHandle hc, int use_graph,
-                            cudaStream_t st) {
-  return launch_k(k_mood_end, dim3(1), dim3(32), st, sc, stage, hc, use_graph);
-}
-
-cudaError_t launch_lower(const MoodArgs& M, uint8_t* ord, const Cascade& C, cudaStream_t st) {
-  return launch_k(k_mood_lower, dim3(kMoodBlocks), dim3(256), st, M, ord, C);
 }
 
 }  // namespace gpm
@@ -796,6 +804,13 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->precision = o.precision;
   h->eager = o.eager ? 1 : 0;
   h->pdl = o.serial_launch ? 0 : 1;
+  h->split_faces = o.split_faces ? 1 : 0;
+  if ((h->precision == GPMOOD_FP32 ? Launch<float>::prepare() : Launch<double>::prepare()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return GPMOOD_E_CUDA;
+  }
   h->coop = 1;
   h->mood_blocks = h->precision == GPMOOD_FP32 ? Launch<float>::mood_loop_blocks()
                                                : Launch<double>::mood_loop_blocks();
@@ -852,7 +867,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   ok = ok && cudaMalloc(&h->fb, nfb) == cudaSuccess;
   ok = ok && cudaMalloc(&h->ord, S * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->first, S * ncell) == cudaSuccess;
-  ok = ok && cudaMalloc(&h->stamp, sizeof(uint32_t) * ncell) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->stamp, 2 * sizeof(uint32_t) * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->queue[0], sizeof(int) * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->queue[1], sizeof(int) * ncell) == cudaSuccess;
   ok = ok && cudaMalloc(&h->sc, sizeof(Scalars)) == cudaSuccess;
@@ -866,7 +881,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   // the face fluxes start at zero: in 1D the y fluxes stay zero
   ok = cudaMemset(h->Fx, 0, fsz * 4 * (size_t)g.ny * (g.nx + 1)) == cudaSuccess &&
        cudaMemset(h->Fy, 0, fsz * 4 * (size_t)(g.ny + 1) * g.nx) == cudaSuccess &&
-       cudaMemset(h->fb, 0, nfb) == cudaSuccess && cudaMemset(h->stamp, 0, 4 * ncell) == cudaSuccess &&
+       cudaMemset(h->fb, 0, nfb) == cudaSuccess && cudaMemset(h->stamp, 0, 2 * sizeof(uint32_t) * ncell) == cudaSuccess &&
        cudaMemset(h->ord, 0, S * ncell) == cudaSuccess &&
        cudaMemset(h->first, 0, S * ncell) == cudaSuccess;
   for (int k = 0; k < h->sch.nbuf && ok; ++k)
@@ -926,7 +941,7 @@ int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
     }
   }
   // MOOD stamps restart with the scalars
-  CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * (size_t)g.nx * g.ny, h->stream));
+  CK(cudaMemsetAsync(h->stamp, 0, 2 * sizeof(uint32_t) * (size_t)g.nx * g.ny, h->stream));
   Scalars z;
   memset(&z, 0, sizeof(z));
   z.rate_bits = 0ull;
@@ -1113,12 +1128,28 @@ int gpmood_kernel_times(gpmood_t h, double* ms, long long* launches) {
 // ---------------------------------------------------------------------------
 int gpmood_step_record(gpmood_t h, double cfl, double dt_fixed, double* tape, uint8_t* otape,
                        double* dt_out) {
+  return gpmood_step_record_states(h, cfl, dt_fixed, tape, otape, nullptr, dt_out);
+}
+
+int gpmood_step_record_states(gpmood_t h, double cfl, double dt_fixed, double* tape,
+                              uint8_t* otape, void* stape, double* dt_out) {
   if (!h || !tape || !otape || (!(cfl > 0.0) && !(dt_fixed > 0.0))) return GPMOOD_E_INVAL;
   if (h->sch.nstages != 3) return GPMOOD_E_INVAL;  // the adjoint follows SSP-RK3
+  if (stape && h->g.dim != 2) return GPMOOD_E_INVAL;
   int rc = graph_step(h, cfl > 0.0 ? cfl : 1.0, dt_fixed > 0.0 ? dt_fixed : 0.0, 0, 0.0, tape,
-                      otape);
+                      otape, stape);
   if (rc) return rc;
   if (dt_out) *dt_out = h->hsc->dt;
+  return GPMOOD_OK;
+}
+
+int gpmood_state_tape_bytes(gpmood_t h, size_t* bytes) {
+  if (!h || !bytes) return GPMOOD_E_INVAL;
+  const Grid& g = h->g;
+  const size_t nf = (size_t)(g.nx + 1) * g.ny + (size_t)g.nx * (g.ny + 1);
+  const size_t qt = (size_t)rule_q(h->cas.top);
+  const size_t real = h->precision == GPMOOD_FP32 ? sizeof(float) : sizeof(double);
+  *bytes = (size_t)h->sch.nstages * 8 * qt * nf * real;
   return GPMOOD_OK;
 }
 
@@ -1183,8 +1214,19 @@ int adj_buffers(gpmood_t h) {
 // w = v - dt (dF/dX)^T v at the stage input X (interior) with radii ords
 template <class Real>
 int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, double dt,
-              const double* v, double* w, const ParityW<Real>& P, const DirectW<Real>& D) {
+              const double* v, double* w, const ParityW<Real>& P, const DirectW<Real>& D,
+              const void* st) {
   const Grid& g = h->g;
+  if (st) {
+    // the recorded face states: no reconstruction, no ghosted copy of X
+    CK(LaunchA<Real>::adj_faces_stored(st, v, ords, g, P, D, h->ax, h->ay, h->stream));
+    CK(LaunchA<Real>::adj_gather(g, D, h->ax, h->ay, h->aG, h->stream));
+    k_adj_fold_y<<<(g.nx + 2 * g.H + 127) / 128, 128, 0, h->stream>>>(h->aG, g);
+    k_adj_fold_x<<<(g.ny + 127) / 128, 128, 0, h->stream>>>(h->aG, g);
+    k_adj_stage_out<<<152 * 8, 256, 0, h->stream>>>(w, v, h->aG, g, dt);
+    CK(cudaGetLastError());
+    return 0;
+  }
   for (int c = 0; c < 4; ++c)
     CK(cudaMemcpy2DAsync(h->aX + c * g.vstride + (size_t)g.H * g.pitch + g.H,
                          sizeof(double) * g.pitch, X + (size_t)c * g.nx * g.ny,
@@ -1204,24 +1246,31 @@ int adj_stage(gpmood_t h, const double* X, const uint8_t* ords, double ts, doubl
 }
 
 template <class Real>
-int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
-                 const double* lam, double* out, const ParityW<Real>& P, const DirectW<Real>& D) {
+int step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, const void* stape,
+                 double dt, double t, const double* lam, double* out, const ParityW<Real>& P,
+                 const DirectW<Real>& D) {
   const size_t nc = (size_t)h->g.nx * h->g.ny, n4 = 4 * nc;
+  // the state tape of stage s
+  size_t sbytes = 0;
+  gpmood_state_tape_bytes(h, &sbytes);
+  auto st = [&](int s) -> const void* {
+    return stape ? (const void*)((const char*)stape + s * (sbytes / 3)) : nullptr;
+  };
   const int nb = 152 * 8;
   double *mu = h->amu, *v = h->av, *w = h->aw;
   // U^{n+1} = (U^n + 2 Y3)/3
   k_lincomb<<<nb, 256, 0, h->stream>>>(mu, 1.0 / 3.0, lam, 0.0, nullptr, (long long)n4);
   k_lincomb<<<nb, 256, 0, h->stream>>>(v, 2.0 / 3.0, lam, 0.0, nullptr, (long long)n4);
   // Y3 = X3 - dt F(X3), X3 = (3 U^n + Y2)/4
-  int rc = adj_stage<Real>(h, tape + 2 * n4, otape + 2 * nc, t + 0.5 * dt, dt, v, w, P, D);
+  int rc = adj_stage<Real>(h, tape + 2 * n4, otape + 2 * nc, t + 0.5 * dt, dt, v, w, P, D, st(2));
   if (rc) return rc;
   k_lincomb<<<nb, 256, 0, h->stream>>>(mu, 1.0, mu, 0.75, w, (long long)n4);
   k_lincomb<<<nb, 256, 0, h->stream>>>(v, 0.25, w, 0.0, nullptr, (long long)n4);
   // Y2 = X2 - dt F(X2), X2 = Y1
-  rc = adj_stage<Real>(h, tape + n4, otape + nc, t + dt, dt, v, w, P, D);
+  rc = adj_stage<Real>(h, tape + n4, otape + nc, t + dt, dt, v, w, P, D, st(1));
   if (rc) return rc;
   // Y1 = X1 - dt F(X1), X1 = U^n
-  rc = adj_stage<Real>(h, tape, otape, t, dt, w, v, P, D);
+  rc = adj_stage<Real>(h, tape, otape, t, dt, w, v, P, D, st(0));
   if (rc) return rc;
   k_lincomb<<<nb, 256, 0, h->stream>>>(out, 1.0, mu, 1.0, v, (long long)n4);
   CK(cudaGetLastError());
@@ -1244,6 +1293,12 @@ int gpmood_step_frozen(gpmood_t h, const uint8_t* otape, double dt) {
 
 int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, double dt, double t,
                         const double* lam_in, double* lam_out) {
+  return gpmood_step_adjoint_states(h, tape, otape, nullptr, dt, t, lam_in, lam_out);
+}
+
+int gpmood_step_adjoint_states(gpmood_t h, const double* tape, const uint8_t* otape,
+                               const void* stape, double dt, double t, const double* lam_in,
+                               double* lam_out) {
   if (!h || !tape || !otape || !lam_in || !lam_out || !(dt > 0.0) || h->g.dim != 2 ||
       h->sch.nstages != 3 || h->g.riemann != 0)  // the reverse Riemann solver is HLLC's
     return GPMOOD_E_INVAL;
@@ -1252,8 +1307,10 @@ int gpmood_step_adjoint(gpmood_t h, const double* tape, const uint8_t* otape, do
   rc = adj_buffers(h);
   if (rc) return rc;
   return h->precision == GPMOOD_FP32
-             ? step_adjoint<float>(h, tape, otape, dt, t, lam_in, lam_out, h->pw32, h->dw32)
-             : step_adjoint<double>(h, tape, otape, dt, t, lam_in, lam_out, h->pw64, h->dw64);
+             ? step_adjoint<float>(h, tape, otape, stape, dt, t, lam_in, lam_out, h->pw32,
+                                   h->dw32)
+             : step_adjoint<double>(h, tape, otape, stape, dt, t, lam_in, lam_out, h->pw64,
+                                    h->dw64);
 }
 
 }  // extern "C"
@@ -1354,7 +1411,8 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   const size_t sz_fy = align256(fsz * 4 * (size_t)(g.ny + 1) * g.nx);
   const size_t nfb = (size_t)(g.nx + 1) * g.ny + (size_t)g.nx * (g.ny + 1);
   const size_t sz_fb = align256(nfb), sz_c3 = align256(3 * ncell);
-  const size_t sz_stamp = align256(sizeof(uint32_t) * ncell), sz_q = align256(sizeof(int) * ncell);
+  const size_t sz_stamp = align256(2 * sizeof(uint32_t) * ncell);
+  const size_t sz_q = align256(sizeof(int) * ncell);
   const size_t sz_sc = align256(sizeof(Scalars));
   const size_t sz_shadow =
       o.precision == GPMOOD_FP32 ? align256(sizeof(float) * 4 * (size_t)g.vstride) : 0;
@@ -1402,6 +1460,10 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   // re-detected neighbours can take O(grid width) iterations
   h->max_iters = o.max_mood_iters > 0 ? o.max_mood_iters
                                       : 64 + 4 * (grid->nx > grid->ny ? grid->nx : grid->ny);
+  h->split_faces = o.split_faces ? 1 : 0;
+  if ((h->precision == GPMOOD_FP32 ? Launch<float>::prepare() : Launch<double>::prepare()) !=
+      cudaSuccess)
+    return GPMOOD_E_CUDA;
   h->coop = 1;
   h->mood_blocks = h->precision == GPMOOD_FP32 ? Launch<float>::mood_loop_blocks()
                                                : Launch<double>::mood_loop_blocks();
@@ -1455,7 +1517,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
 
   // what the kernels expect to start at zero: face-CAD flags and MOOD stamps
   CK(cudaMemsetAsync(h->fb, 0, nfb, h->stream));
-  CK(cudaMemsetAsync(h->stamp, 0, sizeof(uint32_t) * ncell, h->stream));
+  CK(cudaMemsetAsync(h->stamp, 0, 2 * sizeof(uint32_t) * ncell, h->stream));
   rc = gpmood_set_state(h, U_in, 1);
   if (rc) return rc;
   if (t != 0.0) {

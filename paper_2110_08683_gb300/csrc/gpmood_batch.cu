@@ -123,13 +123,15 @@ struct gpmood_batch_s {
   float* Uf[3];  // float shadows of U (FP32 path only, else null)
   void *Fx, *Fy;
   uint8_t *fb, *ord, *first;  // fb: face-state check bits, x faces then y faces
-  uint32_t* stamp;
+  uint32_t* stamp;     // two arrays of MOOD stamps over the pooled cells (odd, even values)
+  int mood_blocks, coop;  // grid of the MOOD loop kernel; 1: cooperative launch
   int* queue[2];
   Prob* probs;
   Scalars *psc, *gsc;  // device: per problem and global
   Scalars* hgsc;       // pinned host mirror of the global scalars
   Item *items_fx[2], *items_fy[2], *items_up, *items_dt;  // [fw 4, fw 8]
-  int n_fx[2], n_fy[2], n_up, n_dt;
+  Item* items_xy;  // fused x+y face blocks: (problem, segment, band of 7 face rows)
+  int n_fx[2], n_fy[2], n_up, n_dt, n_xy;
   ParityW<double> pw64;
   ParityW<float> pw32;
   DirectW<double> dw64;
@@ -137,7 +139,8 @@ struct gpmood_batch_s {
   Control ctl;
   int eager;  // stream launches instead of the captured step graph
   int cur, has_state;
-  // face-kernel variant per sweep (warps per block 4 or 8, persistent blocks)
+  // face-kernel variant: fw[d] warps per block of sweep d (4 or 8), or
+  // fw = {0, 0} for the fused x+y kernel; blocks: its work items
   int tuned, fw[2], blocks[2];
   int up_blocks, dt_blocks, fill_blocks_x;
   cudaGraphExec_t gexec[3][2];
@@ -194,7 +197,7 @@ void batch_free(gpmood_batch_t b) {
   }
   void* ptrs[] = {b->Fx, b->Fy, b->fb, b->ord, b->first, b->stamp, b->queue[0], b->queue[1],
                   b->probs, b->psc, b->gsc, b->items_fx[0], b->items_fx[1], b->items_fy[0],
-                  b->items_fy[1], b->items_up, b->items_dt};
+                  b->items_fy[1], b->items_up, b->items_dt, b->items_xy};
   for (void* p : ptrs) cudaFree(p);
   if (b->hgsc) cudaFreeHost(b->hgsc);
 }
@@ -275,11 +278,28 @@ int launch_faces_batch(gpmood_batch_t b, int dir, const StageArgs<Real>& A,
              : GPMOOD_E_CUDA;
 }
 
-// the autotuner: time both face-kernel variants (4 or 8 warps per block,
-// i.e. 4 or 8 rows per item) on the first stage of the current state and
-// keep the faster per sweep
+// the first-pass faces of every problem in the tuned variant: the fused x+y
+// kernel (fw = {0, 0}) or one sweep per direction
 template <class Real>
-int tune(gpmood_batch_t b, const ParityW<Real>& P) {
+int faces_b(gpmood_batch_t b, const StageArgs<Real>& A, const ParityW<Real>& P,
+            cudaStream_t st) {
+  if (b->fw[0] == 0)
+    return LaunchB<Real>::faces_xy(b->top, A, b->probs, b->psc, b->items_xy, b->n_xy, P, st) ==
+                   cudaSuccess
+               ? 0
+               : GPMOOD_E_CUDA;
+  int rc = launch_faces_batch<Real>(b, 0, A, P, b->fw[0], b->blocks[0], st);
+  if (!rc) rc = launch_faces_batch<Real>(b, 1, A, P, b->fw[1], b->blocks[1], st);
+  return rc;
+}
+
+// the autotuner, on the first stage of the current state: the face kernels
+// (per sweep 4 or 8 warps, i.e. rows, per work item; or the fused x+y
+// kernel, one item per 31 x 7 faces of each direction) and the grid of the
+// update kernel (blocks walking the update items); each variant is timed as
+// the best of two runs after a warm-up run, and the fastest kept
+template <class Real>
+int tune(gpmood_batch_t b, const ParityW<Real>& P, const DirectW<Real>& D) {
   int rc = launch_dt_batch(b, b->cur, b->stream);
   if (rc) return rc;
   rc = launch_fill_batch(b, b->cur, 0, b->stream);
@@ -288,26 +308,65 @@ int tune(gpmood_batch_t b, const ParityW<Real>& P) {
   cudaEvent_t e0, e1;
   CKB(cudaEventCreate(&e0));
   CKB(cudaEventCreate(&e1));
-  for (int dir = 0; dir < 2; ++dir) {
+  // best of runs 2 and 3 of launch(), ms; `before` runs untimed first
+  auto timed = [&](auto launch, auto before) -> float {
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+      before();
+      cudaEventRecord(e0, b->stream);
+      rc = launch();
+      cudaEventRecord(e1, b->stream);
+      if (rc) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < ms_min) ms_min = ms;  // the first run warms up
+    }
+    return ms_min;
+  };
+  auto none = [] {};
+  float split = 0.f;
+  for (int dir = 0; dir < 2 && !rc; ++dir) {
     float best = 1e30f;
     for (int fw : {4, 8}) {
-      float ms_min = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, b->stream);
-        rc = launch_faces_batch<Real>(b, dir, A, P, fw, 0, b->stream);
-        cudaEventRecord(e1, b->stream);
-        if (rc) break;
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0 && ms < ms_min) ms_min = ms;  // the first run warms up
-      }
-      if (rc) break;
-      if (ms_min < best) {
-        best = ms_min;
+      const float ms =
+          timed([&] { return launch_faces_batch<Real>(b, dir, A, P, fw, 0, b->stream); }, none);
+      if (!rc && ms < best) {
+        best = ms;
         b->fw[dir] = fw;
         b->blocks[dir] = dir == 0 ? b->n_fx[fw == 4 ? 0 : 1] : b->n_fy[fw == 4 ? 0 : 1];
       }
+    }
+    split += best;
+  }
+  const float fused = timed(
+      [&] {
+        return LaunchB<Real>::faces_xy(b->top, A, b->probs, b->psc, b->items_xy, b->n_xy, P,
+                                       b->stream) == cudaSuccess
+                   ? 0
+                   : GPMOOD_E_CUDA;
+      },
+      none);
+  if (!rc && fused < split) {
+    b->fw[0] = b->fw[1] = 0;
+    b->blocks[0] = b->blocks[1] = b->n_xy;
+  }
+  // the update kernel's grid; the queue and counters it fills are cleared
+  // before every run
+  float best_up = 1e30f;
+  for (int k : {2, 4, 8, 16}) {
+    const int nb = 152 * k < b->n_up ? 152 * k : b->n_up;
+    const float ms = timed(
+        [&] {
+          return LaunchB<Real>::update(A, b->probs, b->psc, b->items_up, b->n_up, nb, D,
+                                       b->stream) == cudaSuccess
+                     ? 0
+                     : GPMOOD_E_CUDA;
+        },
+        [&] { k_batch_reset<<<1, 32, 0, b->stream>>>(b->gsc); });
+    if (!rc && ms < best_up) {
+      best_up = ms;
+      b->up_blocks = nb;
     }
   }
   cudaEventDestroy(e0);
@@ -325,6 +384,33 @@ void rec(gpmood_batch_t b, int prof, int cls, int open, cudaStream_t st) {
   b->gev_n = k + 1;
 }
 
+// the MOOD loops of every problem in one launch; a driver that refuses the
+// cooperative launch gets a plain launch of the same co-resident grid from
+// then on (the kernel's barrier waits are bounded either way)
+template <class Real>
+int mood_loop_b(gpmood_batch_t b, const StageArgs<Real>& A, int s, const DirectW<Real>& D,
+                cudaStream_t st) {
+  MoodArgs M;
+  M.queue[0] = b->queue[0];
+  M.queue[1] = b->queue[1];
+  M.stamp = b->stamp;
+  M.stamp_stride = b->total_cells;
+  M.sc = b->gsc;
+  cudaError_t e = LaunchB<Real>::mood_loop(A, M, b->probs, b->psc, b->nprob, D, b->cas, s,
+                                           b->mood_blocks, b->coop, st);
+  if (e != cudaSuccess && b->coop) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      cudaGetLastError();
+      b->coop = 0;
+      e = LaunchB<Real>::mood_loop(A, M, b->probs, b->psc, b->nprob, D, b->cas, s,
+                                   b->mood_blocks, 0, st);
+    }
+  }
+  CKB(e);
+  return 0;
+}
+
 template <class Real>
 int capture_stage_b(gpmood_batch_t b, int s, int ia, int ix, int io, const ParityW<Real>& P,
                     const DirectW<Real>& D, int prof) {
@@ -334,51 +420,17 @@ int capture_stage_b(gpmood_batch_t b, int s, int ia, int ix, int io, const Parit
   if (launch_fill_batch(b, ix, s, st)) return GPMOOD_E_CUDA;
   rec(b, prof, GPMOOD_K_GHOST, 0, st);
   rec(b, prof, GPMOOD_K_FACES_X, 1, st);
-  if (launch_faces_batch<Real>(b, 0, A, P, b->fw[0], b->blocks[0], st)) return GPMOOD_E_CUDA;
+  if (faces_b<Real>(b, A, P, st)) return GPMOOD_E_CUDA;
   rec(b, prof, GPMOOD_K_FACES_X, 0, st);
   rec(b, prof, GPMOOD_K_FACES_Y, 1, st);
-  if (launch_faces_batch<Real>(b, 1, A, P, b->fw[1], b->blocks[1], st)) return GPMOOD_E_CUDA;
   rec(b, prof, GPMOOD_K_FACES_Y, 0, st);
   rec(b, prof, GPMOOD_K_UPDATE, 1, st);
   int nb = b->up_blocks < b->n_up ? b->up_blocks : b->n_up;
   CKB(LaunchB<Real>::update(A, b->probs, b->psc, b->items_up, b->n_up, nb, D, st));
-  cudaStreamCaptureStatus cs;
-  cudaGraph_t graph;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
-  cudaGraphConditionalHandle hc;
-  CKB(cudaGraphConditionalHandleCreate(&hc, graph, 0, cudaGraphCondAssignDefault));
-  CKB(launch_mood_begin(b->gsc, s, hc, 1, st));
   rec(b, prof, GPMOOD_K_UPDATE, 0, st);
   rec(b, prof, GPMOOD_K_MOOD, 1, st);
-  CKB(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = hc;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t cnode;
-  CKB(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CKB(cudaStreamBeginCaptureToGraph(b->cs2, body, nullptr, nullptr, 0,
-                                    cudaStreamCaptureModeThreadLocal));
-  MoodArgs M;
-  M.queue[0] = b->queue[0];
-  M.queue[1] = b->queue[1];
-  M.stamp = b->stamp;
-  M.sc = b->gsc;
-  cudaError_t e1 = launch_lower(M, A.ord, b->cas, b->cs2);
-  cudaError_t e2 = LaunchB<Real>::mood_faces(A, M, b->probs, b->psc, b->nprob, D, b->cas, b->cs2);
-  cudaError_t e3 = LaunchB<Real>::mood_update(A, M, b->probs, b->psc, b->nprob, D, b->cs2);
-  cudaError_t e4 = launch_mood_end(b->gsc, s, hc, 1, b->cs2);
-  cudaGraph_t tmp;
-  CKB(cudaStreamEndCapture(b->cs2, &tmp));
-  CKB(e1);
-  CKB(e2);
-  CKB(e3);
-  CKB(e4);
-  CKB(cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  int rc = mood_loop_b<Real>(b, A, s, D, st);
+  if (rc) return rc;
   rec(b, prof, GPMOOD_K_MOOD, 0, st);
   return 0;
 }
@@ -419,26 +471,12 @@ int eager_stage_b(gpmood_batch_t b, int s, int ia, int ix, int io, const ParityW
   cudaStream_t st = b->stream;
   StageArgs<Real> A = batch_args<Real>(b, s, ia, ix, io);
   if (launch_fill_batch(b, ix, s, st)) return GPMOOD_E_CUDA;
-  if (launch_faces_batch<Real>(b, 0, A, P, b->fw[0], b->blocks[0], st)) return GPMOOD_E_CUDA;
-  if (launch_faces_batch<Real>(b, 1, A, P, b->fw[1], b->blocks[1], st)) return GPMOOD_E_CUDA;
+  if (faces_b<Real>(b, A, P, st)) return GPMOOD_E_CUDA;
   int nb = b->up_blocks < b->n_up ? b->up_blocks : b->n_up;
   CKB(LaunchB<Real>::update(A, b->probs, b->psc, b->items_up, b->n_up, nb, D, st));
-  CKB(launch_mood_begin(b->gsc, s, 0, 0, st));
-  MoodArgs M;
-  M.queue[0] = b->queue[0];
-  M.queue[1] = b->queue[1];
-  M.stamp = b->stamp;
-  M.sc = b->gsc;
-  for (;;) {
-    int rc = pull(b);
-    if (rc) return rc;
-    if (!b->hgsc->go) break;
-    CKB(launch_lower(M, A.ord, b->cas, st));
-    CKB(LaunchB<Real>::mood_faces(A, M, b->probs, b->psc, b->nprob, D, b->cas, st));
-    CKB(LaunchB<Real>::mood_update(A, M, b->probs, b->psc, b->nprob, D, st));
-    CKB(launch_mood_end(b->gsc, s, 0, 0, st));
-  }
-  return 0;
+  int rc = mood_loop_b<Real>(b, A, s, D, st);
+  if (rc) return rc;
+  return pull(b);
 }
 
 int eager_step_b(gpmood_batch_t b) {
@@ -464,7 +502,8 @@ int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t
   b->ctl.max_iters = b->max_iters;
   CKB(cudaMemcpyAsync(&b->gsc->ctl, &b->ctl, sizeof(Control), cudaMemcpyHostToDevice, b->stream));
   if (!b->tuned) {
-    int rc = b->precision == GPMOOD_FP32 ? tune<float>(b, b->pw32) : tune<double>(b, b->pw64);
+    int rc = b->precision == GPMOOD_FP32 ? tune<float>(b, b->pw32, b->dw32)
+                                         : tune<double>(b, b->pw64, b->dw64);
     if (rc) return rc;
   }
   const int prof = (b->prof_on && !b->eager) ? 1 : 0;
@@ -475,6 +514,12 @@ int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t
     cudaGraphExec_t& ge = b->gexec[b->cur][prof];
     if (!ge) {
       int rc = capture_b(b, b->cur, prof, &ge);
+      if (rc && b->coop) {
+        // the driver refused a cooperative kernel node: a plain launch of
+        // the same co-resident grid
+        b->coop = 0;
+        rc = capture_b(b, b->cur, prof, &ge);
+      }
       if (rc) return rc;
     }
     CKB(cudaGraphLaunch(ge, b->stream));
@@ -489,12 +534,12 @@ int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t
     }
     for (int k = GPMOOD_K_GHOST; k <= GPMOOD_K_FACES_Y; ++k) b->prof_n[k] += 3;
     b->prof_n[GPMOOD_K_DT] += 5;
-    b->prof_n[GPMOOD_K_UPDATE] += 6;
-    const Scalars& s = *b->hgsc;
-    b->prof_n[GPMOOD_K_MOOD] += 4 * (s.iters[0] + s.iters[1] + s.iters[2]);
+    b->prof_n[GPMOOD_K_UPDATE] += 3;
+    b->prof_n[GPMOOD_K_MOOD] += 3;
   }
   if (b->hgsc->err & kErrDt) return GPMOOD_E_DT;
   if (b->hgsc->err & kErrCap) return GPMOOD_E_MOOD_CAP;
+  if (b->hgsc->err & kErrSync) return GPMOOD_E_SYNC;
   b->cur = (b->cur + 1) % 3;
   return GPMOOD_OK;
 }
@@ -557,6 +602,16 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   b->nprob = nprob;
   b->top = R_max;
   b->precision = o.precision;
+  b->coop = 1;
+  b->mood_blocks = b->precision == GPMOOD_FP32 ? LaunchB<float>::mood_loop_blocks()
+                                               : LaunchB<double>::mood_loop_blocks();
+  if (b->mood_blocks <= 0 ||
+      (b->precision == GPMOOD_FP32 ? LaunchB<float>::prepare() : LaunchB<double>::prepare()) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return GPMOOD_E_CUDA;
+  }
   b->eager = o.eager ? 1 : 0;
   int widest = 0;
   for (int p = 0; p < nprob; ++p) {
@@ -575,7 +630,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   long long soff = 0, fxo = 0, fyo = 0;
   int coff = 0;
   const size_t fsz = sizeof(double);  // face fluxes are FP64 on both paths
-  std::vector<Item> fx4, fx8, fy4, fy8, up, dtl;
+  std::vector<Item> fx4, fx8, fy4, fy8, up, dtl, xy;
   long long max_ghost = 0;
   for (int p = 0; p < nprob; ++p) {
     const gpmood_grid* gr = &grids[p];
@@ -653,6 +708,11 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
       for (int b2 = 0; b2 < by; ++b2)
         for (int s2 = 0; s2 < sy; ++s2) vy.push_back(Item{p, s2, b2, 0});
     }
+    {
+      const int sx = (g.nx + 1 + kSegFaces - 1) / kSegFaces, bb = (g.ny + 1 + kXYBand - 1) / kXYBand;
+      for (int b2 = 0; b2 < bb; ++b2)
+        for (int s2 = 0; s2 < sx; ++s2) xy.push_back(Item{p, s2, b2, 0});
+    }
     for (int by = 0; by < (g.ny + 7) / 8; ++by)
       for (int bx = 0; bx < (g.nx + 31) / 32; ++bx) up.push_back(Item{p, bx, by, 0});
     for (int ch = 0; ch < (P.ncell + 4095) / 4096; ++ch) dtl.push_back(Item{p, ch, 0, 0});
@@ -694,7 +754,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   ok = ok && cudaMalloc(&b->fb, (size_t)(b->fx_elems + b->fy_elems) / 4) == cudaSuccess;
   ok = ok && cudaMalloc(&b->ord, 3 * nc_all) == cudaSuccess;
   ok = ok && cudaMalloc(&b->first, 3 * nc_all) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->stamp, 4 * nc_all) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->stamp, 8 * nc_all) == cudaSuccess;
   ok = ok && cudaMalloc(&b->queue[0], 4 * nc_all) == cudaSuccess;
   ok = ok && cudaMalloc(&b->queue[1], 4 * nc_all) == cudaSuccess;
   ok = ok && cudaMalloc(&b->probs, sizeof(Prob) * nprob) == cudaSuccess;
@@ -707,6 +767,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
   ok = ok && upload_items(fy8, &b->items_fy[1], &b->n_fy[1]) == 0;
   ok = ok && upload_items(up, &b->items_up, &b->n_up) == 0;
   ok = ok && upload_items(dtl, &b->items_dt, &b->n_dt) == 0;
+  ok = ok && upload_items(xy, &b->items_xy, &b->n_xy) == 0;
   ok = ok && cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&b->cs2, cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; k < 64 && ok; ++k) ok = cudaEventCreate(&b->gev[k]) == cudaSuccess;
@@ -716,7 +777,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
          cudaMemset(b->fb, 0, (size_t)(b->fx_elems + b->fy_elems) / 4) == cudaSuccess &&
          cudaMemset(b->ord, 0, 3 * nc_all) == cudaSuccess &&
          cudaMemset(b->first, 0, 3 * nc_all) == cudaSuccess &&
-         cudaMemset(b->stamp, 0, 4 * nc_all) == cudaSuccess &&
+         cudaMemset(b->stamp, 0, 8 * nc_all) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   for (int k = 0; k < 3 && ok; ++k)
     ok = cudaMemset(b->U[k], 0, sizeof(double) * (size_t)b->state_elems) == cudaSuccess &&
@@ -771,7 +832,7 @@ int gpmood_batch_set_state(gpmood_batch_t b, const double* U, int on_device) {
   CKB(cudaMemcpyAsync(b->psc, z.data(), sizeof(Scalars) * b->nprob, cudaMemcpyHostToDevice,
                       b->stream));
   CKB(cudaMemcpyAsync(b->gsc, z.data(), sizeof(Scalars), cudaMemcpyHostToDevice, b->stream));
-  CKB(cudaMemsetAsync(b->stamp, 0, 4 * (size_t)b->total_cells, b->stream));
+  CKB(cudaMemsetAsync(b->stamp, 0, 8 * (size_t)b->total_cells, b->stream));
   CKB(cudaStreamSynchronize(b->stream));
   b->has_state = 1;
   return GPMOOD_OK;
@@ -848,6 +909,13 @@ int gpmood_batch_tuning(gpmood_batch_t b, int* warps, int* blocks) {
     if (warps) warps[d] = b->fw[d];
     if (blocks) blocks[d] = b->blocks[d];
   }
+  return b->tuned ? GPMOOD_OK : GPMOOD_E_NOSTATE;
+}
+
+int gpmood_batch_grids(gpmood_batch_t b, int* update_blocks, int* mood_blocks) {
+  if (!b) return GPMOOD_E_INVAL;
+  if (update_blocks) *update_blocks = b->up_blocks;
+  if (mood_blocks) *mood_blocks = b->mood_blocks;
   return b->tuned ? GPMOOD_OK : GPMOOD_E_NOSTATE;
 }
 

@@ -51,6 +51,8 @@ struct Control {
   int max_iters;     // MOOD iteration cap per stage
   double* tape;      // recorded steps: stage inputs [3][4][ny][nx] (or null)
   uint8_t* otape;    // and the final radii [3][ny][nx]
+  void* stape;       // and the reconstructed face states (Real, or null): per stage
+                     // x faces left, x right, y lower, y upper, each [4][q_top][faces]
 };
 
 // scalars living on the device (one per handle)
@@ -149,12 +151,14 @@ struct StageArgs {
   double wa, wb;
 };
 
-// the two queues alternate: sc->slot names the one holding the cells of the
-// current iteration, the other receives the cells troubled after it;
-// stamp[c] == sc->stamp_cur marks the cells of the current queue
+// the two queues alternate: one holds the cells of the current iteration,
+// the other receives the cells troubled in it.  The cells of the queue
+// worked on with stamp value v carry v in stamp array v % 2 (two arrays of
+// stamp_stride entries each).
 struct MoodArgs {
   int* queue[2];
   uint32_t* stamp;
+  long long stamp_stride;
   Scalars* sc;
 };
 

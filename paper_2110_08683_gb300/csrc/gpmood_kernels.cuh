@@ -215,42 +215,45 @@ __device__ __forceinline__ bool solver_domain(Real rL, Real rR, Real pL, Real pR
 // x-direction HLLC flux; pL/pR return the pressures of the two states so the
 // caller can run face-state CAD without another EoS evaluation.
 // wave speeds S_L = min(uL-cL, uR-cR), S_R = max(uL+cL, uR+cR); the star
-// state is taken on the side of the contact speed S*.
+// state is taken on the side of the contact speed S*.  Every product is an
+// explicit fma or a product rounded on its own, so the compiler cannot fuse
+// operations differently in different kernels: every kernel that solves a
+// face gets the same flux bit for bit.
 template <class Real>
 __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam, Real* F,
                                        Real& pL, Real& pR) {
   const Real gm1 = gam - Real(1);
   Real rL = UL[0], rR = UR[0];
   Real irL = recip(rL), irR = recip(rR);
-  Real uL = UL[1] * irL, vL = UL[2] * irL;
-  Real uR = UR[1] * irR, vR = UR[2] * irR;
-  pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
-  pR = gm1 * (UR[3] - Real(0.5) * (UR[1] * uR + UR[2] * vR));
-  Real cL = sqrt_r(gam * pL * irL), cR = sqrt_r(gam * pR * irR);
+  Real uL, vL, uR, vR;
+  pL = pressure_ir(UL, irL, gm1, uL, vL);
+  pR = pressure_ir(UR, irR, gm1, uR, vR);
+  Real cL = sqrt_r(mul_rn(mul_rn(gam, pL), irL)), cR = sqrt_r(mul_rn(mul_rn(gam, pR), irR));
   Real aL = uL - cL, bL = uR - cR;
   Real SL = aL < bL ? aL : bL;
   Real aR = uL + cL, bR = uR + cR;
   Real SR = aR > bR ? aR : bR;
   Real dL = SL - uL, dR = SR - uR;
-  Real num = pR - pL + rL * uL * dL - rR * uR * dR;
-  Real den = rL * dL - rR * dR;
-  Real Ss = num * recip(den);
+  const Real mL = mul_rn(rL, uL), mR = mul_rn(rR, uR);
+  Real num = fma(-mR, dR, fma(mL, dL, pR - pL));
+  Real den = fma(-rR, dR, mul_rn(rL, dL));
+  Real Ss = mul_rn(num, recip(den));
   bool left = Ss >= Real(0);
-  Real FL[4] = {rL * uL, rL * uL * uL + pL, rL * uL * vL, uL * (UL[3] + pL)};
-  Real FR[4] = {rR * uR, rR * uR * uR + pR, rR * uR * vR, uR * (UR[3] + pR)};
+  Real FL[4] = {mL, fma(mL, uL, pL), mul_rn(mL, vL), mul_rn(uL, UL[3] + pL)};
+  Real FR[4] = {mR, fma(mR, uR, pR), mul_rn(mR, vR), mul_rn(uR, UR[3] + pR)};
   // star state on side K of the contact
   Real rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR;
   Real EK = left ? UL[3] : UR[3], pK = left ? pL : pR, SK = left ? SL : SR;
   Real irK = left ? irL : irR, dK = left ? dL : dR;
-  Real fK = rK * dK * recip(SK - Ss);
-  Real eK = EK * irK + (Ss - uK) * (Ss + pK * irK * recip(dK));
-  Real UKs[4] = {fK, fK * Ss, fK * vK, fK * eK};
+  Real fK = mul_rn(mul_rn(rK, dK), recip(SK - Ss));
+  Real eK = fma(EK, irK, mul_rn(Ss - uK, fma(mul_rn(pK, irK), recip(dK), Ss)));
+  Real UKs[4] = {fK, mul_rn(fK, Ss), mul_rn(fK, vK), mul_rn(fK, eK)};
   Real Fs[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     Real FK = left ? FL[v] : FR[v];
     Real UK = left ? UL[v] : UR[v];
-    Fs[v] = FK + SK * (UKs[v] - UK);
+    Fs[v] = fma(SK, UKs[v] - UK, FK);
   }
   bool useL = SL >= Real(0);
   bool useS = left || (SR > Real(0));
@@ -486,6 +489,58 @@ __device__ __forceinline__ bool face_state_bad(const StageArgs<Real>& A, const G
 }
 
 // ---------------------------------------------------------------------------
+// the face-state tape of a recorded step (Control::stape): the states the
+// step's final fluxes were solved from, so that the adjoint need not
+// reconstruct them again.  Per stage: x faces (left, right states), y faces
+// (lower, upper), each [4 variables][qt points][faces of that direction],
+// qt the rule size of the top radius.  Null when the step records none.
+// ---------------------------------------------------------------------------
+template <class Real>
+__device__ __forceinline__ Real* state_tape(const StageArgs<Real>& A, const Grid& g, int qt,
+                                            int dir, int side) {
+  Real* base = (Real*)A.sc->ctl.stape;
+  if (!base) return nullptr;
+  const long long nfx = (long long)(g.nx + 1) * g.ny, nfy = (long long)g.nx * (g.ny + 1);
+  base += (long long)A.stage * 8 * qt * (nfx + nfy);
+  return dir == 0 ? base + (long long)side * 4 * qt * nfx
+                  : base + 8LL * qt * nfx + (long long)side * 4 * qt * nfy;
+}
+
+// the states UL / UR of point q of face f (of its direction) into the tape
+template <class Real>
+__device__ __forceinline__ void tape_states(Real* tL, Real* tR, int qt, long long nf, long long f,
+                                            int q, const Real* UL, const Real* UR) {
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    tL[((long long)v * qt + q) * nf + f] = UL[v];
+    tR[((long long)v * qt + q) * nf + f] = UR[v];
+  }
+}
+
+// the same for the face between (iL, jL) and its neighbour in direction DIR
+// (a periodic seam face: both copies), when the step records states
+template <class Real, int DIR>
+__device__ __forceinline__ void tape_face(const StageArgs<Real>& A, const Grid& g, int qt, int iL,
+                                          int jL, int q, const Real* UL, const Real* UR) {
+  Real* tL = state_tape<Real>(A, g, qt, DIR, 0);
+  if (!tL) return;
+  Real* tR = state_tape<Real>(A, g, qt, DIR, 1);
+  if (DIR == 0) {
+    const long long nf = (long long)(g.nx + 1) * g.ny;
+    const int f = iL + 1;
+    tape_states(tL, tR, qt, nf, (long long)jL * (g.nx + 1) + f, q, UL, UR);
+    if (g.periodic_x && (f == 0 || f == g.nx))
+      tape_states(tL, tR, qt, nf, (long long)jL * (g.nx + 1) + (f == 0 ? g.nx : 0), q, UL, UR);
+  } else {
+    const long long nf = (long long)g.nx * (g.ny + 1);
+    const int f = jL + 1;
+    tape_states(tL, tR, qt, nf, (long long)f * g.nx + iL, q, UL, UR);
+    if (g.periodic_y && (f == 0 || f == g.ny))
+      tape_states(tL, tR, qt, nf, (long long)(f == 0 ? g.ny : 0) * g.nx + iL, q, UL, UR);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // first-pass faces at the top radius R.  One warp covers 32 consecutive
 // cells of a row (x_faces) or a column (y_faces) and produces the 31 faces
 // between them; the left/lower states come from the neighbouring lane.
@@ -501,11 +556,12 @@ struct FaceTile {
   Real t[4][TS][TF];
 };
 
-// stage the ghosted state X (any element type) around segment `seg` along
-// the sweep and band `band` across it into the shared tile, as Real
+// stage the ghosted state X (any element type) around the block whose first
+// cell is `first_fast` along the sweep and `first_slow` across it into the
+// shared tile, as Real
 template <int R, class Real, int DIR, int FW, class TX>
-__device__ __forceinline__ void tile_load(FaceTile<R, Real, FW>& T_, const TX* X, const Grid& g,
-                                          int seg, int band) {
+__device__ __forceinline__ void tile_load_at(FaceTile<R, Real, FW>& T_, const TX* X,
+                                             const Grid& g, int first_fast, int first_slow) {
   constexpr int TF = FaceTile<R, Real, FW>::TF;
   constexpr int TS = FaceTile<R, Real, FW>::TS;
   constexpr int NE = TS * TF;                 // tile cells of one variable
@@ -513,8 +569,8 @@ __device__ __forceinline__ void tile_load(FaceTile<R, Real, FW>& T_, const TX* X
   constexpr int NP = (NE + NT - 1) / NT;      // tile cells per thread
   Real* tile = &T_.t[0][0][0];
   const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int fast0 = seg * kSegFaces - 1 - R;  // first tile cell along the sweep
-  const int slow0 = band * FW - R;            // first tile cell across it
+  const int fast0 = first_fast - R;           // first tile cell along the sweep
+  const int slow0 = first_slow - R;           // first tile cell across it
   // the cells this thread stages, worked out once for the four variables:
   // consecutive threads take consecutive cells along x (coalesced loads)
   long long off[NP];
@@ -538,6 +594,13 @@ __device__ __forceinline__ void tile_load(FaceTile<R, Real, FW>& T_, const TX* X
     for (int p = 0; p < NP; ++p)
       if (tid + p * NT < NE)
         tile[v * NE + soff[p]] = ok[p] ? (Real)__ldg(X + off[p] + v * g.vstride) : Real(0);
+}
+
+// the tile of segment `seg` along the sweep and band `band` across it
+template <int R, class Real, int DIR, int FW, class TX>
+__device__ __forceinline__ void tile_load(FaceTile<R, Real, FW>& T_, const TX* X, const Grid& g,
+                                          int seg, int band) {
+  tile_load_at<R, Real, DIR, FW>(T_, X, g, seg * kSegFaces - 1, band * FW);
 }
 
 // states at all Gauss points of the two faces of one tile cell across the
@@ -681,6 +744,14 @@ __device__ __forceinline__ void faces_block(const StageArgs<Real>& A, const Grid
     for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, i, j)] = F[v];
     A.fby[(long long)j * g.nx + i] = (uint8_t)((badL ? 1 : 0) | (badR ? 2 : 0));
   }
+  // a recorded step keeps the states for its adjoint
+  if (Real* tL = state_tape<Real>(A, g, Q, DIR, 0)) {
+    Real* tR = state_tape<Real>(A, g, Q, DIR, 1);
+    const long long nf = DIR == 0 ? (long long)(g.nx + 1) * g.ny : (long long)g.nx * (g.ny + 1);
+    const long long f = DIR == 0 ? (long long)j * (g.nx + 1) + i : (long long)j * g.nx + i;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) tape_states(tL, tR, Q, nf, f, q, SL[q], SM[q]);
+  }
 }
 
 template <int R, class Real, int DIR, int FW>
@@ -694,6 +765,200 @@ __global__ void __launch_bounds__(32 * FW) k_faces(StageArgs<Real> A, Grid g,
 }
 
 // ---------------------------------------------------------------------------
+// both first-pass face sweeps in one block (two-dimensional grids).  A block
+// of 8 warps covers 8 rows of a 32-cell segment: lane l, warp w hold cell
+// (i0 + l, j0 + w), i0 = 31 seg - 1, j0 = 7 band - 1, so segments overlap by
+// one column and bands by one row.  Each cell forms its parity sums once per
+// variable and from them both its x states (E/W, kept in registers for the
+// x faces, taken from the neighbouring lane by shuffle) and its y states
+// (N/S, written to shared memory for the y faces between consecutive rows).
+// A thread with l, w >= 1 then solves the x face between (i-1, j) and
+// (i, j) and the y face between (i, j-1) and (i, j).  The arithmetic of
+// every state and flux is that of the separate sweeps (k_faces), so the
+// fluxes are the same bit for bit; y fluxes are stored with lanes along x.
+// ---------------------------------------------------------------------------
+constexpr int kXYRows = 8;               // cell rows of a fused face block (its warps)
+constexpr int kXYBand = kXYRows - 1;     // face rows a block owns
+
+template <int R, class Real>
+struct XYShared {
+  FaceTile<R, Real, kXYRows> tile;
+  Real ys[2][rule_q(R)][4][kXYRows][32];  // [N, S][point][variable][row][lane]
+};
+
+// one fused block: segment `seg` (31 x faces) and band `band` (7 rows of
+// faces) of the grid
+template <int R, class Real>
+__device__ __forceinline__ void faces_xy_block(const StageArgs<Real>& A, const Grid& g,
+                                               const ParityW<Real>& W, int seg, int band,
+                                               XYShared<R, Real>& S) {
+  constexpr int N = stencil_n(R);
+  constexpr int Q = rule_q(R);
+  constexpr int NS = (Q + 1) / 2;
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int i0 = seg * kSegFaces - 1, j0 = band * kXYBand - 1;
+  tile_load_at<R, Real, 0, kXYRows>(S.tile, A.Xr, g, i0, j0);
+  __syncthreads();
+  const int i = i0 + lane, j = j0 + warp;
+  // rows beyond the last y face take no part (their states feed nothing)
+  const bool row_live = j <= g.ny;
+  const bool xrow = warp >= 1 && j < g.ny;  // this warp's x faces are the block's
+  Real SP[Q][4], SM[Q][4];
+  auto& tile = S.tile.t;
+  const int fl = lane + R, sw = warp + R;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    Real s[N];
+    if (row_live) {
+      auto ld = [&](int a, int b) -> Real { return tile[v][sw + b][fl + a]; };
+      parity_sums<R, Real>(ld, s);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) s[k] = Real(0);
+    }
+#pragma unroll
+    for (int kk = 0; kk < NS; ++kk) {
+      const bool middle = (Q & 1) && kk == Q / 2;
+      if (xrow) {
+        // east / west at +g and -g (the x sweep's butterflies)
+        Real T[2][2];
+        parity_dot<R, Real>(W.cx[kk], s, T);
+        if (middle) {
+          SP[kk][v] = T[0][0] + T[1][0];
+          SM[kk][v] = T[0][0] - T[1][0];
+        } else {
+          Real e = T[0][0] + T[0][1], o = T[1][0] + T[1][1];
+          Real e2 = T[0][0] - T[0][1], o2 = T[1][0] - T[1][1];
+          SP[kk][v] = e + o;
+          SM[kk][v] = e - o;
+          SP[Q - 1 - kk][v] = e2 + o2;
+          SM[Q - 1 - kk][v] = e2 - o2;
+        }
+      }
+      // north / south at +g and -g (the y sweep's butterflies), to shared memory
+      Real T[2][2];
+      parity_dot<R, Real>(W.cy[kk], s, T);
+      if (middle) {
+        S.ys[0][kk][v][warp][lane] = T[0][0] + T[0][1];
+        S.ys[1][kk][v][warp][lane] = T[0][0] - T[0][1];
+      } else {
+        Real e = T[0][0] + T[1][0], o = T[0][1] + T[1][1];
+        Real e2 = T[0][0] - T[1][0], o2 = T[0][1] - T[1][1];
+        S.ys[0][kk][v][warp][lane] = e + o;
+        S.ys[1][kk][v][warp][lane] = e - o;
+        S.ys[0][Q - 1 - kk][v][warp][lane] = e2 + o2;
+        S.ys[1][Q - 1 - kk][v][warp][lane] = e2 - o2;
+      }
+    }
+  }
+  const Real gam = (Real)g.gamma;
+  // x faces: the left state from the neighbouring lane
+  if (xrow) {
+    Real SL[Q][4];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) SL[q][v] = __shfl_up_sync(0xffffffffu, SP[q][v], 1);
+    if (lane >= 1 && i <= g.nx) {
+      Real F[4] = {0, 0, 0, 0};
+      bool badL = false, badR = false;
+      auto point = [&](int q, Real* f) {
+        Real pl, pr;
+        riemann_x<Real>(g.riemann, SL[q], SM[q], gam, f, pl, pr);
+        badL |= !(pos_finite(SL[q][0]) && pos_finite(pl));
+        badR |= !(pos_finite(SM[q][0]) && pos_finite(pr));
+      };
+#pragma unroll
+      for (int kk = 0; kk < NS; ++kk) {
+        Real f1[4];
+        point(kk, f1);
+        if (Q - 1 - kk != kk) {
+          Real f2[4];
+          point(Q - 1 - kk, f2);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) F[v] = fma(W.w[kk], add_rn(f1[v], f2[v]), F[v]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) F[v] = fma(W.w[kk], f1[v], F[v]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) A.Fx[fxidx(g, v, i, j)] = F[v];
+      A.fbx[(long long)j * (g.nx + 1) + i] = (uint8_t)((badL ? 1 : 0) | (badR ? 2 : 0));
+      if (Real* tL = state_tape<Real>(A, g, Q, 0, 0)) {
+        Real* tR = state_tape<Real>(A, g, Q, 0, 1);
+        const long long nf = (long long)(g.nx + 1) * g.ny, f = (long long)j * (g.nx + 1) + i;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) tape_states(tL, tR, Q, nf, f, q, SL[q], SM[q]);
+      }
+    }
+  }
+  __syncthreads();
+  // y faces: the lower state from the row below, both from shared memory
+  if (warp >= 1 && lane >= 1 && i < g.nx && j <= g.ny) {
+    Real F[4] = {0, 0, 0, 0};
+    bool badL = false, badR = false;
+    auto point = [&](int q, Real* f) {
+      Real a[4], b[4];
+      a[0] = S.ys[0][q][0][warp - 1][lane];
+      a[1] = S.ys[0][q][2][warp - 1][lane];
+      a[2] = S.ys[0][q][1][warp - 1][lane];
+      a[3] = S.ys[0][q][3][warp - 1][lane];
+      b[0] = S.ys[1][q][0][warp][lane];
+      b[1] = S.ys[1][q][2][warp][lane];
+      b[2] = S.ys[1][q][1][warp][lane];
+      b[3] = S.ys[1][q][3][warp][lane];
+      Real h[4], pl, pr;
+      riemann_x<Real>(g.riemann, a, b, gam, h, pl, pr);
+      f[0] = h[0]; f[1] = h[2]; f[2] = h[1]; f[3] = h[3];
+      badL |= !(pos_finite(a[0]) && pos_finite(pl));
+      badR |= !(pos_finite(b[0]) && pos_finite(pr));
+    };
+#pragma unroll
+    for (int kk = 0; kk < NS; ++kk) {
+      Real f1[4];
+      point(kk, f1);
+      if (Q - 1 - kk != kk) {
+        Real f2[4];
+        point(Q - 1 - kk, f2);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) F[v] = fma(W.w[kk], add_rn(f1[v], f2[v]), F[v]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) F[v] = fma(W.w[kk], f1[v], F[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) A.Fy[fyidx(g, v, i, j)] = F[v];
+    A.fby[(long long)j * g.nx + i] = (uint8_t)((badL ? 1 : 0) | (badR ? 2 : 0));
+    if (Real* tL = state_tape<Real>(A, g, Q, 1, 0)) {
+      Real* tR = state_tape<Real>(A, g, Q, 1, 1);
+      const long long nf = (long long)g.nx * (g.ny + 1), f = (long long)j * g.nx + i;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        Real UL[4], UR[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          UL[v] = S.ys[0][q][v][warp - 1][lane];
+          UR[v] = S.ys[1][q][v][warp][lane];
+        }
+        tape_states(tL, tR, Q, nf, f, q, UL, UR);
+      }
+    }
+  }
+}
+
+template <int R, class Real>
+__global__ void __launch_bounds__(32 * kXYRows, 2) k_faces_xy(StageArgs<Real> A, Grid g,
+                                                           const __grid_constant__ ParityW<Real> W) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char xy_smem[];
+  XYShared<R, Real>& S = *reinterpret_cast<XYShared<R, Real>*>(xy_smem);
+  faces_xy_block<R, Real>(A, g, W, blockIdx.x, blockIdx.y, S);
+}
+
+// ---------------------------------------------------------------------------
 // detection, Steps 4-9 (eqs. CAD, PAD, divV, gradP, plateau, DMP_RK,
 // u2_curvature, u2_a, u2_b) on the candidate Y of cell (i,j) with the ghosted
 // stage input X.  Returns true for a troubled cell.
@@ -703,10 +968,11 @@ __device__ __forceinline__ Real xload(const Real* X, const Grid& g, int v, int i
   return __ldg(X + gidx(g, v, i, j));
 }
 
-// X: the ghosted stage input in Real
-template <class Real>
-__device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Real* d2x,
-                         const Real* d2y, int i, int j, const double* Yd) {
+// X(v, a, b): variable v of the ghosted stage input at (i + a, j + b), in
+// Real; every call below has constant offsets once the loops are unrolled
+template <class Real, class LX>
+__device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const Detect& D,
+                                            const Real* d2x, const Real* d2y, const double* Yd) {
   const Real gm1 = (Real)(g.gamma - 1.0);
   Real Y[4] = {(Real)Yd[0], (Real)Yd[1], (Real)Yd[2], (Real)Yd[3]};
   Real rho = Y[0];
@@ -715,14 +981,14 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
   if (!(rho > Real(0)) || !(p > Real(0))) return true; // Step 5, PAD
   const bool two = g.dim == 2;  // 1D: the x terms and the W/E neighbours only
   if (D.csd_on) {                                      // Step 6, CSD
-    Real rE = xload<Real>(X, g, 0, i + 1, j), rW = xload<Real>(X, g, 0, i - 1, j);
-    Real rN = xload<Real>(X, g, 0, i, j + 1), rS = xload<Real>(X, g, 0, i, j - 1);
-    Real mxE = xload<Real>(X, g, 1, i + 1, j), mxW = xload<Real>(X, g, 1, i - 1, j);
-    Real myE = xload<Real>(X, g, 2, i + 1, j), myW = xload<Real>(X, g, 2, i - 1, j);
-    Real mxN = xload<Real>(X, g, 1, i, j + 1), mxS = xload<Real>(X, g, 1, i, j - 1);
-    Real myN = xload<Real>(X, g, 2, i, j + 1), myS = xload<Real>(X, g, 2, i, j - 1);
-    Real eE = xload<Real>(X, g, 3, i + 1, j), eW = xload<Real>(X, g, 3, i - 1, j);
-    Real eN = xload<Real>(X, g, 3, i, j + 1), eS = xload<Real>(X, g, 3, i, j - 1);
+    Real rE = X(0, 1, 0), rW = X(0, -1, 0);
+    Real rN = X(0, 0, 1), rS = X(0, 0, -1);
+    Real mxE = X(1, 1, 0), mxW = X(1, -1, 0);
+    Real myE = X(2, 1, 0), myW = X(2, -1, 0);
+    Real mxN = X(1, 0, 1), mxS = X(1, 0, -1);
+    Real myN = X(2, 0, 1), myS = X(2, 0, -1);
+    Real eE = X(3, 1, 0), eW = X(3, -1, 0);
+    Real eN = X(3, 0, 1), eS = X(3, 0, -1);
     Real iE = recip(rE), iW = recip(rW), iN = recip(rN), iS = recip(rS);
     // one rounded sequence for every neighbour: mirror neighbours agree bitwise
     const Real SE[4] = {rE, mxE, myE, eE}, SW[4] = {rW, mxW, myW, eW};
@@ -741,14 +1007,14 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
     }
     if (divV >= -(Real)D.sigma_v && gradP <= (Real)D.sigma_p) return false;
   }
-  Real r0 = xload<Real>(X, g, 0, i, j);
+  Real r0 = X(0, 0, 0);
   Real rmin = r0, rmax = r0;
   const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, 1, -1};
   const int nnb = two ? 4 : 2;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     if (m >= nnb) break;
-    Real r = xload<Real>(X, g, 0, i + di[m], j + dj[m]);
+    Real r = X(0, di[m], dj[m]);
     rmin = r < rmin ? r : rmin;
     rmax = r > rmax ? r : rmax;
   }
@@ -766,14 +1032,12 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
       if (m >= 1 + nnb) break;
-      int ii = i + ci[m], jj = j + cj[m];
+      const int a = ci[m], b = cj[m];
       // mirror pairs (S, N) and (W, E) summed first, each product rounded on
       // its own: a mirror-symmetric state gives the same curvature bit for bit
-      const Real ks = add_rn(mul_rn(w[0], xload<Real>(X, g, 0, ii, jj - 1)),
-                             mul_rn(w[4], xload<Real>(X, g, 0, ii, jj + 1)));
-      const Real kw = add_rn(mul_rn(w[1], xload<Real>(X, g, 0, ii - 1, jj)),
-                             mul_rn(w[3], xload<Real>(X, g, 0, ii + 1, jj)));
-      Real k = add_rn(add_rn(ks, kw), mul_rn(w[2], xload<Real>(X, g, 0, ii, jj)));
+      const Real ks = add_rn(mul_rn(w[0], X(0, a, b - 1)), mul_rn(w[4], X(0, a, b + 1)));
+      const Real kw = add_rn(mul_rn(w[1], X(0, a - 1, b)), mul_rn(w[3], X(0, a + 1, b)));
+      Real k = add_rn(add_rn(ks, kw), mul_rn(w[2], X(0, a, b)));
       if (m == 0) {
         cmin = k;
         cmax = k;
@@ -791,6 +1055,48 @@ __device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Re
     if (!(ua || ub)) return true;
   }
   return false;
+}
+
+// X: the ghosted stage input in Real; the loads are issued as the tests
+// reach them (the first pass: many cells in flight hide their latency)
+template <class Real>
+__device__ bool troubled(const Real* X, const Grid& g, const Detect& D, const Real* d2x,
+                         const Real* d2y, int i, int j, const double* Yd) {
+  auto lx = [&](int v, int a, int b) -> Real { return xload<Real>(X, g, v, i + a, j + b); };
+  return troubled_at<Real>(lx, g, D, d2x, d2y, Yd);
+}
+
+// slot of offset (a, b) in the diamond |a| + |b| <= 2 (13 cells)
+__host__ __device__ constexpr int diamond2_slot(int a, int b) {
+  return b == -2 ? 0 : b == -1 ? 2 + a : b == 0 ? 6 + a : b == 1 ? 10 + a : 12;
+}
+
+// the same tests with every value they may read loaded first, in one batch:
+// the densities of the diamond |a| + |b| <= 2 and the momenta and energies
+// of the four face neighbours.  For the MOOD loop, whose few cells per
+// iteration leave the latency of dependent loads exposed.
+template <class Real>
+__device__ bool troubled_prefetched(const Real* X, const Grid& g, const Detect& D,
+                                    const Real* d2x, const Real* d2y, int i, int j,
+                                    const double* Yd) {
+  Real r[13], m[3][4];
+#pragma unroll
+  for (int b = -2; b <= 2; ++b) {
+    const int hb = 2 - (b < 0 ? -b : b);
+#pragma unroll
+    for (int a = -hb; a <= hb; ++a) r[diamond2_slot(a, b)] = xload<Real>(X, g, 0, i + a, j + b);
+  }
+  const int fa[4] = {1, -1, 0, 0}, fb[4] = {0, 0, 1, -1};
+#pragma unroll
+  for (int v = 1; v < 4; ++v)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m[v - 1][k] = xload<Real>(X, g, v, i + fa[k], j + fb[k]);
+  auto lx = [&](int v, int a, int b) -> Real {
+    if (v == 0) return r[diamond2_slot(a, b)];
+    const int k = a == 1 ? 0 : a == -1 ? 1 : b == 1 ? 2 : 3;
+    return m[v - 1][k];
+  };
+  return troubled_at<Real>(lx, g, D, d2x, d2y, Yd);
 }
 
 // candidate of eq. fvm_discrete and the SSP-RK3 combination (eq. rk3) of cell (i,j)
@@ -948,7 +1254,8 @@ __device__ __forceinline__ void recon_direct(const T* X, const Grid& g, const Re
 template <int K, class Real, int DIR>
 __device__ __forceinline__ void face_point(const Real* X, const Grid& g, const DirectW<Real>& Wd,
                                            int iL, int jL, int q, Real* f, bool& badL,
-                                           bool& badR) {
+                                           bool& badR, Real* sUL = nullptr,
+                                           Real* sUR = nullptr) {
   const int iR = iL + (DIR == 0), jR = jL + (DIR == 1);
   const Real gam = (Real)g.gamma;
   Real UL[4], UR[4];
@@ -975,6 +1282,13 @@ __device__ __forceinline__ void face_point(const Real* X, const Grid& g, const D
   }
   badL |= !(pos_finite(UL[0]) && pos_finite(pl));
   badR |= !(pos_finite(UR[0]) && pos_finite(pr));
+  if (sUL) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sUL[v] = UL[v];
+      sUR[v] = UR[v];
+    }
+  }
 }
 
 // face between cell (iL,jL) and its neighbour (iR,jR) in direction DIR at radius K
@@ -1088,12 +1402,13 @@ __device__ __forceinline__ void mood_face_item(const StageArgs<Real>& A, const G
 template <class Real, int DIR>
 __device__ __forceinline__ void face_point_k(int K, const Real* X, const Grid& g,
                                              const DirectW<Real>& Wd, int iL, int jL, int q,
-                                             Real* f, bool& bl, bool& br) {
+                                             Real* f, bool& bl, bool& br, Real* sUL,
+                                             Real* sUR) {
   switch (K) {
-    case 0: face_point<0, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
-    case 1: face_point<1, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
-    case 2: face_point<2, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
-    default: face_point<3, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br); break;
+    case 0: face_point<0, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br, sUL, sUR); break;
+    case 1: face_point<1, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br, sUL, sUR); break;
+    case 2: face_point<2, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br, sUL, sUR); break;
+    default: face_point<3, Real, DIR>(X, g, Wd, iL, jL, q, f, bl, br, sUL, sUR); break;
   }
 }
 
@@ -1186,7 +1501,8 @@ __device__ __forceinline__ bool mood_update_item(const StageArgs<Real>& A, const
   candidate<Real>(A, g, di, dj, A.sc->dt, Y);
   bool flag = false;
   if (A.ord[d] != 0) {
-    flag = face_state_bad<Real>(A, g, di, dj) || troubled<Real>(A.Xr, g, D, d2x, d2y, di, dj, Y);
+    flag = face_state_bad<Real>(A, g, di, dj) ||
+           troubled_prefetched<Real>(A.Xr, g, D, d2x, d2y, di, dj, Y);
   } else {
     Real y[4] = {(Real)Y[0], (Real)Y[1], (Real)Y[2], (Real)Y[3]};
     Real p = (Real)(g.gamma - 1.0) * (y[3] - Real(0.5) * (y[1] * y[1] + y[2] * y[2]) / y[0]);
@@ -1194,50 +1510,6 @@ __device__ __forceinline__ bool mood_update_item(const StageArgs<Real>& A, const
   }
   combine_store<Real>(A, g, di, dj, Y);
   return flag;
-}
-
-// one thread per (queued cell, face)
-template <class Real>
-__global__ void __launch_bounds__(128) k_mood_faces(StageArgs<Real> A, MoodArgs M, Grid g,
-                                                    const __grid_constant__ DirectW<Real> Wd,
-                                                    Cascade C) {
-  pdl_wait();
-  pdl_trigger();
-  const int slot = M.sc->slot;
-  const int n = M.sc->count[slot];
-  const int* queue = M.queue[slot];
-  const uint32_t cur = M.sc->stamp_cur;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4LL * n;
-       t += (long long)gridDim.x * blockDim.x)
-    mood_face_item<Real>(A, g, Wd, C, M.stamp, cur, queue[t >> 2], (int)(t & 3));
-}
-
-// queued cells and their face neighbours
-template <class Real>
-__global__ void __launch_bounds__(256) k_mood_update(StageArgs<Real> A, MoodArgs M, Grid g,
-                                                     Detect D,
-                                                     const __grid_constant__ DirectW<Real> Wd) {
-  pdl_wait();
-  pdl_trigger();
-  const int slot = M.sc->slot;
-  const int n = M.sc->count[slot];
-  const int* queue = M.queue[slot];
-  int* next_queue = M.queue[slot ^ 1];
-  int* next_count = &M.sc->count[slot ^ 1];
-  const uint32_t cur = M.sc->stamp_cur;
-  const int nthreads = gridDim.x * blockDim.x;
-  const int rounds = (n + nthreads - 1) / nthreads;
-  for (int r = 0; r < rounds; ++r) {
-    const int q = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = q < n;
-    const int c = live ? queue[q] : 0;
-    for (int k = 0; k < 5; ++k) {
-      int d = -1;
-      bool flag = false;
-      if (live) flag = mood_update_item<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, M.stamp, cur, c, k, d);
-      queue_push(flag, d, next_queue, next_count);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1293,47 +1565,183 @@ __device__ __forceinline__ bool grid_barrier(Scalars* sc) {
   return ok != 0;
 }
 
+// the stamps of value v: two arrays, one per parity of v, so that an
+// iteration can mark the cells of the next queue (value v + 1) while its own
+// queue's marks (value v) are still being read
+__device__ __forceinline__ uint32_t* stamp_of(const MoodArgs& M, uint32_t v) {
+  return M.stamp + (long long)(v & 1u) * M.stamp_stride;
+}
+
+// problem of a pooled cell index gc: the handle's single problem
 template <class Real>
-__global__ void __launch_bounds__(256) k_mood_loop(StageArgs<Real> A, MoodArgs M, Grid g,
-                                                   Detect D,
-                                                   const __grid_constant__ DirectW<Real> Wd,
-                                                   Cascade C, int stage) {
-  pdl_wait();
+struct SingleSite {
+  const StageArgs<Real>& A;
+  const Grid& g;
+  const Detect& D;
+  const Real* d2x;
+  const Real* d2y;
+  template <class F>
+  __device__ __forceinline__ void with(int gc, F&& f) const {
+    f(A, g, D, d2x, d2y, 0);
+  }
+};
+
+// lane index of a MOOD phase: the warps are ranked block-minor (warp 0 of
+// every block, then warp 1, ...), so the few warps of a short iteration land
+// on different SMs and FP64 sub-partitions instead of queueing on one
+__device__ __forceinline__ long long mood_lane() {
+  return ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+}
+
+// the MOOD face recompute with one lane per Gauss point: lane t covers
+// pooled cell queue[t / 16], face (t / 4) % 4, point t % 4.  Each lane
+// reconstructs its point's two states and solves its Riemann problem; the
+// group's first lane forms the Gauss sum in the order of face_at (mirror
+// pairs summed first), so the flux is the same bit for bit.  Called by whole
+// warps (the loop runs per warp: all 32 lanes take part in the shuffles).
+template <class Real, class Site>
+__device__ __forceinline__ void mood_faces_phase(const Site& site, const MoodArgs& M,
+                                                 const DirectW<Real>& Wd, const Cascade& C,
+                                                 uint32_t cur, const int* queue, int n) {
+  const long long L = 16LL * n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int base = lane & ~3;
+  const uint32_t* stamp = stamp_of(M, cur);
+  for (long long t0 = mood_lane() - lane; t0 < L; t0 += stride) {
+    const long long t = t0 + lane;
+    const int q = (int)(t & 3);
+    const int f = (int)((t >> 2) & 3);
+    const int gc = t < L ? queue[t >> 4] : 0;
+    int iL = 0, jL = 0, K = 0;
+    bool work = false;
+    Real fq[4] = {Real(0), Real(0), Real(0), Real(0)};
+    bool bl = false, br = false;
+    if (t < L)
+      site.with(gc, [&](const StageArgs<Real>& A, const Grid& g, const Detect&, const Real*,
+                        const Real*, int off) {
+        work = mood_face_plan<Real>(A, g, C, stamp + off, cur, gc - off, f, iL, jL, K);
+        if (work && q < rule_q(K)) {
+          // a recorded step keeps the states of the recomputed face
+          const bool keep = A.sc->ctl.stape != nullptr;
+          Real UL[4], UR[4];
+          if (f < 2)
+            face_point_k<Real, 0>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br, keep ? UL : nullptr, UR);
+          else
+            face_point_k<Real, 1>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br, keep ? UL : nullptr, UR);
+          if (keep) {
+            const int qt = rule_q(Wd.top);
+            if (f < 2) tape_face<Real, 0>(A, g, qt, iL, jL, q, UL, UR);
+            else tape_face<Real, 1>(A, g, qt, iL, jL, q, UL, UR);
+          }
+        }
+      });
+    Real fp[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) fp[p][v] = __shfl_sync(0xffffffffu, fq[v], base + p);
+    const unsigned bbl = __ballot_sync(0xffffffffu, bl), bbr = __ballot_sync(0xffffffffu, br);
+    if (work && q == 0) {
+      // face_at's loop over (g, -g) pairs written out per rule size
+      const int Q = rule_q(K);
+      const Real w0 = Wd.w[K][0], w1 = Wd.w[K][1];
+      Real F[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const Real z = Real(0);
+        if (Q == 4) F[v] = fma(w1, add_rn(fp[1][v], fp[2][v]), fma(w0, add_rn(fp[0][v], fp[3][v]), z));
+        else if (Q == 3) F[v] = fma(w1, fp[1][v], fma(w0, add_rn(fp[0][v], fp[2][v]), z));
+        else if (Q == 2) F[v] = fma(w0, add_rn(fp[0][v], fp[1][v]), z);
+        else F[v] = fma(w0, fp[0][v], z);
+      }
+      const uint8_t bits = (uint8_t)((((bbl >> base) & 0xFu) ? 1 : 0) |
+                                     (((bbr >> base) & 0xFu) ? 2 : 0));
+      site.with(gc, [&](const StageArgs<Real>& A, const Grid& g, const Detect&, const Real*,
+                        const Real*, int) {
+        if (f < 2) store_face<Real, 0>(A, g, iL, jL, F, bits);
+        else store_face<Real, 1>(A, g, iL, jL, F, bits);
+      });
+    }
+  }
+}
+
+// re-update + re-detect: item t is entry t % 5 (itself, W, E, S, N) of
+// pooled cell queue[t / 5]; a cell found troubled is lowered one cascade
+// level at once, marked with the next stamp and appended to the next queue
+template <class Real, class Site>
+__device__ __forceinline__ void mood_update_phase(const Site& site, const MoodArgs& M,
+                                                  const DirectW<Real>& Wd, const Cascade& C,
+                                                  uint32_t cur, const int* queue, int n,
+                                                  int* next_queue, int* next_count) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const uint32_t* stamp = stamp_of(M, cur);
+  uint32_t* next_stamp = stamp_of(M, cur + 1);
+  for (long long t = mood_lane(); t < 5LL * n; t += stride) {
+    const int gc = queue[t / 5];
+    int dg = -1;
+    bool flag = false;
+    site.with(gc, [&](const StageArgs<Real>& A, const Grid& g, const Detect& D, const Real* d2x,
+                      const Real* d2y, int off) {
+      int d = -1;
+      flag = mood_update_item<Real>(A, g, D, Wd, d2x, d2y, stamp + off, cur, gc - off,
+                                    (int)(t % 5), d);
+      if (flag) {
+        // only this item updates cell d in this iteration: its radius and
+        // its next stamp are written by no one else
+        A.ord[d] = (uint8_t)C.next[A.ord[d]];
+        next_stamp[off + d] = cur + 1;
+      }
+      dg = d >= 0 ? off + d : -1;
+    });
+    queue_push(flag, dg, next_queue, next_count);
+  }
+}
+
+// the loop itself, for one problem or a batch (Site).  The first-pass queue
+// is lowered and marked in a prologue; then every iteration is
+//   recompute the faces whose EDP1 radius changed  | barrier
+//   re-update + re-detect, lowering and marking the troubled cells
+//   for the next iteration  | barrier
+// and every block reads the new queue length to take the same decision.
+template <class Real, class Site>
+__device__ __forceinline__ void mood_loop_body(const Site& site, const MoodArgs& M,
+                                               const DirectW<Real>& Wd, const Cascade& C,
+                                               int stage) {
   Scalars* sc = M.sc;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   // the first pass filled queue 0; queue 1 receives the first iteration's
   // troubled cells (its count is cleared here, read after two barriers)
   int n = *(volatile int*)&sc->count[0];
   const int nfirst = n;
   int slot = 0, iters = 0, total = n;
-  unsigned cur = sc->stamp_cur;
+  uint32_t cur = sc->stamp_cur + 1;  // stamp of the cells of the first queue
   const int cap = sc->ctl.max_iters;
   if (leader) sc->count[1] = 0;
-  while (n > 0) {
+  bool ok = true;
+  if (n > 0) {
+    uint32_t* st = stamp_of(M, cur);
+    for (long long q = mood_lane(); q < n; q += stride) {
+      const int gc = M.queue[0][q];
+      site.with(gc, [&](const StageArgs<Real>& A, const Grid&, const Detect&, const Real*,
+                        const Real*, int off) {
+        A.ord[gc - off] = (uint8_t)C.next[A.ord[gc - off]];
+      });
+      st[gc] = cur;
+    }
+    ok = grid_barrier(sc);
+  }
+  while (ok && n > 0) {
     if (iters >= cap) {
       if (leader) atomicOr(&sc->err, kErrCap);
       break;
     }
-    cur += 1;  // stamp of the cells of this iteration's queue
     const int* queue = M.queue[slot];
-    for (long long q = gtid; q < n; q += stride) {
-      const int c = queue[q];
-      A.ord[c] = (uint8_t)C.next[A.ord[c]];
-      M.stamp[c] = cur;
-    }
+    mood_faces_phase<Real>(site, M, Wd, C, cur, queue, n);
     if (!grid_barrier(sc)) break;
-    mood_faces_lanes<Real>(A, g, Wd, C, M.stamp, cur, queue, n, gtid, stride);
-    if (!grid_barrier(sc)) break;
-    int* next_queue = M.queue[slot ^ 1];
     int* next_count = &sc->count[slot ^ 1];
-    for (long long t = gtid; t < 5LL * n; t += stride) {
-      int d = -1;
-      const bool flag = mood_update_item<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, M.stamp, cur,
-                                               queue[t / 5], (int)(t % 5), d);
-      queue_push(flag, d, next_queue, next_count);
-    }
+    mood_update_phase<Real>(site, M, Wd, C, cur, queue, n, M.queue[slot ^ 1], next_count);
     if (!grid_barrier(sc)) break;
     n = *(volatile int*)next_count;
     // the queue just worked on receives the next iteration's cells
@@ -1341,15 +1749,29 @@ __global__ void __launch_bounds__(256) k_mood_loop(StageArgs<Real> A, MoodArgs M
     total += n;
     iters += 1;
     slot ^= 1;
+    cur += 1;
   }
   if (leader) {
     sc->nbad_first[stage] = nfirst;
     sc->nbad_total[stage] = total;
     sc->iters[stage] = iters;
-    sc->stamp_cur = cur;
-    sc->slot = slot;
+    sc->stamp_cur = cur;  // every value up to cur has been used
+    sc->slot = 0;
     sc->go = 0;
+    // both queues empty for the next stage, also after a failed loop
+    sc->count[0] = 0;
+    sc->count[1] = 0;
   }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(256) k_mood_loop(StageArgs<Real> A, MoodArgs M, Grid g,
+                                                   Detect D,
+                                                   const __grid_constant__ DirectW<Real> Wd,
+                                                   Cascade C, int stage) {
+  pdl_wait();
+  const SingleSite<Real> site{A, g, D, Wd.d2x, Wd.d2y};
+  mood_loop_body<Real>(site, M, Wd, C, stage);
 }
 
 // ---------------------------------------------------------------------------
@@ -1477,6 +1899,31 @@ __global__ void __launch_bounds__(32 * FW) k_faces_batch(StageArgs<Real> B, cons
   faces_block<R, Real, DIR, FW>(sa, sp.g, W, sw[1], sw[2], tile);
 }
 
+// the fused x+y face kernel over (problem, segment, band) work items
+template <int R, class Real>
+__global__ void __launch_bounds__(32 * kXYRows, 2) k_faces_xy_batch(
+    StageArgs<Real> B, const Prob* probs, const Scalars* psc, const Item* items,
+    const __grid_constant__ ParityW<Real> W) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char xy_smem[];
+  XYShared<R, Real>& S = *reinterpret_cast<XYShared<R, Real>*>(xy_smem);
+  __shared__ Prob sp;
+  __shared__ StageArgs<Real> sa;
+  __shared__ int sw[3];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const Item w = items[blockIdx.x];
+    sp = probs[w.p];
+    sa = problem_args<Real>(B, sp, psc, w.p);
+    sw[0] = psc[w.p].dt == 0.0;  // finished problem
+    sw[1] = w.a;
+    sw[2] = w.b;
+  }
+  __syncthreads();
+  if (sw[0]) return;  // uniform over the block
+  faces_xy_block<R, Real>(sa, sp.g, W, sw[1], sw[2], S);
+}
+
 template <class Real>
 __global__ void __launch_bounds__(256) k_update_batch(StageArgs<Real> B, const Prob* probs,
                                                       const Scalars* psc, const Item* items,
@@ -1522,55 +1969,31 @@ __device__ __forceinline__ int problem_of(const Prob* probs, int nprob, int gc) 
   return lo;
 }
 
+// problem of a pooled cell index gc in a batch (problems sorted by their
+// first cell)
 template <class Real>
-__global__ void __launch_bounds__(128) k_mood_faces_batch(StageArgs<Real> B, MoodArgs M,
-                                                          const Prob* probs, const Scalars* psc,
-                                                          int nprob,
-                                                          const __grid_constant__ DirectW<Real> Wd,
-                                                          Cascade C) {
-  const int slot = M.sc->slot;
-  const int n = M.sc->count[slot];
-  const int* queue = M.queue[slot];
-  const uint32_t cur = M.sc->stamp_cur;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < 4LL * n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int gc = queue[t >> 2];
+struct BatchSite {
+  const StageArgs<Real>& B;
+  const Prob* probs;
+  const Scalars* psc;
+  int nprob;
+  template <class F>
+  __device__ __forceinline__ void with(int gc, F&& f) const {
     const int p = problem_of(probs, nprob, gc);
     const Prob& P = probs[p];
     const StageArgs<Real> A = problem_args<Real>(B, P, psc, p);
-    mood_face_item<Real>(A, P.g, Wd, C, M.stamp + P.cell_off, cur, gc - P.cell_off, (int)(t & 3));
+    f(A, P.g, P.det, d2_of<Real>(P, 0), d2_of<Real>(P, 1), P.cell_off);
   }
-}
+};
 
 template <class Real>
-__global__ void __launch_bounds__(256) k_mood_update_batch(StageArgs<Real> B, MoodArgs M,
-                                                           const Prob* probs, const Scalars* psc,
-                                                           int nprob,
-                                                           const __grid_constant__ DirectW<Real> Wd) {
-  const int slot = M.sc->slot;
-  const int n = M.sc->count[slot];
-  const int* queue = M.queue[slot];
-  int* next_queue = M.queue[slot ^ 1];
-  int* next_count = &M.sc->count[slot ^ 1];
-  const uint32_t cur = M.sc->stamp_cur;
-  const int nthreads = gridDim.x * blockDim.x;
-  const int rounds = (n + nthreads - 1) / nthreads;
-  for (int r = 0; r < rounds; ++r) {
-    const int q = r * nthreads + blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = q < n;
-    const int gc = live ? queue[q] : 0;
-    const int p = problem_of(probs, nprob, gc);
-    const Prob& P = probs[p];
-    const StageArgs<Real> A = problem_args<Real>(B, P, psc, p);
-    for (int k = 0; k < 5; ++k) {
-      int d = -1;
-      bool flag = false;
-      if (live)
-        flag = mood_update_item<Real>(A, P.g, P.det, Wd, d2_of<Real>(P, 0), d2_of<Real>(P, 1),
-                                      M.stamp + P.cell_off, cur, gc - P.cell_off, k, d);
-      queue_push(flag, d >= 0 ? P.cell_off + d : -1, next_queue, next_count);
-    }
-  }
+__global__ void __launch_bounds__(256) k_mood_loop_batch(StageArgs<Real> B, MoodArgs M,
+                                                         const Prob* probs, const Scalars* psc,
+                                                         int nprob,
+                                                         const __grid_constant__ DirectW<Real> Wd,
+                                                         Cascade C, int stage) {
+  const BatchSite<Real> site{B, probs, psc, nprob};
+  mood_loop_body<Real>(site, M, Wd, C, stage);
 }
 
 }  // namespace gpm

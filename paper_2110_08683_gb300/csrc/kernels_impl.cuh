@@ -30,24 +30,46 @@ cudaError_t Launch<Real>::faces(int top, int dir, const StageArgs<Real>& A, cons
   }
 }
 
+template <int R, class Real>
+static cudaError_t faces_xy_r(const StageArgs<Real>& A, const Grid& g, const ParityW<Real>& W,
+                              cudaStream_t st) {
+  dim3 grd((g.nx + 1 + kSegFaces - 1) / kSegFaces, (g.ny + 1 + kXYBand - 1) / kXYBand);
+  return launch_ks(k_faces_xy<R, Real>, grd, dim3(32, kXYRows), sizeof(XYShared<R, Real>), st,
+                   A, g, W);
+}
+
+template <class Real>
+cudaError_t Launch<Real>::faces_xy(int top, const StageArgs<Real>& A, const Grid& g,
+                                   const ParityW<Real>& W, cudaStream_t st) {
+  switch (top) {
+    case 0: return faces_xy_r<0, Real>(A, g, W, st);
+    case 1: return faces_xy_r<1, Real>(A, g, W, st);
+    case 2: return faces_xy_r<2, Real>(A, g, W, st);
+    default: return faces_xy_r<3, Real>(A, g, W, st);
+  }
+}
+
+template <int R, class Real>
+static cudaError_t xy_attr() {
+  return cudaFuncSetAttribute(k_faces_xy<R, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(XYShared<R, Real>));
+}
+
+template <class Real>
+cudaError_t Launch<Real>::prepare() {
+  cudaError_t e = xy_attr<0, Real>();
+  if (e == cudaSuccess) e = xy_attr<1, Real>();
+  if (e == cudaSuccess) e = xy_attr<2, Real>();
+  if (e == cudaSuccess) e = xy_attr<3, Real>();
+  return e;
+}
+
 template <class Real>
 cudaError_t Launch<Real>::update_first(const StageArgs<Real>& A, const Grid& g, const Detect& D,
                                        const DirectW<Real>& Wd, cudaStream_t st) {
   dim3 blk(32, 8);
   dim3 grd((g.nx + 31) / 32, (g.ny + 7) / 8);
   return launch_k(k_update_first<Real>, grd, blk, st, A, g, D, Wd);
-}
-
-template <class Real>
-cudaError_t Launch<Real>::mood_faces(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
-                                     const DirectW<Real>& Wd, const Cascade& C, cudaStream_t st) {
-  return launch_k(k_mood_faces<Real>, dim3(2 * kMoodBlocks), dim3(128), st, A, M, g, Wd, C);
-}
-
-template <class Real>
-cudaError_t Launch<Real>::mood_update(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
-                                      const Detect& D, const DirectW<Real>& Wd, cudaStream_t st) {
-  return launch_k(k_mood_update<Real>, dim3(kMoodBlocks), dim3(256), st, A, M, g, D, Wd);
 }
 
 template <class Real>
@@ -116,6 +138,43 @@ cudaError_t LaunchB<Real>::faces(int top, int dir, int fw, const StageArgs<Real>
 }
 
 template <int R, class Real>
+static cudaError_t faces_xy_batch_r(const StageArgs<Real>& B, const Prob* probs,
+                                    const Scalars* psc, const Item* items, int nitems,
+                                    const ParityW<Real>& W, cudaStream_t st) {
+  return launch_ks(k_faces_xy_batch<R, Real>, dim3(nitems), dim3(32, kXYRows),
+                   sizeof(XYShared<R, Real>), st, B, probs, psc, items, W);
+}
+
+template <class Real>
+cudaError_t LaunchB<Real>::faces_xy(int top, const StageArgs<Real>& B, const Prob* probs,
+                                    const Scalars* psc, const Item* items, int nitems,
+                                    const ParityW<Real>& W, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  switch (top) {
+    case 0: return faces_xy_batch_r<0, Real>(B, probs, psc, items, nitems, W, st);
+    case 1: return faces_xy_batch_r<1, Real>(B, probs, psc, items, nitems, W, st);
+    case 2: return faces_xy_batch_r<2, Real>(B, probs, psc, items, nitems, W, st);
+    default: return faces_xy_batch_r<3, Real>(B, probs, psc, items, nitems, W, st);
+  }
+}
+
+template <int R, class Real>
+static cudaError_t xy_batch_attr() {
+  return cudaFuncSetAttribute(k_faces_xy_batch<R, Real>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(XYShared<R, Real>));
+}
+
+template <class Real>
+cudaError_t LaunchB<Real>::prepare() {
+  cudaError_t e = xy_batch_attr<0, Real>();
+  if (e == cudaSuccess) e = xy_batch_attr<1, Real>();
+  if (e == cudaSuccess) e = xy_batch_attr<2, Real>();
+  if (e == cudaSuccess) e = xy_batch_attr<3, Real>();
+  return e;
+}
+
+template <int R, class Real>
 static int occ_r(int dir, int fw) {
   int n = 0;
   if (fw == 4) {
@@ -148,20 +207,33 @@ cudaError_t LaunchB<Real>::update(const StageArgs<Real>& B, const Prob* probs, c
 }
 
 template <class Real>
-cudaError_t LaunchB<Real>::mood_faces(const StageArgs<Real>& B, const MoodArgs& M,
-                                      const Prob* probs, const Scalars* psc, int nprob,
-                                      const DirectW<Real>& Wd, const Cascade& C,
-                                      cudaStream_t st) {
-  k_mood_faces_batch<Real><<<2 * kMoodBlocks, 128, 0, st>>>(B, M, probs, psc, nprob, Wd, C);
-  return cudaGetLastError();
+cudaError_t LaunchB<Real>::mood_loop(const StageArgs<Real>& B, const MoodArgs& M,
+                                     const Prob* probs, const Scalars* psc, int nprob,
+                                     const DirectW<Real>& Wd, const Cascade& C, int stage,
+                                     int blocks, int coop, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = coop ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_mood_loop_batch<Real>, B, M, probs, psc, nprob, Wd, C, stage);
 }
 
 template <class Real>
-cudaError_t LaunchB<Real>::mood_update(const StageArgs<Real>& B, const MoodArgs& M,
-                                       const Prob* probs, const Scalars* psc, int nprob,
-                                       const DirectW<Real>& Wd, cudaStream_t st) {
-  k_mood_update_batch<Real><<<kMoodBlocks, 256, 0, st>>>(B, M, probs, psc, nprob, Wd);
-  return cudaGetLastError();
+int LaunchB<Real>::mood_loop_blocks() {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mood_loop_batch<Real>, 256, 0) !=
+          cudaSuccess || sms <= 0 || occ <= 0) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * (occ < 2 ? occ : 2);
 }
 
 template <class Real>
@@ -206,6 +278,24 @@ cudaError_t LaunchA<Real>::adj_faces(const double* X, void* Xr, const double* v,
     case 2: return adj_faces_r<2, Real>(XR, v, ord, g, W, Wd, Ax, Ay, st);
     default: return adj_faces_r<3, Real>(XR, v, ord, g, W, Wd, Ax, Ay, st);
   }
+}
+
+template <class Real>
+cudaError_t LaunchA<Real>::adj_faces_stored(const void* st, const double* v, const uint8_t* ord,
+                                            const Grid& g, const ParityW<Real>& W,
+                                            const DirectW<Real>& Wd, const AdjFaces& Ax,
+                                            const AdjFaces& Ay, cudaStream_t s) {
+  const int qt = rule_q(Wd.top);
+  const Real* t = (const Real*)st;
+  const Real* xL = t;
+  const Real* xR = t + 4LL * qt * Ax.nf;
+  const Real* yL = t + 8LL * qt * Ax.nf;
+  const Real* yR = yL + 4LL * qt * Ay.nf;
+  k_adj_faces_stored<Real, 0><<<(int)((Ax.nf + 127) / 128), 128, 0, s>>>(xL, xR, qt, v, ord, g,
+                                                                         W, Wd, Ax);
+  k_adj_faces_stored<Real, 1><<<(int)((Ay.nf + 127) / 128), 128, 0, s>>>(yL, yR, qt, v, ord, g,
+                                                                         W, Wd, Ay);
+  return cudaGetLastError();
 }
 
 template <class Real>

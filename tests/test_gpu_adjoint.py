@@ -110,15 +110,19 @@ def test_fp32_adjoint_close_to_fp64():
     assert rel <= 1e-4, rel
 
 
-def test_resident_tapes_and_recomputed_segments_agree():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_resident_tapes_and_recomputed_segments_agree(precision):
     """The forward that records every step's tape runs the same kernels as
     the plain step, and the reverse pass over resident tapes equals the one
-    that steps the segments again from checkpoints, bit for bit (quadrant
-    problem: MOOD lowers radii, so the frozen masks are not uniform)."""
+    that steps the segments again from checkpoints, bit for bit, whether the
+    re-recorded segments keep their face states (the adjoint then reads
+    them) or not (the adjoint reconstructs them): quadrant problem, MOOD
+    lowers radii, so the frozen masks are not uniform and the MOOD loop's
+    recomputed faces reach the state tape too."""
     from paper_2110_08683_gb300.autograd import rollout
 
     p = I.quadrants(n=40, ny=36, R=3, seed=2)
-    g = gp.GPMood(p)
+    g = gp.GPMood(p, precision)
     U0 = torch.tensor(p["U0"], device="cuda")
     nsteps = 7
     g.set_state(p["U0"])
@@ -128,14 +132,15 @@ def test_resident_tapes_and_recomputed_segments_agree():
     rng = np.random.default_rng(4)
     W = torch.tensor(rng.standard_normal(p["U0"].shape), device="cuda")
     outs, grads = [], []
-    for every, budget in ((None, None), (3, None), (None, 1)):
+    for every, budget, states in ((None, None, True), (3, None, True), (3, None, False),
+                                  (None, 1, True)):
         U0r = U0.clone().requires_grad_()
-        UN = rollout(U0r, g, nsteps, every=every, budget=budget)
+        UN = rollout(U0r, g, nsteps, every=every, budget=budget, states=states)
         (UN * W).sum().backward()
         outs.append(UN.detach().clone())
         grads.append(U0r.grad.clone())
     assert torch.equal(outs[0], plain)
-    for k in (1, 2):
+    for k in (1, 2, 3):
         assert torch.equal(outs[k], outs[0])
         assert torch.equal(grads[k], grads[0])
     assert torch.isfinite(grads[0]).all()

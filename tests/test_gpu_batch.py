@@ -48,8 +48,12 @@ def test_batch_matches_single_handles(precision):
         _, _, ss = s.flags(maps=False)
         assert abs(t[k] - ss["t"]) <= (1e-14 if precision == "fp64" else 1e-6) * ss["t"]
     assert sum(st["nbad_first"]) > 0  # the MOOD loop ran inside the batch
+    # the autotuner's choices: the fused x+y face kernel (warps [0, 0]) or one
+    # sweep per direction with 4 or 8 warps, and the update and MOOD grids
     w, nb = b.tuning()
-    assert all(x in (4, 8) for x in w) and all(x > 0 for x in nb)
+    assert (w == [0, 0] or all(x in (4, 8) for x in w)) and all(x > 0 for x in nb)
+    up, mood = b.grids()
+    assert up > 0 and mood > 0
 
 
 def test_batch_first_step_against_oracle():

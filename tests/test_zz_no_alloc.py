@@ -51,8 +51,9 @@ def test_noalloc_step_matches_handle_step_twice(precision):
 
 
 def test_noalloc_fp32_grid_near_the_scratch_limit():
-    """256 x 256 at R = 3 in FP32 fills 98% of the scratch (three states,
-    their float shadows, fluxes, maps and queues)."""
+    """256 x 256 at R = 3 in FP32, the largest square grid that fits, fills
+    99.7% of the scratch (three states, their float shadows, fluxes, maps,
+    stamps and queues)."""
     two_steps_both_ways(I.quadrants(n=256, R=3, seed=3), "fp32")
 
 
