@@ -122,12 +122,12 @@ def algorithmic_flops_per_face(R=3):
 
 
 def ncu_traffic(precision, kind, scheme="GP-R3"):
-    """DRAM bytes per launch of the x-face kernel on this workload from the
+    """DRAM bytes per launch of the first-pass face kernel on this workload from the
     committed ncu summary, or None when the kernel sources changed since the
     capture.  Rows are keyed by workload and precision ("dmr fp64"), with the
     scheme appended for the third-order schemes ("vortex fp64 POL-MOOD3")."""
     key = f"{kind} {precision}" + ("" if scheme == "GP-R3" else f" {scheme}")
-    path = os.path.join(ROOT, "profiles", "faces_x_traffic.md")
+    path = os.path.join(ROOT, "profiles", "faces_xy_traffic.md")
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -378,10 +378,15 @@ def measure(kind, nx, ny, precision, scheme, steps, warmup, world, local, eager=
     # between them), each bracketed by events, an L2 flush between steps
     launches0 = g.launch_count()
     st0 = g.flags(maps=False)[2]
+    # the state the timed region starts from: the profiled pass replays the
+    # same steps, so its per-class shares describe the timed steps
+    U_start = torch.empty((4, ny, nx), dtype=torch.float64, device="cuda")
+    g.get_state(U_start)
     barrier(world)
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
+    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx-include "timed/" sees these steps
     with torch.cuda.stream(stream):
         for k in range(steps):
             flush.zero_()
@@ -390,6 +395,7 @@ def measure(kind, nx, ny, precision, scheme, steps, warmup, world, local, eager=
             e1[k].record(stream)
     g.sync()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier(world)
     if sampler:
         sampler.stop()
@@ -398,18 +404,23 @@ def measure(kind, nx, ny, precision, scheme, steps, warmup, world, local, eager=
     ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
     value, ms_max = job_rate(nx * ny * steps, ms, world)
 
-    # second timed pass for the per-class shares and the dominant kernel's
-    # duration: the profiled step graphs carry event nodes around every
-    # kernel class (read back after each step).  Captured on first use, so a
-    # few steps run before the counters are reset.
+    # second timed pass over the same steps for the per-class shares and the
+    # dominant kernel's duration: the profiled step graphs carry event nodes
+    # around every kernel class (read back after each step).  Captured on
+    # first use, so a few steps run before the state is set back and the
+    # counters are reset.
     prof = profile and not eager  # per-kernel events exist in the graph mode only
     kt, prof_step_ms, fr = {}, None, []
     if prof:
         g.profile(True)
+        g.set_state(U_start)
+        g.set_time(st0["t"])
         with torch.cuda.stream(stream):
             for _ in range(3):
                 g.step()
         torch.cuda.synchronize()
+        g.set_state(U_start)
+        g.set_time(st0["t"])
         g.profile(True)
         q0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         q1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]

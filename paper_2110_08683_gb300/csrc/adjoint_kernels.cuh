@@ -20,9 +20,27 @@
 
 namespace gpm {
 
+// inverse square root by Newton-Raphson from the hardware approximation:
+// each step y <- y (3/2 - (z/2) y^2) squares the relative error.  FP64:
+// rsqrt.approx.ftz.f64 and two steps; FP32: rsqrt.approx.ftz.f32 and one.
+__device__ __forceinline__ double rsqrt_nr(double z) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(z));
+  const double h = 0.5 * z;
+  y = y * fma(-h * y, y, 1.5);
+  return y * fma(-h * y, y, 1.5);
+}
+__device__ __forceinline__ float rsqrt_nr(float z) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(z));
+  return y * fmaf(-0.5f * z * y, y, 1.5f);
+}
+
 // reverse mode of hllc_x: given the adjoint Fb of the flux, accumulate the
 // adjoints of the two states into UbL / UbR.  The forward expressions are
-// those of hllc_x; only the branch the forward took is differentiated.
+// those of hllc_x (the same algebra; the sound speed as z / sqrt(z), whose
+// derivative 1 / (2 sqrt(z)) comes with it); only the branch the forward
+// took is differentiated.
 template <class Real>
 __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real gam,
                                            const Real* Fb, Real* UbL, Real* UbR) {
@@ -35,7 +53,8 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
   const Real pL = gm1 * (UL[3] - Real(0.5) * (UL[1] * uL + UL[2] * vL));
   const Real pR = gm1 * (UR[3] - Real(0.5) * (UR[1] * uR + UR[2] * vR));
   const Real zL = gam * pL * irL, zR = gam * pR * irR;
-  const Real cL = sqrt_r(zL), cR = sqrt_r(zR);
+  const Real yL = rsqrt_nr(zL), yR = rsqrt_nr(zR);  // 1 / c
+  const Real cL = zL * yL, cR = zR * yR;
   const Real aL = uL - cL, bL = uR - cR;
   const bool selA = aL < bL;
   const Real SL = selA ? aL : bL;
@@ -61,16 +80,18 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
 #pragma unroll
     for (int k = 0; k < 4; ++k) FRb[k] = Fb[k];
   } else {
-    // star state of side K
+    // star state of side K (hllc_x's second form: m = rho_K d_K,
+    // D = 1 / (S_K - S*), rho* = m D, (rho E)* = D (d_K E_K + (S* - u_K) A),
+    // A = m S* + p_K)
     const Real rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR;
     const Real EK = left ? UL[3] : UR[3], pK = left ? pL : pR, SK = left ? SL : SR;
-    const Real irK = left ? irL : irR, dK = left ? dL : dR;
+    const Real dK = left ? dL : dR;
     const Real iD = recip(SK - Ss);
-    const Real idK = recip(dK);
-    const Real fK = rK * dK * iD;
-    const Real t1 = Ss - uK, t2 = Ss + pK * irK * idK;
-    const Real eK = EK * irK + t1 * t2;
-    const Real UKs[4] = {fK, fK * Ss, fK * vK, fK * eK};
+    const Real m = rK * dK;
+    const Real fK = m * iD;
+    const Real t1 = Ss - uK, Aq = m * Ss + pK;
+    const Real Cq = dK * EK + t1 * Aq;
+    const Real UKs[4] = {fK, fK * Ss, fK * vK, iD * Cq};
     const Real* UK = left ? UL : UR;
     // Fs[v] = FK[v] + SK (UKs[v] - UK[v])
     Real FKb[4], UKsb[4], SKb = 0, UKb[4];
@@ -81,38 +102,40 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
       UKsb[k] = SK * Fb[k];
       UKb[k] = -SK * Fb[k];
     }
-    // UKs = fK (1, Ss, vK, eK)
-    Real fKb = UKsb[0] + UKsb[1] * Ss + UKsb[2] * vK + UKsb[3] * eK;
+    // UKs = (fK, fK Ss, fK vK, iD Cq), fK = m iD
+    Real fKb = UKsb[0] + UKsb[1] * Ss + UKsb[2] * vK;
     Ssb += UKsb[1] * fK;
     Real vKb = UKsb[2] * fK;
-    Real eKb = UKsb[3] * fK;
-    // eK = EK irK + t1 t2, t1 = Ss - uK, t2 = Ss + pK irK / dK
-    Real EKb = eKb * irK;
-    Real irKb = eKb * EK;
-    const Real t1b = eKb * t2, t2b = eKb * t1;
-    Ssb += t1b + t2b;
-    Real uKb = -t1b;
-    Real pKb = t2b * irK * idK;
-    irKb += t2b * pK * idK;
-    Real dKb = -t2b * pK * irK * idK * idK;
-    // fK = rK dK / D, D = SK - Ss
-    Real rKb = fKb * dK * iD;
-    dKb += fKb * rK * iD;
-    const Real Db = -fKb * fK * iD;
+    const Real Cb = UKsb[3] * iD;
+    Real iDb = UKsb[3] * Cq + fKb * m;
+    // Cq = dK EK + t1 Aq, t1 = Ss - uK, Aq = m Ss + pK
+    Real dKb = Cb * EK;
+    Real EKb = Cb * dK;
+    const Real Ab = Cb * t1;
+    Ssb += Cb * Aq;
+    Real uKb = -Cb * Aq;
+    Real pKb = Ab;
+    const Real mb = Ab * Ss + fKb * iD;
+    Ssb += Ab * m;
+    // m = rK dK
+    Real rKb = mb * dK;
+    dKb += mb * rK;
+    // iD = 1 / D, D = SK - Ss
+    const Real Db = -iDb * iD * iD;
     SKb += Db;
     Ssb -= Db;
     if (left) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) FLb[k] += FKb[k];
       rLb += rKb; uLb += uKb; vLb += vKb; ELb += EKb; pLb += pKb; SLb += SKb;
-      irLb += irKb; dLb += dKb;
+      dLb += dKb;
 #pragma unroll
       for (int k = 0; k < 4; ++k) UbL[k] += UKb[k];
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) FRb[k] += FKb[k];
       rRb += rKb; uRb += uKb; vRb += vKb; ERb += EKb; pRb += pKb; SRb += SKb;
-      irRb += irKb; dRb += dKb;
+      dRb += dKb;
 #pragma unroll
       for (int k = 0; k < 4; ++k) UbR[k] += UKb[k];
     }
@@ -144,8 +167,8 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
   vRb += FRb[2] * rR * uR;
   pRb += FRb[1] + FRb[3] * uR;
   ERb += FRb[3] * uR;
-  // c = sqrt(gam p ir)
-  const Real zLb = cLb * Real(0.5) * recip(cL), zRb = cRb * Real(0.5) * recip(cR);
+  // c = sqrt(z), z = gam p ir: dc/dz = 1 / (2 c) = y / 2
+  const Real zLb = cLb * Real(0.5) * yL, zRb = cRb * Real(0.5) * yR;
   if (cLb != Real(0)) { pLb += zLb * gam * irL; irLb += zLb * gam * pL; }
   if (cRb != Real(0)) { pRb += zRb * gam * irR; irRb += zRb * gam * pR; }
   // p = gm1 (E - 0.5 (m_x u + m_y v))

@@ -20,6 +20,11 @@ __global__ void k_dt_reduce(const double* X, const float* Xf, Grid g, Scalars* s
   pdl_wait();
   pdl_trigger();
   if (sc->ctl.fixed_dt > 0.0) return;
+  if (sc->rate_ready) {
+    // the previous step's last MOOD loop kernel reduced the rate already
+    if (blockIdx.x == 0 && threadIdx.x == 0 && sc->rate_bad) atomicOr(&sc->err, kErrDt);
+    return;
+  }
   double best = 0.0;
   bool bad = false;
   const long long n = (long long)g.nx * g.ny;
@@ -61,6 +66,8 @@ __global__ void k_dt_finalize(Scalars* sc) {
   if (!(dt > 0.0) || !isfinite(dt)) sc->err |= kErrDt;
   sc->dt = dt;
   sc->rate_bits = 0ull;  // +0 for the next step
+  sc->rate_ready = 0;
+  sc->rate_bad = 0;
   for (int s = 0; s < 5; ++s) {
     sc->iters[s] = 0;
     sc->nbad_first[s] = 0;

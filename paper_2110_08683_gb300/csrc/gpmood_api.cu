@@ -305,10 +305,11 @@ int push_control_if_changed(gpmood_t h) {
   return push_control(h);
 }
 
-// kernels launched by one step: the gate of a gated graph (1), dt (2), per
-// stage fill, faces x (and y in 2D), update, the MOOD loop, finish (1)
+// kernels launched by one step: the gate of a gated graph (1), dt (2), the
+// ghost fill of the first stage's input (1), per stage the face kernels, the
+// update and the MOOD loop (which fills the next stage's ghosts), finish (1)
 int step_base_launches(int nstages, int face_kernels, int gated) {
-  return (gated ? 1 : 0) + 2 + nstages * (3 + face_kernels) + 1;
+  return (gated ? 1 : 0) + 2 + 1 + nstages * (2 + face_kernels) + 1;
 }
 // first-pass face kernels a stage: 1 (fused, or 1D), 2 (split 2D)
 int face_kernels(const gpmood_t h) { return (h->g.dim == 2 && h->split_faces) ? 2 : 1; }
@@ -348,7 +349,8 @@ cudaError_t faces_both(gpmood_t h, const StageArgs<Real>& A, const ParityW<Real>
 template <class Real>
 int first_pass(gpmood_t h, const StageArgs<Real>& A, int ix, int s, const ParityW<Real>& P,
                const DirectW<Real>& D, cudaStream_t st) {
-  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
+  // the later stages' inputs were filled by the previous stage's loop kernel
+  if (s == 0) CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
   CK(faces_both<Real>(h, A, P, st));
   CK(Launch<Real>::update_first(A, h->g, h->det, D, st));
   return 0;
@@ -361,14 +363,29 @@ template <class Real>
 int mood_loop(gpmood_t h, const StageArgs<Real>& A, int s, const DirectW<Real>& D,
               cudaStream_t st) {
   const MoodArgs M = mood_args<Real>(h);
-  cudaError_t e =
-      Launch<Real>::mood_loop(A, M, h->g, h->det, D, h->cas, s, h->mood_blocks, h->coop, st);
+  // the loop kernel's tail: the ghost cells of the next stage's input (this
+  // stage's output), or after the last stage the CFL rate of the new state
+  LoopTail T;
+  memset(&T, 0, sizeof(T));
+  float* shadow = nullptr;  // the output's float shadow (FP32 path)
+  if constexpr (sizeof(Real) == sizeof(float)) shadow = A.outr;
+  if (s + 1 < h->sch.nstages) {
+    T.X = A.out;
+    T.Xf = shadow;
+    T.tfrac = h->sch.st[s + 1].tfrac;
+  } else {
+    T.rate = 1;
+    T.Xrate = A.out;
+    T.Xfrate = shadow;
+  }
+  cudaError_t e = Launch<Real>::mood_loop(A, M, h->g, h->det, D, h->cas, s, T, h->mood_blocks,
+                                          h->coop, st);
   if (e != cudaSuccess && h->coop) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       cudaGetLastError();
       h->coop = 0;
-      e = Launch<Real>::mood_loop(A, M, h->g, h->det, D, h->cas, s, h->mood_blocks, 0, st);
+      e = Launch<Real>::mood_loop(A, M, h->g, h->det, D, h->cas, s, T, h->mood_blocks, 0, st);
     }
   }
   CK(e);
@@ -454,8 +471,9 @@ int capture_stage(gpmood_t h, int s, int rot, const ParityW<Real>& P, const Dire
     k_tape_state<<<152 * 4, 256, 0, st>>>(h->U[ix], h->g, h->sc, s);
     CK(cudaGetLastError());
   }
+  // the later stages' inputs were filled by the previous stage's loop kernel
   rec_event(h, prof, GPMOOD_K_GHOST, 1, st);
-  CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
+  if (s == 0) CK(launch_fill(h->U[ix], h->Uf[ix], h->g, h->sc, h->sch.st[s].tfrac, st));
   rec_event(h, prof, GPMOOD_K_GHOST, 0, st);
   if (h->g.dim == 2 && !h->split_faces) {
     // both directions in one kernel, timed as the x-face class
@@ -615,7 +633,7 @@ int graph_step(gpmood_t h, double cfl, double fixed_dt, int clip, double t_end,
     }
     const int S = h->sch.nstages;
     h->prof_n[GPMOOD_K_DT] += 2;
-    h->prof_n[GPMOOD_K_GHOST] += S;
+    h->prof_n[GPMOOD_K_GHOST] += 1;
     h->prof_n[GPMOOD_K_FACES_X] += S;
     h->prof_n[GPMOOD_K_FACES_Y] += (h->g.dim == 2 && h->split_faces) ? S : 0;
     h->prof_n[GPMOOD_K_UPDATE] += S;

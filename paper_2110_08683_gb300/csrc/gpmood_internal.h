@@ -72,6 +72,22 @@ struct Scalars {
   int nactive;                  // batches: problems still advancing in this step
   unsigned int bar_count;       // grid barrier of the MOOD loop kernel: arrivals
   unsigned int bar_gen;         // and generation (count returns to 0 after each use)
+  int rate_ready;               // rate_bits holds the CFL rate of the current state
+  int rate_bad;                 // and that state had a cell with no admissible rate
+};
+
+// work the MOOD loop kernel of a stage does once its loop has ended, while its
+// grid is resident: fill the ghost cells of the stage's output, which the
+// next stage reads (X, and its float shadow Xf on the FP32 path, at time
+// t + tfrac dt), and, after the last stage, reduce the CFL rate of the new
+// state for the next step's time step
+struct LoopTail {
+  double* X;     // null: no ghost fill
+  float* Xf;
+  double tfrac;
+  int rate;      // 1: the rate of X_rate (and its shadow) into Scalars::rate_bits
+  const double* Xrate;
+  const float* Xfrate;
 };
 
 constexpr int kErrDt = 1;       // non-finite or non-positive time step

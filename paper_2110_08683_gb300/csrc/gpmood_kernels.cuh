@@ -241,13 +241,18 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   bool left = Ss >= Real(0);
   Real FL[4] = {mL, fma(mL, uL, pL), mul_rn(mL, vL), mul_rn(uL, UL[3] + pL)};
   Real FR[4] = {mR, fma(mR, uR, pR), mul_rn(mR, vR), mul_rn(uR, UR[3] + pR)};
-  // star state on side K of the contact
+  // star state on side K of the contact: with m = rho_K (S_K - u_K) and
+  // D = 1 / (S_K - S*), rho* = m D and
+  //   (rho E)* = rho* (E_K/rho_K + (S* - u_K)(S* + p_K / m))
+  //            = D ((S_K - u_K) E_K + (S* - u_K)(m S* + p_K)),
+  // the second form needing no reciprocal of rho_K (S_K - u_K)
   Real rK = left ? rL : rR, uK = left ? uL : uR, vK = left ? vL : vR;
   Real EK = left ? UL[3] : UR[3], pK = left ? pL : pR, SK = left ? SL : SR;
-  Real irK = left ? irL : irR, dK = left ? dL : dR;
-  Real fK = mul_rn(mul_rn(rK, dK), recip(SK - Ss));
-  Real eK = fma(EK, irK, mul_rn(Ss - uK, fma(mul_rn(pK, irK), recip(dK), Ss)));
-  Real UKs[4] = {fK, mul_rn(fK, Ss), mul_rn(fK, vK), mul_rn(fK, eK)};
+  Real dK = left ? dL : dR;
+  const Real m = mul_rn(rK, dK), iD = recip(SK - Ss);
+  Real fK = mul_rn(m, iD);
+  Real UKs[4] = {fK, mul_rn(fK, Ss), mul_rn(fK, vK),
+                 mul_rn(iD, fma(dK, EK, mul_rn(Ss - uK, fma(m, Ss, pK))))};
   Real Fs[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -1764,14 +1769,53 @@ __device__ __forceinline__ void mood_loop_body(const Site& site, const MoodArgs&
   }
 }
 
+// the loop's tail (LoopTail): every interior value of the stage output is
+// final once the loop has ended (the last phase ended at a grid barrier, or
+// the first pass, a previous kernel, wrote them all)
+__device__ __forceinline__ void mood_loop_tail(const Grid& g, Scalars* sc, const LoopTail& T) {
+  const long long tid = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 +
+                        (threadIdx.x & 31);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (T.X) {
+    const double t = sc->t + T.tfrac * sc->dt;
+    const long long n = ghost_count(g);
+    for (long long k = tid; k < n; k += stride) fill_ghost(T.X, T.Xf, g, t, k);
+  }
+  if (T.rate) {
+    // as k_dt_reduce, for the next step: the maximum CFL rate over the cells
+    double best = 0.0;
+    bool bad = false;
+    const long long n = (long long)g.nx * g.ny;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+      const int i = (int)(c % g.nx), j = (int)(c / g.nx);
+      double a;
+      if (!cell_rate_at(T.Xrate, T.Xfrate, g, i, j, a)) bad = true;
+      else best = a > best ? a : best;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && g.rate_floor > best) best = g.rate_floor;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      best = ob > best ? ob : best;
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+      if (bad) atomicOr(&sc->rate_bad, 1);
+      if (best > 0.0) atomicMax(&sc->rate_bits, (unsigned long long)__double_as_longlong(best));
+    }
+    // readers are later kernels: the flag can go up before every block is done
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->rate_ready = 1;
+  }
+}
+
 template <class Real>
 __global__ void __launch_bounds__(256) k_mood_loop(StageArgs<Real> A, MoodArgs M, Grid g,
                                                    Detect D,
                                                    const __grid_constant__ DirectW<Real> Wd,
-                                                   Cascade C, int stage) {
+                                                   Cascade C, int stage, LoopTail T) {
   pdl_wait();
   const SingleSite<Real> site{A, g, D, Wd.d2x, Wd.d2y};
   mood_loop_body<Real>(site, M, Wd, C, stage);
+  mood_loop_tail(g, M.sc, T);
 }
 
 // ---------------------------------------------------------------------------

@@ -51,7 +51,8 @@ struct Launch {
   // blocks (cooperative when `coop`)
   static cudaError_t mood_loop(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
                                const Detect& D, const DirectW<Real>& Wd, const Cascade& C,
-                               int stage, int blocks, int coop, cudaStream_t st);
+                               int stage, const LoopTail& T, int blocks, int coop,
+                               cudaStream_t st);
   // co-resident blocks of the MOOD loop kernel on this device (its grid)
   static int mood_loop_blocks();
 };

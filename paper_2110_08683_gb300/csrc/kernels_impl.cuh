@@ -75,7 +75,8 @@ cudaError_t Launch<Real>::update_first(const StageArgs<Real>& A, const Grid& g, 
 template <class Real>
 cudaError_t Launch<Real>::mood_loop(const StageArgs<Real>& A, const MoodArgs& M, const Grid& g,
                                     const Detect& D, const DirectW<Real>& Wd, const Cascade& C,
-                                    int stage, int blocks, int coop, cudaStream_t st) {
+                                    int stage, const LoopTail& T, int blocks, int coop,
+                                    cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(256);
@@ -87,7 +88,7 @@ cudaError_t Launch<Real>::mood_loop(const StageArgs<Real>& A, const MoodArgs& M,
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = coop ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_mood_loop<Real>, A, M, g, D, Wd, C, stage);
+  return cudaLaunchKernelEx(&cfg, k_mood_loop<Real>, A, M, g, D, Wd, C, stage, T);
 }
 
 template <class Real>

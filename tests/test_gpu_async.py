@@ -94,10 +94,11 @@ def test_failure_stops_the_queued_steps():
 
 @pytest.mark.parametrize("problem", ["vortex", "quadrants"])
 def test_launch_count_is_counted_on_the_device(problem):
-    # every step launches the gate, the two time-step kernels, four kernels a
-    # stage (ghost fill, the x and y faces in one kernel, update, the MOOD
-    # loop) and the finishing one, whether MOOD iterates (quadrants) or not
-    # (the vortex)
+    # every step launches the gate, the two time-step kernels, the ghost fill
+    # of the first stage's input, three kernels a stage (the x and y faces in
+    # one kernel, update, the MOOD loop, which fills the next stage's ghosts
+    # or reduces the next step's CFL rate) and the finishing one, whether
+    # MOOD iterates (quadrants) or not (the vortex)
     p = I.vortex(n=64, R=3) if problem == "vortex" else I.quadrants(n=64, R=3, seed=4)
     g = gp.GPMood(p)
     g.set_state(p["U0"])
@@ -105,7 +106,7 @@ def test_launch_count_is_counted_on_the_device(problem):
     for _ in range(5):
         g.step_async()
     g.sync()
-    assert g.launch_count() - n0 == 5 * (1 + 2 + 3 * 4 + 1)
+    assert g.launch_count() - n0 == 5 * (1 + 2 + 1 + 3 * 3 + 1)
     if problem == "quadrants":
         assert sum(g.flags(maps=False)[2]["iters"]) > 0
     g.close()

@@ -292,11 +292,14 @@ def test_sod_1d_run_to_t_end(precision):
     assert err < 7e-3, err  # the oracle's own error at 128 cells is 5.5e-3
     assert (Ug[0] > 0).all()
     m0 = p["U0"][0].sum() / n
-    # round-off only (no wave reaches the ends): 1e-13 relative per step in
-    # FP64; the FP32 path's reconstruction of the uniform end states rounds in
-    # float, so the outflow faces carry float-level fluxes (periodic domains,
-    # with no boundary flux, hold 1e-13 in both paths: the conservation tests)
-    per_step = 1e-13 if precision == "fp64" else 1e-12
+    # the total changes only by the fluxes through the two end faces (eq.
+    # fvm_discrete summed over the cells), and no wave reaches the ends: in
+    # FP64 those fluxes vanish to round-off, 1e-13 relative per step.  The
+    # FP32 path solves the end faces in float, so each carries a mass flux of
+    # a few float ulps of rho c: with dt / L = 0.003 that is up to 1e-9 of
+    # the mass per step (periodic domains, with no boundary flux, hold 1e-13
+    # in both paths: the conservation tests)
+    per_step = 1e-13 if precision == "fp64" else 1e-9
     assert abs(Ug[0].sum() / n - m0) <= ng * per_step * m0
 
 
