@@ -137,22 +137,24 @@ __device__ __forceinline__ Real pressure_of(const Real* U, Real gm1) {
   return gm1 * (U[3] - Real(0.5) * (U[1] * U[1] + U[2] * U[2]) * ir);
 }
 
-template <class Real>
-__device__ __forceinline__ bool finite_r(Real x) {
-  return isfinite(x);
+// finite (neither infinite nor NaN), decided on the bit pattern
+__device__ __forceinline__ bool finite_r(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffll) < 0x7ff0000000000000ll;
 }
+__device__ __forceinline__ bool finite_r(float x) { return isfinite(x); }
 
-// reciprocal by Newton-Raphson from the hardware approximation: each step
-// r <- r + r (1 - x r) squares the relative error.  FP64: rcp.approx.ftz.f64
-// and two steps; FP32: rcp.approx.ftz.f32 (within 1 ulp) and one step.  Zero
-// or non-finite x give a non-finite result.
+// reciprocal from the hardware approximation r (rcp.approx.ftz.f64, whose
+// relative error stays below 2^-20 on this GPU): with e = 1 - x r,
+// 1/x = r / (1 - e) = r (1 + e + e^2 + ...), and the series cut after e^2
+// leaves a relative error below 2^-60 before the final rounding (one FMA
+// fewer than two Newton-Raphson steps).  FP32: rcp.approx.ftz.f32 (within 1
+// ulp) and one Newton-Raphson step r + r (1 - x r).  Zero or non-finite x
+// give a non-finite result.
 __device__ __forceinline__ double recip(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ float recip(float x) {
   float r;
@@ -160,10 +162,23 @@ __device__ __forceinline__ float recip(float x) {
   return fmaf(r, fmaf(-x, r, 1.0f), r);
 }
 
-// square root of a sound-speed argument: FP64 the IEEE square root; FP32 the
+// square root of a sound-speed argument z > 0 (the Riemann solvers; outside
+// their domain the result is NaN, and so is their flux).  FP64: from the
+// hardware inverse square root y (rsqrt.approx.ftz.f64, relative error below
+// 2^-20 on this GPU), s = z y and two corrections s <- s + (y/2)(z - s^2),
+// each of which multiplies the relative error by about that of y: within
+// one unit in the last place, in six FP64 operations where the IEEE square
+// root takes the FP64 pipe about as long as seven and a half.  FP32: the
 // hardware approximation sqrt.approx.ftz.f32 (the FP32 path's reconstruction
-// and Riemann solver are FP32 arithmetic throughout)
-__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+// and Riemann solver are FP32 arithmetic throughout).
+__device__ __forceinline__ double sqrt_r(double z) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(z));
+  const double h = __dmul_rn(0.5, y);
+  double s = __dmul_rn(z, y);
+  s = fma(h, fma(-s, s, z), s);
+  return fma(h, fma(-s, s, z), s);
+}
 __device__ __forceinline__ float sqrt_r(float x) {
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -206,6 +221,50 @@ __device__ __forceinline__ bool pos_finite(float x) {
   const int b = __float_as_int(x);
   return b > 0 && b < 0x7f800000;
 }
+// comparisons of doubles on the integer pipes.  An FP64 compare, min or max
+// occupies the FP64 pipe like an FMA does (on this GPU about 64 cycles per
+// warp instruction per sub-partition), a 64-bit integer compare a few
+// cycles.  The IEEE order of doubles that are not NaN is the order of the
+// keys b ^ ((b >> 63) & 0x7fff...) of their bit patterns b, save that -0 and
+// +0 compare equal; each helper gives exactly the IEEE result for the inputs
+// its name allows.  FP32 keeps the hardware compare, which is cheap.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ bool is_nan(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
+}
+// a < b, a and b not NaN
+__device__ __forceinline__ bool lt_num(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return order_key(a) < order_key(b) && ((ia | ib) << 1) != 0;
+}
+__device__ __forceinline__ bool lt_num(float a, float b) { return a < b; }
+// a < b with NaN (false when either is NaN)
+__device__ __forceinline__ bool lt_ieee(double a, double b) {
+  return !is_nan(a) && !is_nan(b) && lt_num(a, b);
+}
+__device__ __forceinline__ bool lt_ieee(float a, float b) { return a < b; }
+// a <= b with NaN (false when either is NaN)
+__device__ __forceinline__ bool le_ieee(double a, double b) {
+  return !is_nan(a) && !is_nan(b) && !lt_num(b, a);
+}
+__device__ __forceinline__ bool le_ieee(float a, float b) { return a <= b; }
+// x >= 0 and x > 0, x not NaN
+__device__ __forceinline__ bool ge0_num(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 || b == (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool ge0_num(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool gt0_num(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool gt0_num(float x) { return x > 0.0f; }
+// a < b ? a : b and a > b ? a : b, a and b not NaN
+template <class Real>
+__device__ __forceinline__ Real min_num(Real a, Real b) { return lt_num(a, b) ? a : b; }
+template <class Real>
+__device__ __forceinline__ Real max_num(Real a, Real b) { return lt_num(b, a) ? a : b; }
+
 template <class Real>
 __device__ __forceinline__ bool solver_domain(Real rL, Real rR, Real pL, Real pR) {
   // rho > 0 and p > 0 (non-finite inputs give a NaN flux anyway)
@@ -218,7 +277,9 @@ __device__ __forceinline__ bool solver_domain(Real rL, Real rR, Real pL, Real pR
 // state is taken on the side of the contact speed S*.  Every product is an
 // explicit fma or a product rounded on its own, so the compiler cannot fuse
 // operations differently in different kernels: every kernel that solves a
-// face gets the same flux bit for bit.
+// face gets the same flux bit for bit.  Inside the solver's domain every
+// value is finite, so the comparisons run on the integer pipes (outside it
+// the flux is NaN whatever they decide).
 template <class Real>
 __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam, Real* F,
                                        Real& pL, Real& pR) {
@@ -229,18 +290,16 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   pL = pressure_ir(UL, irL, gm1, uL, vL);
   pR = pressure_ir(UR, irR, gm1, uR, vR);
   Real cL = sqrt_r(mul_rn(mul_rn(gam, pL), irL)), cR = sqrt_r(mul_rn(mul_rn(gam, pR), irR));
-  Real aL = uL - cL, bL = uR - cR;
-  Real SL = aL < bL ? aL : bL;
-  Real aR = uL + cL, bR = uR + cR;
-  Real SR = aR > bR ? aR : bR;
+  const Real SL = min_num(uL - cL, uR - cR);
+  const Real SR = max_num(uL + cL, uR + cR);
   Real dL = SL - uL, dR = SR - uR;
   const Real mL = mul_rn(rL, uL), mR = mul_rn(rR, uR);
   Real num = fma(-mR, dR, fma(mL, dL, pR - pL));
   Real den = fma(-rR, dR, mul_rn(rL, dL));
   Real Ss = mul_rn(num, recip(den));
-  bool left = Ss >= Real(0);
-  Real FL[4] = {mL, fma(mL, uL, pL), mul_rn(mL, vL), mul_rn(uL, UL[3] + pL)};
-  Real FR[4] = {mR, fma(mR, uR, pR), mul_rn(mR, vR), mul_rn(uR, UR[3] + pR)};
+  const bool left = ge0_num(Ss);
+  const bool useL = ge0_num(SL);
+  const bool useS = left || gt0_num(SR);
   // star state on side K of the contact: with m = rho_K (S_K - u_K) and
   // D = 1 / (S_K - S*), rho* = m D and
   //   (rho E)* = rho* (E_K/rho_K + (S* - u_K)(S* + p_K / m))
@@ -253,19 +312,18 @@ __device__ __forceinline__ void hllc_x(const Real* UL, const Real* UR, Real gam,
   Real fK = mul_rn(m, iD);
   Real UKs[4] = {fK, mul_rn(fK, Ss), mul_rn(fK, vK),
                  mul_rn(iD, fma(dK, EK, mul_rn(Ss - uK, fma(m, Ss, pK))))};
-  Real Fs[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    Real FK = left ? FL[v] : FR[v];
-    Real UK = left ? UL[v] : UR[v];
-    Fs[v] = fma(SK, UKs[v] - UK, FK);
-  }
-  bool useL = SL >= Real(0);
-  bool useS = left || (SR > Real(0));
+  // one physical flux is ever used: F_L when S_L >= 0, F_R when S_R <= 0,
+  // else the star flux F_K + S_K (U*_K - U_K) on side K
+  const bool sideL = useL || (useS && left);
+  const Real uX = sideL ? uL : uR, vX = sideL ? vL : vR, pX = sideL ? pL : pR;
+  const Real mX = sideL ? mL : mR, EX = sideL ? UL[3] : UR[3];
+  const Real FX[4] = {mX, fma(mX, uX, pX), mul_rn(mX, vX), mul_rn(uX, EX + pX)};
+  const bool star = !useL && useS;
   const bool dom = solver_domain(rL, rR, pL, pR);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    F[v] = useL ? FL[v] : (useS ? Fs[v] : FR[v]);
+    const Real UK = left ? UL[v] : UR[v];
+    F[v] = star ? fma(SK, UKs[v] - UK, FX[v]) : FX[v];
     if (!dom) qnan(F[v]);
   }
 }
@@ -282,16 +340,14 @@ __device__ __forceinline__ void hll_x(const Real* UL, const Real* UR, Real gam, 
   pL = pressure_ir(UL, irL, gm1, uL, vL);
   pR = pressure_ir(UR, irR, gm1, uR, vR);
   Real cL = sqrt_r(mul_rn(mul_rn(gam, pL), irL)), cR = sqrt_r(mul_rn(mul_rn(gam, pR), irR));
-  Real aL = uL - cL, bL = uR - cR;
-  Real SL = aL < bL ? aL : bL;
-  Real aR = uL + cL, bR = uR + cR;
-  Real SR = aR > bR ? aR : bR;
+  const Real SL = min_num(uL - cL, uR - cR);
+  const Real SR = max_num(uL + cL, uR + cR);
   // physical fluxes by the same rounded sequence on both sides
   const Real mL = mul_rn(rL, uL), mR = mul_rn(rR, uR);
   Real FL[4] = {mL, fma(mL, uL, pL), mul_rn(mL, vL), mul_rn(uL, UL[3] + pL)};
   Real FR[4] = {mR, fma(mR, uR, pR), mul_rn(mR, vR), mul_rn(uR, UR[3] + pR)};
   const Real iw = recip(SR - SL);
-  const bool useL = SL >= Real(0), useR = !(SR > Real(0));
+  const bool useL = ge0_num(SL), useR = !gt0_num(SR);
   const bool dom = solver_domain(rL, rR, pL, pR);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -335,8 +391,8 @@ __device__ __forceinline__ bool cell_rate(const double* S, const Grid& g, double
   const double p = (g.gamma - 1.0) * (S[3] - 0.5 * (S[1] * u + S[2] * v));
   const double cs = sqrt(g.gamma * p * ir);
   const double ax = (fabs(u) + cs) * g.inv_dx, ay = (fabs(v) + cs) * g.inv_dy;
-  rate = (g.dim == 1 || ax > ay) ? ax : ay;  // a NaN state makes both rates NaN
-  return rate > 0.0 && isfinite(rate);
+  rate = (g.dim == 1 || lt_ieee(ay, ax)) ? ax : ay;  // a NaN state makes both rates NaN
+  return pos_finite(rate);
 }
 
 // the same rate on the FP32 path: from the float shadow, in float
@@ -982,8 +1038,8 @@ __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const De
   Real Y[4] = {(Real)Yd[0], (Real)Yd[1], (Real)Yd[2], (Real)Yd[3]};
   Real rho = Y[0];
   Real p = gm1 * (Y[3] - Real(0.5) * (Y[1] * Y[1] + Y[2] * Y[2]) * recip(Y[0]));
-  if (!finite_r(rho) || !finite_r(p)) return true;   // Step 4, CAD
-  if (!(rho > Real(0)) || !(p > Real(0))) return true; // Step 5, PAD
+  if (!finite_r(rho) || !finite_r(p)) return true;    // Step 4, CAD
+  if (!gt0_num(rho) || !gt0_num(p)) return true;       // Step 5, PAD
   const bool two = g.dim == 2;  // 1D: the x terms and the W/E neighbours only
   if (D.csd_on) {                                      // Step 6, CSD
     Real rE = X(0, 1, 0), rW = X(0, -1, 0);
@@ -1004,13 +1060,13 @@ __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const De
     Real pN = pressure_ir(SN, iN, gm1, tmp, vN);
     Real pS = pressure_ir(SS, iS, gm1, tmp, vS);
     const Real hx = Real(0.5) * (Real)g.inv_dx, hy = Real(0.5) * (Real)g.inv_dy;
-    Real mx_ = pE < pW ? pE : pW, my_ = pN < pS ? pN : pS;
+    Real mx_ = lt_ieee(pE, pW) ? pE : pW, my_ = lt_ieee(pN, pS) ? pN : pS;
     Real divV = (uE - uW) * hx, gradP = fabs(pE - pW) * hx * recip(mx_);
     if (two) {
       divV += (vN - vS) * hy;
       gradP += fabs(pN - pS) * hy * recip(my_);
     }
-    if (divV >= -(Real)D.sigma_v && gradP <= (Real)D.sigma_p) return false;
+    if (le_ieee(-(Real)D.sigma_v, divV) && le_ieee(gradP, (Real)D.sigma_p)) return false;
   }
   Real r0 = X(0, 0, 0);
   Real rmin = r0, rmax = r0;
@@ -1020,11 +1076,11 @@ __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const De
   for (int m = 0; m < 4; ++m) {
     if (m >= nnb) break;
     Real r = X(0, di[m], dj[m]);
-    rmin = r < rmin ? r : rmin;
-    rmax = r > rmax ? r : rmax;
+    rmin = lt_ieee(r, rmin) ? r : rmin;
+    rmax = lt_ieee(rmax, r) ? r : rmax;
   }
-  if (rmax - rmin < (Real)D.plateau_thr) return false;  // Step 7, plateau
-  if (rmin <= rho && rho <= rmax) return false;          // Step 8, DMP
+  if (lt_ieee(rmax - rmin, (Real)D.plateau_thr)) return false;   // Step 7, plateau
+  if (le_ieee(rmin, rho) && le_ieee(rho, rmax)) return false;     // Step 8, DMP
   // Step 9, u2 with the App. B second-derivative weights (R=1 stencil in
   // the order b=-1: (0,-1); b=0: (-1,0),(0,0),(1,0); b=1: (0,1))
   const int ci[5] = {0, -1, 1, 0, 0}, cj[5] = {0, 0, 0, 1, -1};
@@ -1047,16 +1103,16 @@ __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const De
         cmin = k;
         cmax = k;
       } else {
-        cmin = k < cmin ? k : cmin;
-        cmax = k > cmax ? k : cmax;
+        cmin = lt_ieee(k, cmin) ? k : cmin;
+        cmax = lt_ieee(cmax, k) ? k : cmax;
       }
     }
-    bool same = cmin * cmax > -delta;
+    bool same = lt_ieee(-delta, cmin * cmax);
     Real acmax = fabs(cmax), acmin = fabs(cmin);
-    bool ua = same && (acmax > acmin ? acmax : acmin) < delta;
+    bool ua = same && lt_ieee(lt_ieee(acmin, acmax) ? acmax : acmin, delta);
     // |Cmin|/|Cmax| >= 1/2 written without the division; equal for every
     // non-NaN input once (a) is taken into account
-    bool ub = same && acmin >= Real(0.5) * acmax;
+    bool ub = same && le_ieee(Real(0.5) * acmax, acmin);
     if (!(ua || ub)) return true;
   }
   return false;
@@ -1790,12 +1846,12 @@ __device__ __forceinline__ void mood_loop_tail(const Grid& g, Scalars* sc, const
       const int i = (int)(c % g.nx), j = (int)(c / g.nx);
       double a;
       if (!cell_rate_at(T.Xrate, T.Xfrate, g, i, j, a)) bad = true;
-      else best = a > best ? a : best;
+      else best = max_num(a, best);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && g.rate_floor > best) best = g.rate_floor;
     for (int o = 16; o > 0; o >>= 1) {
       const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      best = ob > best ? ob : best;
+      best = max_num(ob, best);
     }
     bad = __any_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0) {
