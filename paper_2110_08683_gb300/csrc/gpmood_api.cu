@@ -819,6 +819,7 @@ int gpmood_create(const gpmood_grid* grid, double gamma, int R_max, double ell,
   h->det.csd_on = o.csd_off ? 0 : 1;
   h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
   h->det.delta = fmin(g.dx, g.dy);
+  detect_derive(h->det, g);
   h->precision = o.precision;
   h->eager = o.eager ? 1 : 0;
   h->pdl = o.serial_launch ? 0 : 1;
@@ -1473,6 +1474,7 @@ extern "C" int gpmood_step_noalloc(const gpmood_grid* grid, double gamma, int R_
   h->det.csd_on = o.csd_off ? 0 : 1;
   h->det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
   h->det.delta = fmin(g.dx, g.dy);
+  detect_derive(h->det, g);
   h->precision = o.precision;
   // a safety net only: radii never rise, so the loop ends; chains of
   // re-detected neighbours can take O(grid width) iterations

@@ -673,6 +673,7 @@ int gpmood_batch_create(const gpmood_grid* grids, int nprob, double gamma, int R
     P.det.csd_on = o.csd_off ? 0 : 1;
     P.det.plateau_thr = fmin(g.dx * g.dx * g.dx, g.dy * g.dy * g.dy);
     P.det.delta = fmin(g.dx, g.dy);
+    detect_derive(P.det, g);
     int da[25], db[25];
     double d2x[25], d2y[25];
     if (gpw_second_derivative(g.dx, g.dy, ell[p], da, db, d2x, d2y) != 5) {

@@ -125,7 +125,25 @@ struct Detect {
   int csd_on;
   double plateau_thr;   // min(dx^3, dy^3)
   double delta;         // min(dx, dy)
+  // set by detect_derive: the tests' constants in both precisions, so that
+  // no kernel converts or combines them once per cell
+  double gm1, hx, hy;   // gamma - 1, 1 / (2 dx), 1 / (2 dy)
+  float sigma_v_f, sigma_p_f, plateau_thr_f, delta_f, gm1_f, hx_f, hy_f;
 };
+
+// the derived members of D, once its own members and the grid are set
+inline void detect_derive(Detect& D, const Grid& g) {
+  D.gm1 = g.gamma - 1.0;
+  D.hx = 0.5 * g.inv_dx;
+  D.hy = 0.5 * g.inv_dy;
+  D.sigma_v_f = (float)D.sigma_v;
+  D.sigma_p_f = (float)D.sigma_p;
+  D.plateau_thr_f = (float)D.plateau_thr;
+  D.delta_f = (float)D.delta;
+  D.gm1_f = (float)(g.gamma - 1.0);
+  D.hx_f = 0.5f * (float)g.inv_dx;
+  D.hy_f = 0.5f * (float)g.inv_dy;
+}
 
 // one RK stage as buffer roles (slots relative to the step's rotation of
 // the state buffers) and the coefficients of StageArgs; w, out2 = -1: none

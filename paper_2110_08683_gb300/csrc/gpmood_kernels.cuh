@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "gpmood_internal.h"
+#include "fp_bits.h"
 
 namespace gpm {
 
@@ -1024,6 +1025,22 @@ __global__ void __launch_bounds__(32 * kXYRows, 2) k_faces_xy(StageArgs<Real> A,
 // u2_curvature, u2_a, u2_b) on the candidate Y of cell (i,j) with the ghosted
 // stage input X.  Returns true for a troubled cell.
 // ---------------------------------------------------------------------------
+// a detection constant in the precision of the tests (Detect holds both)
+template <class Real>
+__device__ __forceinline__ Real det_c(double d, float f);
+template <>
+__device__ __forceinline__ double det_c<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float det_c<float>(double, float f) { return f; }
+
+// a double in the precision of the tests: FP32 rounds it on the integer pipes
+template <class Real>
+__device__ __forceinline__ Real to_real(double x);
+template <>
+__device__ __forceinline__ double to_real<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_real<float>(double x) { return fpb_double_to_float_rn(x); }
+
 template <class Real>
 __device__ __forceinline__ Real xload(const Real* X, const Grid& g, int v, int i, int j) {
   return __ldg(X + gidx(g, v, i, j));
@@ -1034,8 +1051,9 @@ __device__ __forceinline__ Real xload(const Real* X, const Grid& g, int v, int i
 template <class Real, class LX>
 __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const Detect& D,
                                             const Real* d2x, const Real* d2y, const double* Yd) {
-  const Real gm1 = (Real)(g.gamma - 1.0);
-  Real Y[4] = {(Real)Yd[0], (Real)Yd[1], (Real)Yd[2], (Real)Yd[3]};
+  const Real gm1 = det_c<Real>(D.gm1, D.gm1_f);
+  Real Y[4] = {to_real<Real>(Yd[0]), to_real<Real>(Yd[1]), to_real<Real>(Yd[2]),
+               to_real<Real>(Yd[3])};
   Real rho = Y[0];
   Real p = gm1 * (Y[3] - Real(0.5) * (Y[1] * Y[1] + Y[2] * Y[2]) * recip(Y[0]));
   if (!finite_r(rho) || !finite_r(p)) return true;    // Step 4, CAD
@@ -1059,14 +1077,16 @@ __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const De
     Real pW = pressure_ir(SW, iW, gm1, uW, tmp);
     Real pN = pressure_ir(SN, iN, gm1, tmp, vN);
     Real pS = pressure_ir(SS, iS, gm1, tmp, vS);
-    const Real hx = Real(0.5) * (Real)g.inv_dx, hy = Real(0.5) * (Real)g.inv_dy;
+    const Real hx = det_c<Real>(D.hx, D.hx_f), hy = det_c<Real>(D.hy, D.hy_f);
     Real mx_ = lt_ieee(pE, pW) ? pE : pW, my_ = lt_ieee(pN, pS) ? pN : pS;
     Real divV = (uE - uW) * hx, gradP = fabs(pE - pW) * hx * recip(mx_);
     if (two) {
       divV += (vN - vS) * hy;
       gradP += fabs(pN - pS) * hy * recip(my_);
     }
-    if (le_ieee(-(Real)D.sigma_v, divV) && le_ieee(gradP, (Real)D.sigma_p)) return false;
+    if (le_ieee(-det_c<Real>(D.sigma_v, D.sigma_v_f), divV) &&
+        le_ieee(gradP, det_c<Real>(D.sigma_p, D.sigma_p_f)))
+      return false;
   }
   Real r0 = X(0, 0, 0);
   Real rmin = r0, rmax = r0;
@@ -1079,12 +1099,12 @@ __device__ __forceinline__ bool troubled_at(const LX& X, const Grid& g, const De
     rmin = lt_ieee(r, rmin) ? r : rmin;
     rmax = lt_ieee(rmax, r) ? r : rmax;
   }
-  if (lt_ieee(rmax - rmin, (Real)D.plateau_thr)) return false;   // Step 7, plateau
+  if (lt_ieee(rmax - rmin, det_c<Real>(D.plateau_thr, D.plateau_thr_f))) return false;  // Step 7
   if (le_ieee(rmin, rho) && le_ieee(rho, rmax)) return false;     // Step 8, DMP
   // Step 9, u2 with the App. B second-derivative weights (R=1 stencil in
   // the order b=-1: (0,-1); b=0: (-1,0),(0,0),(1,0); b=1: (0,1))
   const int ci[5] = {0, -1, 1, 0, 0}, cj[5] = {0, 0, 0, 1, -1};
-  const Real delta = (Real)D.delta;
+  const Real delta = det_c<Real>(D.delta, D.delta_f);
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
     if (d == 1 && !two) break;
@@ -1161,17 +1181,32 @@ __device__ bool troubled_prefetched(const Real* X, const Grid& g, const Detect& 
 }
 
 // candidate of eq. fvm_discrete and the SSP-RK3 combination (eq. rk3) of cell (i,j)
+// the stage's flux-difference coefficients h dt / dx and h dt / dy
+struct StageC {
+  double cx, cy;
+};
+template <class Real>
+__device__ __forceinline__ StageC stage_coeffs(const StageArgs<Real>& A, const Grid& g,
+                                               double dt) {
+  const double hdt = A.h * dt;
+  return StageC{hdt * g.inv_dx, hdt * g.inv_dy};
+}
+
+// per variable two differences and two fmas
 template <class Real>
 __device__ __forceinline__ void candidate(const StageArgs<Real>& A, const Grid& g, int i, int j,
-                                          double dt, double* Y) {
-  // h dt / dx and h dt / dy once; per variable two differences and two fmas
-  const double hdt = A.h * dt, cx = hdt * g.inv_dx, cy = hdt * g.inv_dy;
+                                          StageC k, double* Y) {
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     double fe = A.Fx[fxidx(g, v, i + 1, j)], fw = A.Fx[fxidx(g, v, i, j)];
     double gn = A.Fy[fyidx(g, v, i, j + 1)], gs = A.Fy[fyidx(g, v, i, j)];
-    Y[v] = fma(-cx, fe - fw, fma(-cy, gn - gs, A.X[gidx(g, v, i, j)]));
+    Y[v] = fma(-k.cx, fe - fw, fma(-k.cy, gn - gs, A.X[gidx(g, v, i, j)]));
   }
+}
+template <class Real>
+__device__ __forceinline__ void candidate(const StageArgs<Real>& A, const Grid& g, int i, int j,
+                                          double dt, double* Y) {
+  candidate<Real>(A, g, i, j, stage_coeffs<Real>(A, g, dt), Y);
 }
 
 template <class Real>
@@ -1184,7 +1219,7 @@ __device__ __forceinline__ void combine_store(const StageArgs<Real>& A, const Gr
     const double o = A.ca != 0.0 ? fma(A.ca, A.U0[k], A.cb * Y[v])
                                  : (A.cb == 1.0 ? Y[v] : A.cb * Y[v]);
     A.out[k] = o;
-    if constexpr (sizeof(Real) == sizeof(float)) A.outr[k] = (float)o;
+    if constexpr (sizeof(Real) == sizeof(float)) A.outr[k] = fpb_double_to_float_rn(o);
     if (A.out2) A.out2[k] = fma(A.wa, A.W[k], A.wb * Y[v]);
   }
 }
@@ -1209,15 +1244,14 @@ template <class Real>
 __device__ __forceinline__ void update_cell_w(const StageArgs<Real>& A, const Grid& g,
                                               const Detect& D, const DirectW<Real>& Wd,
                                               const Real* d2x, const Real* d2y, int i, int j,
-                                              int cell_off) {
+                                              int cell_off, StageC k) {
   const bool in = i < g.nx && j < g.ny;
   bool bad = false;
   int c = 0;
   if (in) {
     c = cidx(g, i, j);
-    const double dt = A.sc->dt;
     double Y[4];
-    candidate<Real>(A, g, i, j, dt, Y);
+    candidate<Real>(A, g, i, j, k, Y);
     const int top = Wd.top;
     if (top != 0) {
       bad = face_state_bad<Real>(A, g, i, j) || troubled<Real>(A.Xr, g, D, d2x, d2y, i, j, Y);
@@ -1238,8 +1272,13 @@ __global__ void __launch_bounds__(256) k_update_first(StageArgs<Real> A, Grid g,
                                                       const __grid_constant__ DirectW<Real> Wd) {
   pdl_wait();
   pdl_trigger();
+  // the stage coefficients once per block: FP64 work is charged per warp
+  // instruction, so a value every warp computed would cost every warp
+  __shared__ StageC k;
+  if (threadIdx.x == 0 && threadIdx.y == 0) k = stage_coeffs<Real>(A, g, A.sc->dt);
+  __syncthreads();
   update_cell_w<Real>(A, g, D, Wd, Wd.d2x, Wd.d2y, blockIdx.x * blockDim.x + threadIdx.x,
-                      blockIdx.y * blockDim.y + threadIdx.y, 0);
+                      blockIdx.y * blockDim.y + threadIdx.y, 0, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -1433,9 +1472,12 @@ __device__ __forceinline__ bool mood_face_plan(const StageArgs<Real>& A, const G
                                                int& K) {
   const int i = c % g.nx, j = c / g.nx;
   if (f >= 2 && g.dim == 1) return false;  // no y faces in 1D
+  // every load of the decision depends on c alone: all are issued before
+  // the first test, so that one memory latency covers them
+  bool other = false;  // the face is the other queued cell's
   if (f == 0 || f == 2) {
     int nb = neighbour(g, i, j, f);
-    if (nb >= 0 && stamp[nb] == cur) return false;
+    other = nb >= 0 && stamp[nb] == cur;
   }
   iL = i;
   jL = j;
@@ -1445,6 +1487,7 @@ __device__ __forceinline__ bool mood_face_plan(const StageArgs<Real>& A, const G
   int nl, bl, nr, br;
   radius_pair(g, A.ord, stamp, cur, C, iL, jL, nl, bl);
   radius_pair(g, A.ord, stamp, cur, C, iR, jR, nr, br);
+  if (other) return false;
   K = nl < nr ? nl : nr;
   const int Kold = bl < br ? bl : br;
   return K != Kold;  // else the EDP1 order of this face is unchanged
@@ -1543,25 +1586,28 @@ __device__ __forceinline__ bool mood_update_item(const StageArgs<Real>& A, const
   d = k == 0 ? c : neighbour(g, i, j, k - 1);
   if (d < 0) return false;
   const int di = d % g.nx, dj = d / g.nx;
+  // the loads of the ownership test and of the candidate depend on d alone:
+  // all are issued before the test, so that one memory latency covers them
+  bool taken = false;  // cell d is updated by another queued cell's item
   if (k > 0) {
-    if (stamp[d] == cur) {
-      d = -1;
-      return false;
-    }
+    taken = stamp[d] == cur;
     // earlier entries of d's own list: W, E, S (in that order) before c
     const int back = k == 1 ? 1 : k == 2 ? 0 : k == 3 ? 3 : 2;
-    for (int e = 0; e < back; ++e) {
+    for (int e = 0; e < 3; ++e) {
+      if (e >= back) break;
       int o = neighbour(g, di, dj, e);
-      if (o >= 0 && stamp[o] == cur) {
-        d = -1;
-        return false;
-      }
+      taken |= o >= 0 && stamp[o] == cur;
     }
   }
   double Y[4];
   candidate<Real>(A, g, di, dj, A.sc->dt, Y);
+  const int od = A.ord[d];
+  if (taken) {
+    d = -1;
+    return false;
+  }
   bool flag = false;
-  if (A.ord[d] != 0) {
+  if (od != 0) {
     flag = face_state_bad<Real>(A, g, di, dj) ||
            troubled_prefetched<Real>(A.Xr, g, D, d2x, d2y, di, dj, Y);
   } else {
@@ -2031,6 +2077,7 @@ __global__ void __launch_bounds__(256) k_update_batch(StageArgs<Real> B, const P
                                                       const __grid_constant__ DirectW<Real> Wd) {
   __shared__ Prob sp;
   __shared__ StageArgs<Real> sa;
+  __shared__ StageC sk;
   __shared__ int sw[3];
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -2042,6 +2089,7 @@ __global__ void __launch_bounds__(256) k_update_batch(StageArgs<Real> B, const P
       sw[0] = psc[w.p].dt == 0.0;
       sw[1] = w.a;
       sw[2] = w.b;
+      if (!sw[0]) sk = stage_coeffs<Real>(sa, sp.g, sa.sc->dt);
     }
     __syncthreads();
     const int i = sw[1] * 32 + threadIdx.x, j = sw[2] * 8 + threadIdx.y;
@@ -2054,7 +2102,7 @@ __global__ void __launch_bounds__(256) k_update_batch(StageArgs<Real> B, const P
       continue;
     }
     update_cell_w<Real>(sa, sp.g, sp.det, Wd, d2_of<Real>(sp, 0), d2_of<Real>(sp, 1), i, j,
-                        sp.cell_off);
+                        sp.cell_off, sk);
   }
 }
 
