@@ -1446,20 +1446,6 @@ __device__ __forceinline__ void store_face(const StageArgs<Real>& A, const Grid&
   }
 }
 
-template <class Real, int DIR>
-__device__ void recompute_face(const StageArgs<Real>& A, const Grid& g, const DirectW<Real>& Wd,
-                               int iL, int jL, int K) {
-  Real F[4];
-  bool bl, br;
-  switch (K) {
-    case 0: face_at<0, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-    case 1: face_at<1, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-    case 2: face_at<2, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-    default: face_at<3, Real, DIR>(A.Xr, g, Wd, iL, jL, F, bl, br); break;
-  }
-  store_face<Real, DIR>(A, g, iL, jL, F, (uint8_t)((bl ? 1 : 0) | (br ? 2 : 0)));
-}
-
 // face f (0 W, 1 E, 2 S, 3 N) of queued cell c: recompute it if its EDP1
 // radius changed; the face shared with another queued cell is done by the
 // west/south one
@@ -1493,16 +1479,97 @@ __device__ __forceinline__ bool mood_face_plan(const StageArgs<Real>& A, const G
   return K != Kold;  // else the EDP1 order of this face is unchanged
 }
 
+// one Gauss point of a face recomputed by the MOOD loop, with the radius K
+// and the direction (0 x, 1 y) as run-time values: the lanes of one warp
+// hold faces of both directions and of several radii, and a compiled
+// variant per (K, direction) would run each variant present in the warp one
+// after the other, Riemann solver included.  One path for all: the stencil
+// rows beyond K are predicated off, and the y direction swaps the momenta
+// around the x solver by selects.  The arithmetic is that of
+// face_point<K, Real, DIR> (recon_direct's order, the same solver), so the
+// flux is the same bit for bit.  z: this point's weights of the left and
+// right states ([K][face][q][.] of DirectW, staged in shared memory).
 template <class Real>
-__device__ __forceinline__ void mood_face_item(const StageArgs<Real>& A, const Grid& g,
-                                               const DirectW<Real>& Wd, const Cascade& C,
-                                               const uint32_t* stamp, uint32_t cur, int c, int f) {
-  int iL, jL, K;
-  if (!mood_face_plan<Real>(A, g, C, stamp, cur, c, f, iL, jL, K)) return;
-  if (f < 2) recompute_face<Real, 0>(A, g, Wd, iL, jL, K);
-  else recompute_face<Real, 1>(A, g, Wd, iL, jL, K);
+__device__ __forceinline__ void recon_rt(const Real* X, const Grid& g, const Real* zL,
+                                         const Real* zR, int K, int iL, int jL, int iR, int jR,
+                                         Real* UL, Real* UR) {
+  // the stencil rows and their mirror pairs as loops that run K deep, the
+  // eight (side, variable) sums of one term side by side; each sum sees the
+  // operations of recon_direct<K> in their order
+  const long long vs = g.vstride;
+  const Real* XL = X + (long long)(jL + g.H) * g.pitch + (iL + g.H);
+  const Real* XR = X + (long long)(jR + g.H) * g.pitch + (iR + g.H);
+  Real sL[4], sR[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) sL[v] = sR[v] = Real(0);
+  int row = 0;  // stencil index of the row's first cell
+#pragma unroll 1
+  for (int b = -K; b <= K; ++b) {
+    const int hb = K - (b < 0 ? -b : b);
+    const int mid = row + hb;  // (0, b)
+    const Real* L0 = XL + (long long)b * g.pitch;
+    const Real* R0 = XR + (long long)b * g.pitch;
+    Real tL[4], tR[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      tL[v] = mul_rn(zL[mid], __ldg(L0 + v * vs));
+      tR[v] = mul_rn(zR[mid], __ldg(R0 + v * vs));
+    }
+#pragma unroll 1
+    for (int a = 1; a <= hb; ++a) {
+      const Real lp = zL[mid + a], lm = zL[mid - a], rp = zR[mid + a], rm = zR[mid - a];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        tL[v] = add_rn(tL[v], add_rn(mul_rn(lp, __ldg(L0 + v * vs + a)),
+                                     mul_rn(lm, __ldg(L0 + v * vs - a))));
+        tR[v] = add_rn(tR[v], add_rn(mul_rn(rp, __ldg(R0 + v * vs + a)),
+                                     mul_rn(rm, __ldg(R0 + v * vs - a))));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sL[v] = add_rn(sL[v], tL[v]);
+      sR[v] = add_rn(sR[v], tR[v]);
+    }
+    row += 2 * hb + 1;
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    UL[v] = K == 0 ? __ldg(XL + v * vs) : sL[v];
+    UR[v] = K == 0 ? __ldg(XR + v * vs) : sR[v];
+  }
 }
 
+template <class Real>
+__device__ __forceinline__ void face_point_rt(int K, int dir, const Real* X, const Grid& g,
+                                              const Real* zL, const Real* zR, int iL, int jL,
+                                              Real* f, bool& badL, bool& badR, Real* sUL,
+                                              Real* sUR) {
+  const int iR = iL + (dir == 0), jR = jL + (dir == 1);
+  Real UL[4], UR[4];
+  recon_rt<Real>(X, g, zL, zR, K, iL, jL, iR, jR, UL, UR);
+  const bool y = dir != 0;
+  const Real a[4] = {UL[0], y ? UL[2] : UL[1], y ? UL[1] : UL[2], UL[3]};
+  const Real b[4] = {UR[0], y ? UR[2] : UR[1], y ? UR[1] : UR[2], UR[3]};
+  Real h[4], pl, pr;
+  riemann_x<Real>(g.riemann, a, b, (Real)g.gamma, h, pl, pr);
+  f[0] = h[0];
+  f[1] = y ? h[2] : h[1];
+  f[2] = y ? h[1] : h[2];
+  f[3] = h[3];
+  badL |= !(pos_finite(UL[0]) && pos_finite(pl));
+  badR |= !(pos_finite(UR[0]) && pos_finite(pr));
+  if (sUL) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sUL[v] = UL[v];
+      sUR[v] = UR[v];
+    }
+  }
+}
+
+// the compiled variant of radius K (the FP32 path: its arithmetic is cheap
+// next to the run-time loops' overhead)
 template <class Real, int DIR>
 __device__ __forceinline__ void face_point_k(int K, const Real* X, const Grid& g,
                                              const DirectW<Real>& Wd, int iL, int jL, int q,
@@ -1516,60 +1583,19 @@ __device__ __forceinline__ void face_point_k(int K, const Real* X, const Grid& g
   }
 }
 
-// the MOOD face recompute of queued cells with one lane per Gauss point:
-// lane t covers cell queue[t / 16], face (t / 4) % 4, point t % 4.  Each
-// lane reconstructs its point's two states and solves its Riemann problem;
-// the group's first lane forms the Gauss sum in the order of face_at (mirror
-// pairs summed first), so the flux is the same bit for bit, with a quarter
-// of the dependent-operation chain per thread.  Called by whole warps.
+// DirectW's reconstruction weights, staged in shared memory by the FP64
+// MOOD kernel: the lanes of a warp read different radii, faces and points,
+// which a kernel parameter serves one address at a time
 template <class Real>
-__device__ __forceinline__ void mood_faces_lanes(const StageArgs<Real>& A, const Grid& g,
-                                                 const DirectW<Real>& Wd, const Cascade& C,
-                                                 const uint32_t* stamp, uint32_t cur,
-                                                 const int* queue, int n, long long gtid0,
-                                                 long long stride) {
-  const long long L = 16LL * n;
-  const int lane = threadIdx.x & 31;
-  const int base = lane & ~3;
-  // the loop runs per warp: all 32 lanes take part in the shuffles
-  for (long long t0 = gtid0 - lane; t0 < L; t0 += stride) {
-    const long long t = t0 + lane;
-    const int q = (int)(t & 3);
-    const int f = (int)((t >> 2) & 3);
-    int iL = 0, jL = 0, K = 0;
-    bool work = false;
-    if (t < L) work = mood_face_plan<Real>(A, g, C, stamp, cur, queue[t >> 4], f, iL, jL, K);
-    const int Q = rule_q(K);
-    Real fq[4] = {Real(0), Real(0), Real(0), Real(0)};
-    bool bl = false, br = false;
-    if (work && q < Q) {
-      if (f < 2) face_point_k<Real, 0>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br);
-      else face_point_k<Real, 1>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br);
-    }
-    Real fp[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) fp[p][v] = __shfl_sync(0xffffffffu, fq[v], base + p);
-    const unsigned bbl = __ballot_sync(0xffffffffu, bl), bbr = __ballot_sync(0xffffffffu, br);
-    if (work && q == 0) {
-      // face_at's loop over (g, -g) pairs written out per rule size
-      const Real w0 = Wd.w[K][0], w1 = Wd.w[K][1];
-      Real F[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const Real z = Real(0);
-        if (Q == 4) F[v] = fma(w1, add_rn(fp[1][v], fp[2][v]), fma(w0, add_rn(fp[0][v], fp[3][v]), z));
-        else if (Q == 3) F[v] = fma(w1, fp[1][v], fma(w0, add_rn(fp[0][v], fp[2][v]), z));
-        else if (Q == 2) F[v] = fma(w0, add_rn(fp[0][v], fp[1][v]), z);
-        else F[v] = fma(w0, fp[0][v], z);
-      }
-      const uint8_t bits = (uint8_t)((((bbl >> base) & 0xFu) ? 1 : 0) |
-                                     (((bbr >> base) & 0xFu) ? 2 : 0));
-      if (f < 2) store_face<Real, 0>(A, g, iL, jL, F, bits);
-      else store_face<Real, 1>(A, g, iL, jL, F, bits);
-    }
-  }
+struct MoodW {
+  Real z[4][4][kMaxQ][kMaxN];
+};
+template <class Real>
+__device__ __forceinline__ void stage_mood_weights(const DirectW<Real>& Wd, MoodW<Real>& S) {
+  Real* zs = &S.z[0][0][0][0];
+  const Real* zd = &Wd.z[0][0][0][0];
+  for (int k = threadIdx.x; k < 4 * 4 * kMaxQ * kMaxN; k += blockDim.x) zs[k] = zd[k];
+  __syncthreads();
 }
 
 // entry k (0 itself, 1 W, 2 E, 3 S, 4 N) of queued cell c's neighbourhood:
@@ -1708,8 +1734,9 @@ __device__ __forceinline__ long long mood_lane() {
 // warps (the loop runs per warp: all 32 lanes take part in the shuffles).
 template <class Real, class Site>
 __device__ __forceinline__ void mood_faces_phase(const Site& site, const MoodArgs& M,
-                                                 const DirectW<Real>& Wd, const Cascade& C,
-                                                 uint32_t cur, const int* queue, int n) {
+                                                 const DirectW<Real>& Wd, const MoodW<Real>& MW,
+                                                 const Cascade& C, uint32_t cur,
+                                                 const int* queue, int n) {
   const long long L = 16LL * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
@@ -1732,7 +1759,11 @@ __device__ __forceinline__ void mood_faces_phase(const Site& site, const MoodArg
           // a recorded step keeps the states of the recomputed face
           const bool keep = A.sc->ctl.stape != nullptr;
           Real UL[4], UR[4];
-          if (f < 2)
+          const int dir = f < 2 ? 0 : 1;
+          if constexpr (sizeof(Real) == sizeof(double))
+            face_point_rt<Real>(K, dir, A.Xr, g, MW.z[K][2 * dir][q], MW.z[K][2 * dir + 1][q],
+                                iL, jL, fq, bl, br, keep ? UL : nullptr, UR);
+          else if (dir == 0)
             face_point_k<Real, 0>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br, keep ? UL : nullptr, UR);
           else
             face_point_k<Real, 1>(K, A.Xr, g, Wd, iL, jL, q, fq, bl, br, keep ? UL : nullptr, UR);
@@ -1750,17 +1781,20 @@ __device__ __forceinline__ void mood_faces_phase(const Site& site, const MoodArg
       for (int v = 0; v < 4; ++v) fp[p][v] = __shfl_sync(0xffffffffu, fq[v], base + p);
     const unsigned bbl = __ballot_sync(0xffffffffu, bl), bbr = __ballot_sync(0xffffffffu, br);
     if (work && q == 0) {
-      // face_at's loop over (g, -g) pairs written out per rule size
+      // face_at's loop over (g, -g) pairs, one path for every rule size:
+      // Q = 4: w1 (f1 + f2) + w0 (f0 + f3); Q = 3: w1 f1 + w0 (f0 + f2);
+      // Q = 2: w0 (f0 + f1); Q = 1: w0 (f0 + 0), which rounds as w0 f0
       const int Q = rule_q(K);
       const Real w0 = Wd.w[K][0], w1 = Wd.w[K][1];
       Real F[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const Real z = Real(0);
-        if (Q == 4) F[v] = fma(w1, add_rn(fp[1][v], fp[2][v]), fma(w0, add_rn(fp[0][v], fp[3][v]), z));
-        else if (Q == 3) F[v] = fma(w1, fp[1][v], fma(w0, add_rn(fp[0][v], fp[2][v]), z));
-        else if (Q == 2) F[v] = fma(w0, add_rn(fp[0][v], fp[1][v]), z);
-        else F[v] = fma(w0, fp[0][v], z);
+        const Real last = Q == 4 ? fp[3][v] : Q == 3 ? fp[2][v] : Q == 2 ? fp[1][v] : z;
+        const Real inner = fma(w0, add_rn(fp[0][v], last), z);
+        const Real mid = Q == 4 ? add_rn(fp[1][v], fp[2][v]) : fp[1][v];
+        const Real outer = fma(w1, mid, inner);
+        F[v] = Q >= 3 ? outer : inner;
       }
       const uint8_t bits = (uint8_t)((((bbl >> base) & 0xFu) ? 1 : 0) |
                                      (((bbr >> base) & 0xFu) ? 2 : 0));
@@ -1827,7 +1861,10 @@ __device__ __forceinline__ void mood_loop_body(const Site& site, const MoodArgs&
   const int cap = sc->ctl.max_iters;
   if (leader) sc->count[1] = 0;
   bool ok = true;
+  __shared__ MoodW<Real> MW;
   if (n > 0) {
+    // n is the same in every block; FP32 reads the kernel parameter
+    if constexpr (sizeof(Real) == sizeof(double)) stage_mood_weights<Real>(Wd, MW);
     uint32_t* st = stamp_of(M, cur);
     for (long long q = mood_lane(); q < n; q += stride) {
       const int gc = M.queue[0][q];
@@ -1845,7 +1882,7 @@ __device__ __forceinline__ void mood_loop_body(const Site& site, const MoodArgs&
       break;
     }
     const int* queue = M.queue[slot];
-    mood_faces_phase<Real>(site, M, Wd, C, cur, queue, n);
+    mood_faces_phase<Real>(site, M, Wd, MW, C, cur, queue, n);
     if (!grid_barrier(sc)) break;
     int* next_count = &sc->count[slot ^ 1];
     mood_update_phase<Real>(site, M, Wd, C, cur, queue, n, M.queue[slot ^ 1], next_count);
@@ -1910,7 +1947,7 @@ __device__ __forceinline__ void mood_loop_tail(const Grid& g, Scalars* sc, const
 }
 
 template <class Real>
-__global__ void __launch_bounds__(256) k_mood_loop(StageArgs<Real> A, MoodArgs M, Grid g,
+__global__ void __launch_bounds__(256, 2) k_mood_loop(StageArgs<Real> A, MoodArgs M, Grid g,
                                                    Detect D,
                                                    const __grid_constant__ DirectW<Real> Wd,
                                                    Cascade C, int stage, LoopTail T) {
@@ -2135,7 +2172,7 @@ struct BatchSite {
 };
 
 template <class Real>
-__global__ void __launch_bounds__(256) k_mood_loop_batch(StageArgs<Real> B, MoodArgs M,
+__global__ void __launch_bounds__(256, 2) k_mood_loop_batch(StageArgs<Real> B, MoodArgs M,
                                                          const Prob* probs, const Scalars* psc,
                                                          int nprob,
                                                          const __grid_constant__ DirectW<Real> Wd,
