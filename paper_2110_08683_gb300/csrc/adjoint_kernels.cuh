@@ -20,6 +20,10 @@
 
 namespace gpm {
 
+// x != 0 as IEEE decides it (a NaN is nonzero), on the integer pipes in FP64
+__device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(float x) { return x != 0.0f; }
+
 // inverse square root by Newton-Raphson from the hardware approximation:
 // each step y <- y (3/2 - (z/2) y^2) squares the relative error.  FP64:
 // rsqrt.approx.ftz.f64 and two steps; FP32: rsqrt.approx.ftz.f32 and one.
@@ -56,30 +60,28 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
   const Real yL = rsqrt_nr(zL), yR = rsqrt_nr(zR);  // 1 / c
   const Real cL = zL * yL, cR = zR * yR;
   const Real aL = uL - cL, bL = uR - cR;
-  const bool selA = aL < bL;
+  const bool selA = lt_num(aL, bL);
   const Real SL = selA ? aL : bL;
   const Real aR = uL + cL, bR = uR + cR;
-  const bool selAR = aR > bR;
+  const bool selAR = lt_num(bR, aR);
   const Real SR = selAR ? aR : bR;
   const Real dL = SL - uL, dR = SR - uR;
   const Real num = pR - pL + rL * uL * dL - rR * uR * dR;
   const Real den = rL * dL - rR * dR;
   const Real iden = recip(den);
   const Real Ss = num * iden;
-  const bool left = Ss >= Real(0);
-  const bool useL = SL >= Real(0);
-  const bool useS = !useL && (left || (SR > Real(0)));
+  // the forward's decisions, compared on the integer pipes (the taped
+  // states lie in the solver's domain, where every value is finite)
+  const bool left = ge0_num(Ss);
+  const bool useL = ge0_num(SL);
+  const bool useS = !useL && (left || gt0_num(SR));
+  // the one physical flux the forward used: F_L if S_L >= 0, F_R if
+  // S_R <= 0, else F_K of the star side; its adjoint is Fb in every case
+  const bool sideL = useL || (useS && left);
   // adjoints of the intermediates
   Real rLb = 0, rRb = 0, uLb = 0, uRb = 0, vLb = 0, vRb = 0, pLb = 0, pRb = 0, ELb = 0, ERb = 0;
   Real SLb = 0, SRb = 0, Ssb = 0, irLb = 0, irRb = 0, dLb = 0, dRb = 0;
-  Real FLb[4] = {0, 0, 0, 0}, FRb[4] = {0, 0, 0, 0};
-  if (useL) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) FLb[k] = Fb[k];
-  } else if (!useS) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) FRb[k] = Fb[k];
-  } else {
+  if (useS) {
     // star state of side K (hllc_x's second form: m = rho_K d_K,
     // D = 1 / (S_K - S*), rho* = m D, (rho E)* = D (d_K E_K + (S* - u_K) A),
     // A = m S* + p_K)
@@ -94,10 +96,9 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
     const Real UKs[4] = {fK, fK * Ss, fK * vK, iD * Cq};
     const Real* UK = left ? UL : UR;
     // Fs[v] = FK[v] + SK (UKs[v] - UK[v])
-    Real FKb[4], UKsb[4], SKb = 0, UKb[4];
+    Real UKsb[4], SKb = 0, UKb[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      FKb[k] = Fb[k];
       SKb += Fb[k] * (UKs[k] - UK[k]);
       UKsb[k] = SK * Fb[k];
       UKb[k] = -SK * Fb[k];
@@ -125,15 +126,11 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
     SKb += Db;
     Ssb -= Db;
     if (left) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) FLb[k] += FKb[k];
       rLb += rKb; uLb += uKb; vLb += vKb; ELb += EKb; pLb += pKb; SLb += SKb;
       dLb += dKb;
 #pragma unroll
       for (int k = 0; k < 4; ++k) UbL[k] += UKb[k];
     } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) FRb[k] += FKb[k];
       rRb += rKb; uRb += uKb; vRb += vKb; ERb += EKb; pRb += pKb; SRb += SKb;
       dRb += dKb;
 #pragma unroll
@@ -156,21 +153,23 @@ __device__ __forceinline__ void hllc_x_vjp(const Real* UL, const Real* UR, Real 
   Real cLb = 0, cRb = 0;
   if (selA) { uLb += SLb; cLb -= SLb; } else { uRb += SLb; cRb -= SLb; }
   if (selAR) { uLb += SRb; cLb += SRb; } else { uRb += SRb; cRb += SRb; }
-  // physical fluxes FL = (rL uL, rL uL uL + pL, rL uL vL, uL (EL + pL))
-  rLb += FLb[0] * uL + FLb[1] * uL * uL + FLb[2] * uL * vL;
-  uLb += FLb[0] * rL + FLb[1] * Real(2) * rL * uL + FLb[2] * rL * vL + FLb[3] * (UL[3] + pL);
-  vLb += FLb[2] * rL * uL;
-  pLb += FLb[1] + FLb[3] * uL;
-  ELb += FLb[3] * uL;
-  rRb += FRb[0] * uR + FRb[1] * uR * uR + FRb[2] * uR * vR;
-  uRb += FRb[0] * rR + FRb[1] * Real(2) * rR * uR + FRb[2] * rR * vR + FRb[3] * (UR[3] + pR);
-  vRb += FRb[2] * rR * uR;
-  pRb += FRb[1] + FRb[3] * uR;
-  ERb += FRb[3] * uR;
+  // the physical flux of side X, F = (r u, r u u + p, r u v, u (E + p))
+  {
+    const Real rX = sideL ? rL : rR, uX = sideL ? uL : uR, vX = sideL ? vL : vR;
+    const Real pX = sideL ? pL : pR, EX = sideL ? UL[3] : UR[3];
+    const Real rXb = Fb[0] * uX + Fb[1] * uX * uX + Fb[2] * uX * vX;
+    const Real uXb = Fb[0] * rX + Fb[1] * Real(2) * rX * uX + Fb[2] * rX * vX + Fb[3] * (EX + pX);
+    const Real vXb = Fb[2] * rX * uX, pXb = Fb[1] + Fb[3] * uX, EXb = Fb[3] * uX;
+    if (sideL) {
+      rLb += rXb; uLb += uXb; vLb += vXb; pLb += pXb; ELb += EXb;
+    } else {
+      rRb += rXb; uRb += uXb; vRb += vXb; pRb += pXb; ERb += EXb;
+    }
+  }
   // c = sqrt(z), z = gam p ir: dc/dz = 1 / (2 c) = y / 2
   const Real zLb = cLb * Real(0.5) * yL, zRb = cRb * Real(0.5) * yR;
-  if (cLb != Real(0)) { pLb += zLb * gam * irL; irLb += zLb * gam * pL; }
-  if (cRb != Real(0)) { pRb += zRb * gam * irR; irRb += zRb * gam * pR; }
+  if (nonzero(cLb)) { pLb += zLb * gam * irL; irLb += zLb * gam * pL; }
+  if (nonzero(cRb)) { pRb += zRb * gam * irR; irRb += zRb * gam * pR; }
   // p = gm1 (E - 0.5 (m_x u + m_y v))
   ELb += pLb * gm1;
   Real mxLb = -Real(0.5) * gm1 * pLb * uL, myLb = -Real(0.5) * gm1 * pLb * vL;
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(32 * FW) k_adj_faces_sweep(
 // direction's left and right states [4][qt][faces] of the stage.  The states
 // are those the forward solved from, so the result equals the sweep's.
 template <class Real, int DIR>
-__global__ void __launch_bounds__(128) k_adj_faces_stored(
+__global__ void __launch_bounds__(128, 4) k_adj_faces_stored(
     const Real* tL, const Real* tR, int qt, const double* vin, const uint8_t* ord, Grid g,
     const __grid_constant__ ParityW<Real> W, const __grid_constant__ DirectW<Real> Wd,
     AdjFaces A) {
