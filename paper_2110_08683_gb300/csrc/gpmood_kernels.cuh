@@ -1010,8 +1010,12 @@ __device__ __forceinline__ void faces_xy_block(const StageArgs<Real>& A, const G
   }
 }
 
+// resident blocks of the fused face kernel: FP64 2 (128 registers), FP32 4
+template <class Real>
+constexpr int xy_min_blocks() { return sizeof(Real) == sizeof(double) ? 2 : 4; }
+
 template <int R, class Real>
-__global__ void __launch_bounds__(32 * kXYRows, 2) k_faces_xy(StageArgs<Real> A, Grid g,
+__global__ void __launch_bounds__(32 * kXYRows, xy_min_blocks<Real>()) k_faces_xy(StageArgs<Real> A, Grid g,
                                                            const __grid_constant__ ParityW<Real> W) {
   pdl_wait();
   pdl_trigger();
