@@ -2088,7 +2088,7 @@ __global__ void __launch_bounds__(32 * FW) k_faces_batch(StageArgs<Real> B, cons
 
 // the fused x+y face kernel over (problem, segment, band) work items
 template <int R, class Real>
-__global__ void __launch_bounds__(32 * kXYRows, 2) k_faces_xy_batch(
+__global__ void __launch_bounds__(32 * kXYRows, xy_min_blocks<Real>()) k_faces_xy_batch(
     StageArgs<Real> B, const Prob* probs, const Scalars* psc, const Item* items,
     const __grid_constant__ ParityW<Real> W) {
   pdl_wait();
