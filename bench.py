@@ -742,11 +742,14 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": k, "warmup": 0, "ms_per_step": span * 1e3 / k, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        # the same configuration keys as the GPU arm's line; how the oracle
+        # ran (host processes, the bounded sample) is in cpu_baseline
         "config": {"workload": workload_name(kind, *DEFAULT_SIZE[kind], scheme),
                    "cells": DEFAULT_SIZE[kind][0] * DEFAULT_SIZE[kind][1], "precision": "fp64",
-                   "parallelism": f"host, {P} processes", "sample_cells": nx * ny},
+                   "parallelism": f"replicas x{world}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
-                         "sample": sample,
+                         "sample": sample, "sample_cells": nx * ny,
+                         "processes": P,
                          "single_thread": {"value": one, "unit": UNIT, "cores": 1,
                                            "seconds": round(span1, 2)},
                          "host": host_info()},

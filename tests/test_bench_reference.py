@@ -28,4 +28,5 @@ def test_reference_arm_prints_one_json_line():
                         "d2h_bytes_per_step": 0}
     # the workload is the full double Mach reflection; each step of the
     # oracle is a step of the same problem on the sample grid
-    assert d["config"]["cells"] == 4096 * 1024 and d["config"]["sample_cells"] == 64 * 16
+    assert d["config"]["cells"] == 4096 * 1024 and d["cpu_baseline"]["sample_cells"] == 64 * 16
+    assert d["config"]["parallelism"] == "replicas x1"
