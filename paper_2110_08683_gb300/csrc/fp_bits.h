@@ -61,3 +61,34 @@ FPB_FN float fpb_double_to_float_rn(double x) {
   if (rem > half || (rem == half && (k & 1ull))) k += 1ull;
   return fpb_float_of_bits(sign | (uint32_t)k);
 }
+
+// comparisons of doubles on integer arithmetic.  The IEEE order of doubles
+// that are not NaN is the order of the keys b ^ ((b >> 63) & 0x7fff...) of
+// their bit patterns b, read as signed integers, save that -0 and +0 compare
+// equal.  Each function gives exactly the IEEE answer for the inputs its
+// name allows ("num": neither is NaN; "ieee": any input, false with a NaN).
+FPB_FN int64_t fpb_order_key(double x) {
+  const int64_t b = (int64_t)fpb_bits_of_double(x);
+  return b ^ ((b >> 63) & INT64_MAX);
+}
+FPB_FN int fpb_is_nan(double x) {
+  return (int64_t)(fpb_bits_of_double(x) & 0x7fffffffffffffffull) > 0x7ff0000000000000ll;
+}
+// a < b
+FPB_FN int fpb_lt_num(double a, double b) {
+  const uint64_t both = fpb_bits_of_double(a) | fpb_bits_of_double(b);
+  return fpb_order_key(a) < fpb_order_key(b) && (both << 1) != 0;
+}
+FPB_FN int fpb_lt_ieee(double a, double b) {
+  return !fpb_is_nan(a) && !fpb_is_nan(b) && fpb_lt_num(a, b);
+}
+// a <= b
+FPB_FN int fpb_le_ieee(double a, double b) {
+  return !fpb_is_nan(a) && !fpb_is_nan(b) && !fpb_lt_num(b, a);
+}
+// x >= 0 and x > 0
+FPB_FN int fpb_ge0_num(double x) {
+  const int64_t b = (int64_t)fpb_bits_of_double(x);
+  return b >= 0 || b == INT64_MIN;
+}
+FPB_FN int fpb_gt0_num(double x) { return (int64_t)fpb_bits_of_double(x) > 0; }

@@ -222,43 +222,25 @@ __device__ __forceinline__ bool pos_finite(float x) {
   const int b = __float_as_int(x);
   return b > 0 && b < 0x7f800000;
 }
-// comparisons of doubles on the integer pipes.  An FP64 compare, min or max
+// comparisons of doubles on the integer pipes (fp_bits.h: the IEEE answer
+// exactly, for the inputs each name allows).  An FP64 compare, min or max
 // occupies the FP64 pipe like an FMA does (on this GPU about 64 cycles per
 // warp instruction per sub-partition), a 64-bit integer compare a few
-// cycles.  The IEEE order of doubles that are not NaN is the order of the
-// keys b ^ ((b >> 63) & 0x7fff...) of their bit patterns b, save that -0 and
-// +0 compare equal; each helper gives exactly the IEEE result for the inputs
-// its name allows.  FP32 keeps the hardware compare, which is cheap.
-__device__ __forceinline__ long long order_key(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-__device__ __forceinline__ bool is_nan(double x) {
-  return (__double_as_longlong(x) & 0x7fffffffffffffffll) > 0x7ff0000000000000ll;
-}
+// cycles.  FP32 keeps the hardware compare, which is cheap.
+__device__ __forceinline__ bool is_nan(double x) { return fpb_is_nan(x); }
 // a < b, a and b not NaN
-__device__ __forceinline__ bool lt_num(double a, double b) {
-  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
-  return order_key(a) < order_key(b) && ((ia | ib) << 1) != 0;
-}
+__device__ __forceinline__ bool lt_num(double a, double b) { return fpb_lt_num(a, b); }
 __device__ __forceinline__ bool lt_num(float a, float b) { return a < b; }
 // a < b with NaN (false when either is NaN)
-__device__ __forceinline__ bool lt_ieee(double a, double b) {
-  return !is_nan(a) && !is_nan(b) && lt_num(a, b);
-}
+__device__ __forceinline__ bool lt_ieee(double a, double b) { return fpb_lt_ieee(a, b); }
 __device__ __forceinline__ bool lt_ieee(float a, float b) { return a < b; }
 // a <= b with NaN (false when either is NaN)
-__device__ __forceinline__ bool le_ieee(double a, double b) {
-  return !is_nan(a) && !is_nan(b) && !lt_num(b, a);
-}
+__device__ __forceinline__ bool le_ieee(double a, double b) { return fpb_le_ieee(a, b); }
 __device__ __forceinline__ bool le_ieee(float a, float b) { return a <= b; }
 // x >= 0 and x > 0, x not NaN
-__device__ __forceinline__ bool ge0_num(double x) {
-  const long long b = __double_as_longlong(x);
-  return b >= 0 || b == (long long)0x8000000000000000ull;
-}
+__device__ __forceinline__ bool ge0_num(double x) { return fpb_ge0_num(x); }
 __device__ __forceinline__ bool ge0_num(float x) { return x >= 0.0f; }
-__device__ __forceinline__ bool gt0_num(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool gt0_num(double x) { return fpb_gt0_num(x); }
 __device__ __forceinline__ bool gt0_num(float x) { return x > 0.0f; }
 // a < b ? a : b and a > b ? a : b, a and b not NaN
 template <class Real>
