@@ -99,7 +99,8 @@ def faces_flops_per_face(R=3, fused=False):
     return (256 * sums + (224 + 256) * dots) / (2 * 7 * 31) + riemann
 
 
-FACE_KERNEL_SOURCES = ("gpmood_kernels.cuh", "gpmood_internal.h", "kernels_impl.cuh")
+FACE_KERNEL_SOURCES = ("gpmood_kernels.cuh", "gpmood_internal.h", "kernels_impl.cuh",
+                       "fp_bits.h")
 
 
 def kernel_source_hash():
