@@ -107,7 +107,7 @@ void prim_to_cons(const double* P, double gam, double* U) {
 
 // a pointer kernels may dereference: device memory as given (on_device), or
 // page-locked host memory through its device mapping; null for pageable
-// host memory, which goes through the driver's staged copies
+// host memory, which goes through the CUDA driver's staged copies
 const double* device_view(const double* p, int on_device) {
   if (on_device) return p;
   cudaPointerAttributes a;
@@ -291,7 +291,7 @@ void write_control(gpmood_t h, double cfl, double fixed_dt, int clip, double t_e
 }
 
 int push_control(gpmood_t h) {
-  // pageable source: staged by the driver at the call, so the host copy may
+  // pageable source: staged by the CUDA driver at the call, so the host copy may
   // change right after
   CK(cudaMemcpyAsync(&h->sc->ctl, &h->ctl, sizeof(Control), cudaMemcpyHostToDevice, h->stream));
   h->ctl_dev = h->ctl;
@@ -582,20 +582,20 @@ int capture_step(gpmood_t h, int cur, int prof, int record, cudaGraphExec_t* out
   g_pdl = h->pdl;
   int rc = capture_step_impl(h, cur, prof, record, want_gate, out);
   if (rc && h->pdl) {
-    // the driver refused programmatic edges in the step graph: plain
+    // the CUDA driver refused programmatic edges in the step graph: plain
     // stream order from now on
     h->pdl = 0;
     g_pdl = 0;
     rc = capture_step_impl(h, cur, prof, record, want_gate, out);
   }
   if (rc && h->coop) {
-    // the driver refused a cooperative kernel node: a plain launch of the
+    // the CUDA driver refused a cooperative kernel node: a plain launch of the
     // same co-resident grid
     h->coop = 0;
     rc = capture_step_impl(h, cur, prof, record, want_gate, out);
   }
   if (rc && want_gate && h->gated_ok == 0) {
-    // the driver refused the gated graph: plain graphs without the gate, and
+    // the CUDA driver refused the gated graph: plain graphs without the gate, and
     // asynchronous steps run synchronously from now on
     h->gated_ok = -1;
     rc = capture_step_impl(h, cur, prof, record, 0, out);
@@ -947,7 +947,7 @@ int gpmood_set_state(gpmood_t h, const double* U, int on_device) {
     k_set_interior<<<152 * 8, 256, 0, h->stream>>>(src, h->U[0], h->Uf[0], g);
     CK(cudaGetLastError());
   } else {
-    // pageable host memory: staged copies by the driver
+    // pageable host memory: staged copies by the CUDA driver
     for (int v = 0; v < 4; ++v) {
       double* dst = h->U[0] + v * g.vstride + (size_t)g.H * g.pitch + g.H;
       const double* s = U + (size_t)v * g.nx * g.ny;

@@ -515,7 +515,7 @@ int batch_step(gpmood_batch_t b, double cfl, double fixed_dt, int clip, double t
     if (!ge) {
       int rc = capture_b(b, b->cur, prof, &ge);
       if (rc && b->coop) {
-        // the driver refused a cooperative kernel node: a plain launch of
+        // the CUDA driver refused a cooperative kernel node: a plain launch of
         // the same co-resident grid
         b->coop = 0;
         rc = capture_b(b, b->cur, prof, &ge);

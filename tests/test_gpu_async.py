@@ -164,7 +164,7 @@ def test_fused_face_kernel_equals_the_two_sweeps(precision, R):
 def test_state_io_through_pinned_host_memory(precision):
     """set_state / get_state on page-locked host buffers go through one
     kernel that reads or writes the host memory directly; pageable buffers
-    through the driver's staged copies.  Both give the same steps."""
+    through the CUDA driver's staged copies.  Both give the same steps."""
     torch = pytest.importorskip("torch")
     p = _quads()
     shape = p["U0"].shape
